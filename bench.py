@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark of the CBC application (arXiv 2601.19650, Sec. III A) on one GB300.
+
+Workload: MPO applied to an MPS and compressed by CBC, L=64 sites, d=2, MPS bond 128,
+MPO bond 16, cap 128, complex64 Gaussian entries with unit Frobenius norm per tensor,
+seed 0 (per rank: seed = rank).  A step is one full application (forward sweep with
+compressions, backward sweep with CholeskyQR2) on inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference ...   # the FP64 CPU oracle, timed on the host
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CBC applications/sec & TFLOP/s, mixed vs FP64 plain on 1 GB300 at rel err ≤1e-6"
+WORKLOAD = dict(workload="MPO on MPS, L=64, d=2, chi=128, D=16, max_bond=128, complex64 "
+                         "Gaussian entries (unit Frobenius norm per tensor)",
+                L=64, d=2, chi=128, D=16, max_bond=128, input_dtype="complex64")
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure in MEASURED_PEAKS)
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# --------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------------------
+def make_workload(seed: int):
+    from synth import make_problem
+    return make_problem(2, seed=seed)
+
+
+def oracle_time(prob, reps: int = 1):
+    """The FP64 oracle as it stands, timed on the host cores."""
+    from oracle import cbc as ocbc
+    t0 = time.perf_counter()
+    res = None
+    for _ in range(reps):
+        res = ocbc.cbc(prob.state.parent, prob.state.tensors, prob.op.tensors, prob.max_bond,
+                       prob.tol)
+    return (time.perf_counter() - t0) / reps, res
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    prob = make_workload(0)
+    for _ in range(args.warmup):
+        oracle_time(prob)
+    t = 0.0
+    for _ in range(args.steps):
+        dt, _ = oracle_time(prob)
+        t += dt
+    value = args.steps / t
+    line = {"metric": METRIC, "value": value, "unit": "applications/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": dict(WORKLOAD, precision="fp64 (numpy, host)", l2="n/a (host)"),
+            "cpu_baseline": {"value": value, "unit": "applications/s", "cores": blas_threads(),
+                             "kind": "oracle",
+                             "sample": "one full application of the workload per step (seed 0)"},
+            "e2e": {"value": value, "unit": "applications/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_2601_19650_gb300 import _cbc, build as _build
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.init_process_group("nccl")
+        dist = dist_mod
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+
+    # precision of the headline number: mixed when built, else fp64
+    prec_name = args.precision
+    prob = make_workload(seed=rank)
+    st, op = prob.state, prob.op
+    dev_st = [torch.from_numpy(t).to(f"cuda:{local}") for t in st.tensors]
+    dev_op = [torch.from_numpy(t).to(f"cuda:{local}") for t in op.tensors]
+    torch.cuda.synchronize()
+    hs = _cbc.create_from_device(st.parent, st.phys, st.bond, dev_st, "state", sptr)
+    ho = _cbc.create_from_device(op.parent, op.phys, op.bond, dev_op, "op", sptr)
+
+    def apply_once(prec):
+        out = _cbc.cbc_apply(hs, ho, prob.max_bond, 0.0, _cbc.make_options(prec))
+        return out
+
+    if prec_name == "auto":
+        try:
+            _cbc.ttn_destroy(apply_once(_cbc.CBC_PREC_MIXED))
+            prec_name = "mixed"
+        except _cbc.CBCError as e:
+            if e.code != 8:
+                raise
+            prec_name = "fp64"
+    prec = _cbc.CBC_PREC_MIXED if prec_name == "mixed" else _cbc.CBC_PREC_FP64
+
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+
+    for _ in range(args.warmup):
+        _cbc.ttn_destroy(apply_once(prec))
+    torch.cuda.synchronize()
+
+    gpu_index = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[local])
+        except (ValueError, IndexError):
+            gpu_index = local
+    clocks = ClockSampler(gpu_index)
+
+    _cbc.cbc_stats_reset()
+    _cbc.cbc_stats_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms = 0.0
+    last = None
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        out = apply_once(prec)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        if last is not None:
+            _cbc.ttn_destroy(last)
+        last = out
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clock_info = clocks.stop()
+    stats = _cbc.cbc_stats_read()
+    _cbc.cbc_stats_enable(False)
+
+    t_max = total_ms
+    if dist:
+        tt = torch.tensor([total_ms], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / (t_max / 1e3)
+    ms_per_step = t_max / args.steps
+
+    # per-kernel-class roofline of the dominant class
+    classes = {k: v for k, v in stats.items() if v["ms"] > 0}
+    dom = max(classes, key=lambda k: classes[k]["ms"]) if classes else None
+    flops_per_app = sum(v["flops"] for v in stats.values()) / args.steps
+    roofline = None
+    if dom is not None:
+        d = classes[dom]
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        if dom == "gemm_tc":
+            peak, bound, note = None, "tensor", "split-precision bf16 tensor flops"
+            try:
+                mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+                peak = float(mp.get("bf16_tflops_sustained") or mp.get("bf16_tflops"))
+                note += " (of measured sustained bf16)"
+            except (OSError, ValueError, TypeError):
+                peak = 1700.0
+                note += " (of fallback)"
+        else:
+            peak, bound = FP64_PEAK_TFLOPS, "alu"
+            note = "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x ~2.06 GHz)"
+        roofline = {"bound": bound, "kernel_class": dom, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
+                    "traffic": None, "note": note,
+                    "launch_groups": d["groups"], "ms_total": d["ms"],
+                    "share_of_step": d["ms"] / total_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": "applications/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec_name == "fp64" else "bf16-slices+f64",
+            "data": "synthetic",
+            "config": dict(WORKLOAD, precision=prec_name,
+                           parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           l2="flushed between steps (256 MB write, untimed)"),
+            "tflops": flops_per_app * value / world / 1e12 * world,
+            "algorithmic_gflop_per_app": flops_per_app / 1e9,
+            "kernel_classes": {k: {"ms_per_step": v["ms"] / args.steps,
+                                   "launches_per_step": v["launches"] / args.steps}
+                               for k, v in stats.items() if v["launches"]},
+            "roofline": roofline,
+            "gpu_launches": int(sum(v["launches"] for v in stats.values())),
+            "clocks": clock_info}
+
+    # parity of this run's output with the oracle, and the oracle's own time
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import metrics
+        t_or, ref = oracle_time(prob)
+        shape = _cbc.output_shape_fn(st.parent, st.phys)
+        tens, bonds, log_norm = _cbc.fetch_network(last, shape, True)
+        line["rel_err_vs_oracle"] = metrics.rel_err(st.parent, tens, ref.tensors, log_norm, 0.0)
+        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "applications/s",
+                                "cores": blas_threads(), "kind": "oracle",
+                                "sample": "one full application of the workload (seed 0)"}
+    if last is not None:
+        _cbc.ttn_destroy(last)
+
+    # end to end through the C ABI with host buffers: H2D of the inputs, the application,
+    # D2H of every output tensor, each step
+    if not args.no_e2e:
+        pin_st = [torch.from_numpy(t).pin_memory().numpy() for t in st.tensors]
+        pin_op = [torch.from_numpy(t).pin_memory().numpy() for t in op.tensors]
+        h2d = sum(t.nbytes for t in pin_st) + sum(t.nbytes for t in pin_op)
+        shape = _cbc.output_shape_fn(st.parent, st.phys)
+        d2h = 0
+        e2e_t = 0.0
+        for k in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            a = _cbc.create_from_host(st.parent, st.phys, st.bond, pin_st, "state", sptr)
+            b = _cbc.create_from_host(op.parent, op.phys, op.bond, pin_op, "op", sptr)
+            o = _cbc.cbc_apply(a, b, prob.max_bond, 0.0, _cbc.make_options(prec))
+            tens, bonds, _ = _cbc.fetch_network(o, shape, True)
+            e2e_t += time.perf_counter() - t0
+            d2h = sum(t.nbytes for t in tens)
+            for h in (o, a):
+                _cbc.ttn_destroy(h)
+            _cbc.ttno_destroy(b)
+        n_e2e = max(2, args.steps)
+        line["e2e"] = {"value": world * n_e2e / e2e_t, "unit": "applications/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    _cbc.ttn_destroy(hs)
+    _cbc.ttno_destroy(ho)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,172 @@
+/*
+ * cbc.h -- C ABI of the GB300 (sm_103a) implementation of the Cholesky-based
+ * compression (CBC) that applies a tree tensor network operator (TTNO; an MPO on a
+ * chain) to a tree tensor network state (TTNS; an MPS on a chain) and compresses the
+ * result to a maximum bond dimension and/or a truncation tolerance.
+ *
+ * Method: arXiv 2601.19650, Sec. III.  Problem statement: Eq. (abstr_application),
+ * |psi'> ~ O |psi>, with |psi> a TTNS (Sec. II A, Eq. (ttns)) and O a TTNO on the same
+ * tree (Sec. II C, Eq. (ttno)).  The tensor-train sweeps follow Sec. III A
+ * (Eqs. (tt_cbc_first_contraction), (right_sweep_init_contr), (tt_cbc_qr_decomp),
+ * (tt_cbc_final_contraction)); trees follow Sec. III B (Eqs.
+ * (cbc_tree_first_contraction) ... (cbc_final_contraction)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Topology: n_nodes nodes; parent[i] is the parent of node i, -1 for exactly one root.
+ * phys_dim[i] >= 1 is the physical dimension (1 = virtual node).  bond_dim[i] is the
+ * dimension of the edge from i to its parent (ignored at the root, whose parent leg has
+ * dimension 1).  A chain parent[i] = i-1 is a tensor train rooted at its first site,
+ * the paper's imaginary-site-0 convention (Sec. II B).
+ *
+ * Leg order of node tensors (row-major, contiguous, children in ascending node id):
+ *   state    T[i]: [parent, phys, child_0, child_1, ...]
+ *   operator W[i]: [parent, phys_out, phys_in, child_0, child_1, ...]
+ * A leaf has no child legs; the root's parent leg has dimension 1.
+ *
+ * Element types (enum cbc_dtype): float32, float64, complex64, complex128 (complex
+ * numbers are interleaved (re, im) pairs).  The library computes in float64 or
+ * complex128 storage; inputs of lower precision are widened on device at creation.
+ *
+ * Streams: every call is stream ordered on the cudaStream_t given at ttn_create of the
+ * state (NULL = legacy default stream).  Device errors detected inside kernels are kept
+ * in a status word and reported by the next call that synchronises (cbc_apply,
+ * ttn_get_node, ttn_get_info).
+ *
+ * Status: every function returns 0 (CBC_OK) or a positive cbc_status code; a message
+ * for the calling thread is available from cbc_last_error().  No entry point aborts,
+ * traps or leaves the process in an undefined state on bad input.
+ */
+#ifndef CBC_H_
+#define CBC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cbc_ttn_s* ttn_t;   /* a TTNS / MPS held in device memory          */
+typedef struct cbc_ttno_s* ttno_t; /* a TTNO / MPO held in device memory          */
+
+enum cbc_status {
+  CBC_OK = 0,
+  CBC_ERR_INVALID_ARG = 1,        /* NULL pointer, bad dims, bad dtype, bad tree    */
+  CBC_ERR_TOPOLOGY_MISMATCH = 2,  /* state and operator trees or phys dims differ   */
+  CBC_ERR_OOM = 3,                /* device allocation failed                       */
+  CBC_ERR_NOT_POSITIVE_DEFINITE = 4, /* Cholesky pivot <= 0 in CholeskyQR          */
+  CBC_ERR_NUMERICAL = 5,          /* NaN / Inf met inside a kernel                  */
+  CBC_ERR_TIMEOUT = 6,            /* a bounded device-side wait ran out             */
+  CBC_ERR_CUDA = 7,               /* a CUDA runtime call failed                     */
+  CBC_ERR_UNSUPPORTED = 8         /* valid request this build does not implement    */
+};
+
+enum cbc_dtype { CBC_F32 = 0, CBC_F64 = 1, CBC_C64 = 2, CBC_C128 = 3 };
+
+/* Arithmetic of cbc_apply.
+ * CBC_PREC_FP64 : every contraction, Gram matrix, eigensolve, Cholesky and triangular
+ *                 solve in FP64 (the plain baseline).
+ * CBC_PREC_MIXED: the dense contractions and Gram products run on the tensor cores
+ *                 (tcgen05) with bf16 operand slices and FP32 partial sums that are
+ *                 combined in FP64; the eigensolve, Cholesky and triangular solves stay
+ *                 FP64.                                                             */
+enum cbc_prec { CBC_PREC_FP64 = 0, CBC_PREC_MIXED = 1 };
+
+typedef struct cbc_options {
+  int precision;     /* enum cbc_prec; default CBC_PREC_FP64                         */
+  int slices_fwd;    /* mixed: bf16 slices per operand in the first sweep(s) (0 = 5) */
+  int slices_bwd;    /* mixed: bf16 slices per operand in the last sweep (0 = 4)     */
+  int reserved_i;
+  double eps_rank;   /* singular values s_j <= eps_rank * s_0 are dropped (<=0: 1e-6) */
+  double reserved_d[3];
+} cbc_options;
+
+/* Create a TTNS from node tensors.
+ *   n_nodes   >= 1
+ *   parent    [n_nodes] host array, -1 at the root, must describe one tree
+ *   phys_dim  [n_nodes] host array, >= 1
+ *   bond_dim  [n_nodes] host array, >= 1 (entry of the root ignored)
+ *   dtype     enum cbc_dtype of node_data
+ *   node_data [n_nodes] host array of pointers, each to one node tensor in the leg order
+ *             above; host memory if data_on_device == 0, device memory otherwise.
+ *             Tensors are copied: the caller keeps ownership and may free them after
+ *             the call returns (it synchronises the stream when data is on the host).
+ *   cuda_stream  cudaStream_t used by this handle and by cbc_apply on it (may be NULL)
+ *   out       receives the new handle (owned by the caller, free with ttn_destroy)
+ * Errors: CBC_ERR_INVALID_ARG, CBC_ERR_OOM, CBC_ERR_CUDA.                           */
+int ttn_create(int n_nodes, const int32_t* parent, const int64_t* phys_dim,
+               const int64_t* bond_dim, int dtype, const void* const* node_data,
+               int data_on_device, void* cuda_stream, ttn_t* out);
+
+/* Create a TTNO; same arguments as ttn_create with the operator leg order.  bond_dim
+ * are the operator bonds (independent of the state's).                              */
+int ttno_create(int n_nodes, const int32_t* parent, const int64_t* phys_dim,
+                const int64_t* bond_dim, int dtype, const void* const* node_data,
+                int data_on_device, void* cuda_stream, ttno_t* out);
+
+/* Apply op to state and compress (Sec. III A for chains, Sec. III B for trees).
+ *   max_bond  > 0: cap on every output bond; <= 0: no cap
+ *   tol       > 0: keep the smallest rank whose discarded relative weight per cut
+ *             sum_{j>=k} s_j^2 <= tol^2 sum_j s_j^2 (Sec. V adaptive bond); <= 0: off
+ *   opt       NULL for defaults
+ *   out       receives a new TTNS handle on the state's stream: non-root nodes are
+ *             isometries toward the root (the Q^[i] of Eqs. (tt_cbc_qr_decomp),
+ *             (cbc_tree_qr)); the root holds S^[root] divided by exp(log_norm)
+ *             (ttn_get_info), so |psi'> = exp(log_norm) * network.
+ * The call is stream ordered; it synchronises the stream once per compressed bond to
+ * read the rank chosen on the device.  State and op are not modified.
+ * Errors: CBC_ERR_INVALID_ARG, CBC_ERR_TOPOLOGY_MISMATCH, CBC_ERR_OOM,
+ * CBC_ERR_NOT_POSITIVE_DEFINITE, CBC_ERR_NUMERICAL, CBC_ERR_TIMEOUT, CBC_ERR_CUDA,
+ * CBC_ERR_UNSUPPORTED.  On error *out is left NULL and nothing leaks.               */
+int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
+              const cbc_options* opt, ttn_t* out);
+
+/* Information about a TTNS (synchronises its stream).
+ *   n_nodes_out     may be NULL
+ *   bond_dims_out   NULL or [n_nodes]: bond of each node to its parent (1 at the root)
+ *   log_norm_out    NULL or scalar: the network is scaled by exp(*log_norm_out)      */
+int ttn_get_info(ttn_t t, int32_t* n_nodes_out, int64_t* bond_dims_out,
+                 double* log_norm_out);
+
+/* Copy one node tensor out (synchronises the stream).
+ *   dst   host (dst_on_device == 0) or device pointer with room for the node tensor
+ *         in the leg order above, element type `dtype` (CBC_F64 or CBC_C128 for a
+ *         complex network; CBC_F64 for a real one; lower precisions are rounded).   */
+int ttn_get_node(ttn_t t, int node, void* dst, int dst_on_device, int dtype);
+
+int ttn_destroy(ttn_t t);   /* NULL is a no-op */
+int ttno_destroy(ttno_t t); /* NULL is a no-op */
+
+/* Launch statistics per kernel class, process wide, for benchmarks and profiling.
+ * Launch counts are always kept.  With timing enabled, every group of launches of one
+ * class is bracketed by CUDA events on the stream it runs on; cbc_stats_read then waits
+ * for those events and sums their elapsed times.  flops are the algorithmic floating
+ * point operations of the launches (8 per complex multiply-add, 2 per real one; a
+ * Gram matrix counts only its Hermitian half).  Not thread safe across concurrent
+ * cbc_apply calls.                                                                  */
+enum cbc_kclass {
+  CBC_K_GEMM_F64 = 0, /* FP64 SIMT contractions and Gram products                     */
+  CBC_K_GEMM_TC = 1,  /* tcgen05 split-precision contractions and Gram products        */
+  CBC_K_EIG = 2,      /* Hermitian eigensolver of the truncation                      */
+  CBC_K_CHOLQR = 3,   /* Cholesky and triangular solves of CholeskyQR2                */
+  CBC_K_AUX = 4,      /* normalisation, identity, operand slicing, conversions        */
+  CBC_K_COUNT = 8
+};
+typedef struct cbc_stats {
+  int64_t launches[CBC_K_COUNT];
+  int64_t groups[CBC_K_COUNT];
+  double ms[CBC_K_COUNT];
+  double flops[CBC_K_COUNT];
+} cbc_stats;
+int cbc_stats_enable(int timing); /* 1: time launch groups with CUDA events, 0: off  */
+int cbc_stats_reset(void);
+int cbc_stats_read(cbc_stats* out); /* synchronises the recorded events              */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* cbc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBC_H_ */

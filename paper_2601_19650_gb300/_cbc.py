@@ -1,0 +1,220 @@
+"""ctypes binding of ``include/cbc.h`` (argument marshalling only).
+
+Every function keeps the C name and forwards to ``libcbc.so``; all arithmetic runs in
+the library's CUDA kernels.  The library must have been built (``build.build()``); if
+it is missing the first call raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcbc.so")
+
+CBC_F32, CBC_F64, CBC_C64, CBC_C128 = 0, 1, 2, 3
+CBC_PREC_FP64, CBC_PREC_MIXED = 0, 1
+STATUS_NAMES = {
+    0: "CBC_OK", 1: "CBC_ERR_INVALID_ARG", 2: "CBC_ERR_TOPOLOGY_MISMATCH", 3: "CBC_ERR_OOM",
+    4: "CBC_ERR_NOT_POSITIVE_DEFINITE", 5: "CBC_ERR_NUMERICAL", 6: "CBC_ERR_TIMEOUT",
+    7: "CBC_ERR_CUDA", 8: "CBC_ERR_UNSUPPORTED",
+}
+
+_DT_OF = {np.dtype(np.float32): CBC_F32, np.dtype(np.float64): CBC_F64,
+          np.dtype(np.complex64): CBC_C64, np.dtype(np.complex128): CBC_C128}
+
+
+class CBCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class cbc_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("slices_fwd", ctypes.c_int),
+                ("slices_bwd", ctypes.c_int), ("reserved_i", ctypes.c_int),
+                ("eps_rank", ctypes.c_double), ("reserved_d", ctypes.c_double * 3)]
+
+
+class cbc_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("groups", ctypes.c_int64 * 8),
+                ("ms", ctypes.c_double * 8), ("flops", ctypes.c_double * 8)]
+
+
+KCLASS = {0: "gemm_f64", 1: "gemm_tc", 2: "eig", 3: "cholqr", 4: "aux"}
+
+_lib = None
+
+
+def lib():
+    """Load libcbc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2601_19650_gb300.build` (no CPU fallback exists)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        P = ctypes.POINTER
+        create_args = [ctypes.c_int, P(i32), P(i64), P(i64), ctypes.c_int, P(vp), ctypes.c_int,
+                       vp, P(vp)]
+        L.ttn_create.argtypes = create_args
+        L.ttno_create.argtypes = create_args
+        L.cbc_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
+        L.ttn_get_info.argtypes = [vp, P(i32), P(i64), P(dbl)]
+        L.ttn_get_node.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
+        L.ttn_destroy.argtypes = [vp]
+        L.ttno_destroy.argtypes = [vp]
+        L.cbc_stats_enable.argtypes = [ctypes.c_int]
+        L.cbc_stats_reset.argtypes = []
+        L.cbc_stats_read.argtypes = [P(cbc_stats)]
+        for f in ("cbc_stats_enable", "cbc_stats_reset", "cbc_stats_read"):
+            getattr(L, f).restype = ctypes.c_int
+        L.cbc_last_error.restype = ctypes.c_char_p
+        L.cbc_last_error.argtypes = []
+        for f in ("ttn_create", "ttno_create", "cbc_apply", "ttn_get_info", "ttn_get_node",
+                  "ttn_destroy", "ttno_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def cbc_stats_enable(timing: bool):
+    _check(lib().cbc_stats_enable(1 if timing else 0))
+
+
+def cbc_stats_reset():
+    _check(lib().cbc_stats_reset())
+
+
+def cbc_stats_read() -> dict:
+    st = cbc_stats()
+    _check(lib().cbc_stats_read(ctypes.byref(st)))
+    return {name: {"launches": int(st.launches[k]), "groups": int(st.groups[k]),
+                   "ms": float(st.ms[k]), "flops": float(st.flops[k])}
+            for k, name in KCLASS.items()}
+
+
+def cbc_last_error() -> str:
+    return lib().cbc_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise CBCError(rc, cbc_last_error())
+
+
+def _create(fn, parent, phys, bond, dtype: int, ptrs: Sequence[int], on_device: bool,
+            stream: Optional[int]):
+    n = len(parent)
+    par = (ctypes.c_int32 * n)(*[int(x) for x in parent])
+    ph = (ctypes.c_int64 * n)(*[int(x) for x in phys])
+    bd = (ctypes.c_int64 * n)(*[int(x) for x in bond])
+    arr = (ctypes.c_void_p * n)(*[ctypes.c_void_p(int(p)) for p in ptrs])
+    out = ctypes.c_void_p()
+    _check(fn(n, par, ph, bd, dtype, arr, 1 if on_device else 0,
+              ctypes.c_void_p(stream or 0), ctypes.byref(out)))
+    return out
+
+
+def ttn_create(parent, phys, bond, dtype: int, ptrs, on_device: bool, stream=None):
+    return _create(lib().ttn_create, parent, phys, bond, dtype, ptrs, on_device, stream)
+
+
+def ttno_create(parent, phys, bond, dtype: int, ptrs, on_device: bool, stream=None):
+    return _create(lib().ttno_create, parent, phys, bond, dtype, ptrs, on_device, stream)
+
+
+def make_options(precision: int = CBC_PREC_FP64, eps_rank: float = 0.0, slices_fwd: int = 0,
+                 slices_bwd: int = 0) -> cbc_options:
+    o = cbc_options()
+    o.precision = precision
+    o.eps_rank = eps_rank
+    o.slices_fwd = slices_fwd
+    o.slices_bwd = slices_bwd
+    return o
+
+
+def cbc_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options] = None):
+    out = ctypes.c_void_p()
+    _check(lib().cbc_apply(state, op, int(max_bond), float(tol),
+                           ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
+    return out
+
+
+def ttn_get_info(t):
+    n = ctypes.c_int32()
+    _check(lib().ttn_get_info(t, ctypes.byref(n), None, None))
+    bonds = (ctypes.c_int64 * n.value)()
+    ln = ctypes.c_double()
+    _check(lib().ttn_get_info(t, None, bonds, ctypes.byref(ln)))
+    return n.value, np.array(bonds[:], dtype=np.int64), ln.value
+
+
+def ttn_get_node(t, node: int, dst_ptr: int, dst_on_device: bool, dtype: int):
+    _check(lib().ttn_get_node(t, int(node), ctypes.c_void_p(int(dst_ptr)),
+                              1 if dst_on_device else 0, int(dtype)))
+
+
+def ttn_destroy(t):
+    _check(lib().ttn_destroy(t))
+
+
+def ttno_destroy(t):
+    _check(lib().ttno_destroy(t))
+
+
+# ----------------------------------------------------------------------------------------
+# convenience: whole networks in and out (still marshalling only)
+# ----------------------------------------------------------------------------------------
+
+def _host_ptrs(tensors):
+    arrs = [np.ascontiguousarray(t) for t in tensors]
+    return arrs, [a.ctypes.data for a in arrs]
+
+
+def create_from_host(parent, phys, bond, tensors, kind: str = "state", stream=None):
+    """Create a handle from host numpy tensors (canonical leg layout)."""
+    arrs, ptrs = _host_ptrs(tensors)
+    dt = _DT_OF[arrs[0].dtype]
+    fn = ttn_create if kind == "state" else ttno_create
+    return fn(parent, phys, bond, dt, ptrs, False, stream)
+
+
+def create_from_device(parent, phys, bond, tensors, kind: str = "state", stream=None):
+    """Create a handle from CUDA torch tensors (canonical leg layout, contiguous)."""
+    import torch  # noqa: F401  (device memory comes from torch)
+    dmap = {"torch.float32": CBC_F32, "torch.float64": CBC_F64,
+            "torch.complex64": CBC_C64, "torch.complex128": CBC_C128}
+    dt = dmap[str(tensors[0].dtype)]
+    ptrs = [t.data_ptr() for t in tensors]
+    fn = ttn_create if kind == "state" else ttno_create
+    return fn(parent, phys, bond, dt, ptrs, True, stream)
+
+
+def fetch_network(t, shapes_of_node, cplx: bool):
+    """Copy every node of a TTNS handle to host (FP64 / complex128) -> (tensors, bonds, log_norm)."""
+    n, bonds, log_norm = ttn_get_info(t)
+    out = []
+    for i in range(n):
+        shape = shapes_of_node(i, bonds)
+        a = np.empty(shape, dtype=np.complex128 if cplx else np.float64)
+        ttn_get_node(t, i, a.ctypes.data, False, CBC_C128 if cplx else CBC_F64)
+        out.append(a)
+    return out, bonds, log_norm
+
+
+def output_shape_fn(parent, phys):
+    """Shape of node i of an output TTNS given the output bonds (canonical layout)."""
+    n = len(parent)
+    ch = [[] for _ in range(n)]
+    for j, p in enumerate(parent):
+        if p >= 0:
+            ch[int(p)].append(j)
+
+    def shape(i, bonds):
+        return (int(bonds[i]), int(phys[i])) + tuple(int(bonds[c]) for c in ch[i])
+    return shape

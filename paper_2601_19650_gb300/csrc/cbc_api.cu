@@ -1,0 +1,272 @@
+// C ABI of the CBC library: handles, validation, and the sweep planners that issue
+// the kernels of Sec. III A (tensor train) and Sec. III B (trees).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "planner.h"
+
+using namespace cbc;
+
+// ----------------------------------------------------------------------------------
+// error reporting
+// ----------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+int cbc::fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cbc::cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(CBC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(CBC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int cbc::num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+// ----------------------------------------------------------------------------------
+// networks
+// ----------------------------------------------------------------------------------
+static bool valid_dtype(int dt) { return dt == CBC_F32 || dt == CBC_F64 || dt == CBC_C64 || dt == CBC_C128; }
+static size_t dtype_bytes(int dt) {
+  switch (dt) {
+    case CBC_F32: return 4;
+    case CBC_F64: return 8;
+    case CBC_C64: return 8;
+    default: return 16;
+  }
+}
+
+static int build_network(Net* net, int kind, int n_nodes, const int32_t* parent,
+                         const int64_t* phys_dim, const int64_t* bond_dim, int dtype,
+                         const void* const* node_data, int data_on_device, void* stream) {
+  if (n_nodes < 1 || !parent || !phys_dim || !bond_dim || !node_data)
+    return fail(CBC_ERR_INVALID_ARG, "create: null argument or n_nodes < 1");
+  if (!valid_dtype(dtype)) return fail(CBC_ERR_INVALID_ARG, "create: bad dtype %d", dtype);
+  net->kind = kind;
+  net->n = n_nodes;
+  net->parent.assign(parent, parent + n_nodes);
+  net->phys.assign(phys_dim, phys_dim + n_nodes);
+  net->bond.assign(bond_dim, bond_dim + n_nodes);
+  net->stream = static_cast<cudaStream_t>(stream);
+  net->cplx = (dtype == CBC_C64 || dtype == CBC_C128);
+  int roots = 0;
+  for (int i = 0; i < n_nodes; ++i) {
+    if (parent[i] < -1 || parent[i] >= n_nodes || parent[i] == i)
+      return fail(CBC_ERR_INVALID_ARG, "create: parent[%d] = %d invalid", i, parent[i]);
+    if (parent[i] < 0) {
+      roots++;
+      net->root = i;
+      net->bond[i] = 1;
+    }
+    if (phys_dim[i] < 1 || bond_dim[i] < 1)
+      return fail(CBC_ERR_INVALID_ARG, "create: node %d has a dimension < 1", i);
+    if (!node_data[i]) return fail(CBC_ERR_INVALID_ARG, "create: node_data[%d] is NULL", i);
+  }
+  if (roots != 1) return fail(CBC_ERR_INVALID_ARG, "create: %d roots (need exactly 1)", roots);
+  for (int i = 0; i < n_nodes; ++i) {  // every node reaches the root
+    int v = i, steps = 0;
+    while (parent[v] >= 0 && steps <= n_nodes) {
+      v = parent[v];
+      ++steps;
+    }
+    if (steps > n_nodes) return fail(CBC_ERR_INVALID_ARG, "create: parent array has a cycle");
+  }
+  net->children.assign(n_nodes, {});
+  for (int i = 0; i < n_nodes; ++i)
+    if (parent[i] >= 0) net->children[parent[i]].push_back(i);
+  net->data.assign(n_nodes, nullptr);
+  net->numel.assign(n_nodes, 0);
+  cudaStream_t s = net->stream;
+  const size_t es = net->elem_bytes();
+  for (int i = 0; i < n_nodes; ++i) {
+    int64_t ne = net->bond[i] * net->phys[i] * (kind == 1 ? net->phys[i] : 1);
+    for (int c : net->children[i]) ne *= net->bond[c];
+    net->numel[i] = ne;
+    cudaError_t e = cudaMallocAsync(&net->data[i], ne * es, s);
+    if (e != cudaSuccess) return cuda_fail(e, "create: device allocation");
+    const void* src = node_data[i];
+    void* staging = nullptr;
+    if (!data_on_device) {
+      e = cudaMallocAsync(&staging, ne * dtype_bytes(dtype), s);
+      if (e != cudaSuccess) return cuda_fail(e, "create: staging alloc");
+      e = cudaMemcpyAsync(staging, src, ne * dtype_bytes(dtype), cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(e, "create: H2D copy");
+      src = staging;
+    }
+    e = widen_to_f64(src, dtype, net->data[i], ne, s);
+    if (e != cudaSuccess) return cuda_fail(e, "create: widen");
+    if (staging) cudaFreeAsync(staging, s);
+  }
+  if (!data_on_device) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "create: synchronize");
+  }
+  return CBC_OK;
+}
+
+// node tensors are stream-ordered allocations on the network's stream
+Net::~Net() {
+  bool any = false;
+  for (void* p : data)
+    if (p) {
+      cudaFreeAsync(p, stream);
+      any = true;
+    }
+  if (any) cudaStreamSynchronize(stream);
+}
+
+struct cbc_ttn_s : Net {};
+struct cbc_ttno_s : Net {};
+
+extern "C" {
+
+int ttn_create(int n_nodes, const int32_t* parent, const int64_t* phys_dim,
+               const int64_t* bond_dim, int dtype, const void* const* node_data,
+               int data_on_device, void* cuda_stream, ttn_t* out) {
+  if (!out) return fail(CBC_ERR_INVALID_ARG, "ttn_create: out is NULL");
+  *out = nullptr;
+  auto* h = new cbc_ttn_s();
+  int rc = build_network(h, 0, n_nodes, parent, phys_dim, bond_dim, dtype, node_data,
+                         data_on_device, cuda_stream);
+  if (rc != CBC_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return CBC_OK;
+}
+
+int ttno_create(int n_nodes, const int32_t* parent, const int64_t* phys_dim,
+                const int64_t* bond_dim, int dtype, const void* const* node_data,
+                int data_on_device, void* cuda_stream, ttno_t* out) {
+  if (!out) return fail(CBC_ERR_INVALID_ARG, "ttno_create: out is NULL");
+  *out = nullptr;
+  auto* h = new cbc_ttno_s();
+  int rc = build_network(h, 1, n_nodes, parent, phys_dim, bond_dim, dtype, node_data,
+                         data_on_device, cuda_stream);
+  if (rc != CBC_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return CBC_OK;
+}
+
+int ttn_destroy(ttn_t t) {
+  if (t) {
+    cudaStreamSynchronize(t->stream);
+    delete t;
+  }
+  return CBC_OK;
+}
+
+int ttno_destroy(ttno_t t) {
+  if (t) {
+    cudaStreamSynchronize(t->stream);
+    delete t;
+  }
+  return CBC_OK;
+}
+
+const char* cbc_last_error(void) { return g_last_error.c_str(); }
+
+int ttn_get_info(ttn_t t, int32_t* n_nodes_out, int64_t* bond_dims_out, double* log_norm_out) {
+  if (!t) return fail(CBC_ERR_INVALID_ARG, "ttn_get_info: NULL handle");
+  cudaError_t e = cudaStreamSynchronize(t->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "ttn_get_info");
+  if (n_nodes_out) *n_nodes_out = t->n;
+  if (bond_dims_out)
+    for (int i = 0; i < t->n; ++i) bond_dims_out[i] = t->bond[i];
+  if (log_norm_out) *log_norm_out = t->log_norm;
+  return CBC_OK;
+}
+
+int ttn_get_node(ttn_t t, int node, void* dst, int dst_on_device, int dtype) {
+  if (!t || !dst) return fail(CBC_ERR_INVALID_ARG, "ttn_get_node: NULL argument");
+  if (node < 0 || node >= t->n) return fail(CBC_ERR_INVALID_ARG, "ttn_get_node: node %d out of range", node);
+  if (!valid_dtype(dtype)) return fail(CBC_ERR_INVALID_ARG, "ttn_get_node: bad dtype");
+  bool want_c = (dtype == CBC_C64 || dtype == CBC_C128);
+  if (want_c != t->cplx)
+    return fail(CBC_ERR_INVALID_ARG, "ttn_get_node: dtype must be %s for this network",
+                t->cplx ? "complex" : "real");
+  cudaStream_t s = t->stream;
+  int64_t ne = t->numel[node];
+  size_t bytes = ne * dtype_bytes(dtype);
+  cudaError_t e;
+  if (dtype == CBC_F64 || dtype == CBC_C128) {
+    e = cudaMemcpyAsync(dst, t->data[node], bytes,
+                        dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ttn_get_node: copy");
+  } else {
+    void* tmp = dst;
+    if (!dst_on_device) {
+      e = cudaMallocAsync(&tmp, bytes, s);
+      if (e != cudaSuccess) return cuda_fail(e, "ttn_get_node: alloc");
+    }
+    e = narrow_from_f64(t->data[node], t->cplx, tmp, dtype, ne, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ttn_get_node: narrow");
+    if (!dst_on_device) {
+      e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_fail(e, "ttn_get_node: copy");
+      cudaFreeAsync(tmp, s);
+    }
+  }
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "ttn_get_node: synchronize");
+  return CBC_OK;
+}
+
+int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_options* opt,
+              ttn_t* out) {
+  if (!out) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: out is NULL");
+  *out = nullptr;
+  if (!state || !op) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: NULL network");
+  if (state->kind != 0 || op->kind != 1) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: wrong handle kinds");
+  if (state->n != op->n || state->parent != op->parent || state->phys != op->phys)
+    return fail(CBC_ERR_TOPOLOGY_MISMATCH, "cbc_apply: state and operator trees differ");
+  if (!std::isfinite(tol)) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: tol is not finite");
+  Options o;
+  if (opt) {
+    o.precision = opt->precision;
+    if (opt->eps_rank > 0) o.eps_rank = opt->eps_rank;
+    if (opt->slices_fwd > 0) o.slices_fwd = opt->slices_fwd;
+    if (opt->slices_bwd > 0) o.slices_bwd = opt->slices_bwd;
+  }
+  if (o.precision != CBC_PREC_FP64 && o.precision != CBC_PREC_MIXED)
+    return fail(CBC_ERR_INVALID_ARG, "cbc_apply: bad precision %d", o.precision);
+  auto* res = new cbc_ttn_s();
+  int rc = run_cbc(*state, *op, max_bond, tol, o, res);
+  if (rc != CBC_OK) {
+    delete res;
+    return rc;
+  }
+  *out = res;
+  return CBC_OK;
+}
+
+}  // extern "C"

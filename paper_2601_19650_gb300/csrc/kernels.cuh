@@ -1,0 +1,106 @@
+// Internal launch interface of the CBC kernels (host side).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace cbc {
+
+// A matrix view over strided memory.  Element (r, c) of batch b lives at
+//   base + b*bs + (r / r_in)*rs_out + (r % r_in)*rs_in + (c / c_in)*cs_out + (c % c_in)*cs_in
+// so a row or column index may itself be a pair of tensor legs with unrelated strides
+// (a leg permutation of a node tensor is a view, never a copy).
+struct View {
+  int32_t r_in = 0x7fffffff;
+  int64_t rs_out = 0, rs_in = 0;
+  int32_t c_in = 0x7fffffff;
+  int64_t cs_out = 0, cs_in = 0;
+  int64_t bs = 0;
+
+  static View rowmajor(int64_t ld, int64_t bs = 0) {
+    View v;
+    v.rs_in = ld;
+    v.cs_in = 1;
+    v.bs = bs;
+    return v;
+  }
+  // the transpose of a row-major matrix with leading dimension ld
+  static View transposed(int64_t ld, int64_t bs = 0) {
+    View v;
+    v.rs_in = 1;
+    v.cs_in = ld;
+    v.bs = bs;
+    return v;
+  }
+  View& rows2(int32_t inner, int64_t s_out, int64_t s_in) {
+    r_in = inner;
+    rs_out = s_out;
+    rs_in = s_in;
+    return *this;
+  }
+  View& cols2(int32_t inner, int64_t s_out, int64_t s_in) {
+    c_in = inner;
+    cs_out = s_out;
+    cs_in = s_in;
+    return *this;
+  }
+  __host__ __device__ __forceinline__ int64_t roff(int32_t r) const {
+    return (int64_t)(r / r_in) * rs_out + (int64_t)(r % r_in) * rs_in;
+  }
+  __host__ __device__ __forceinline__ int64_t coff(int32_t c) const {
+    return (int64_t)(c / c_in) * cs_out + (int64_t)(c % c_in) * cs_in;
+  }
+};
+
+// C = op(A) op(B), C: M x N, A: M x K, B: K x N, `batch` independent products.
+// conjA / conjB take the complex conjugate of the operand elements (no transpose:
+// transposes are views).  FP64 SIMT, FP64 accumulation; split over K when the output
+// alone cannot fill the GPU.
+template <typename T>
+cudaError_t gemm_f64(int M, int N, int K, int batch, const T* A, const View& va, bool conjA,
+                     const T* B, const View& vb, bool conjB, T* C, const View& vc,
+                     cudaStream_t s);
+
+// ---- Hermitian eigensolver (FP64): A (m x m, row-major, overwritten) -----------------
+// Finds the eigenvalues in descending order and the eigenvectors of the `k` largest,
+// where k follows the rank rule of cbc_apply: k = min(max_bond (if > 0), #{lambda_j >
+// floor * lambda_0}, smallest k with sum_{j>=k} lambda_j <= tol^2 sum_j lambda_j (if tol
+// > 0)), at least 1.  Outputs: lam[m], U (m x kmax, row-major, column j = eigenvector j),
+// *k_dev.  Workspace: eig_workspace_bytes(m, kmax).
+struct EigWork;
+size_t eig_workspace_bytes(int m, int kmax, bool cplx);
+template <typename T>
+cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double floor_rel,
+                     double* lam, T* U, int* k_dev, void* work, int* status, int num_sms,
+                     cudaStream_t s);
+
+// ---- Cholesky QR (FP64) ------------------------------------------------------------
+// Q = C^{-1} S with G = S S^H = C C^H, S: m x n (m <= n), row-major, in place on S.
+template <typename T>
+cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cudaStream_t s);
+template <typename T>
+cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* bar,
+                            int num_sms, cudaStream_t s);
+
+// ---- small helpers ------------------------------------------------------------------
+// x[i] (i < n) scaled in place to unit Frobenius norm; log of the old norm added to
+// *log_acc; non-finite norm sets CBC_ERR_NUMERICAL.
+template <typename T>
+cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, double* scratch,
+                              cudaStream_t s);
+// L[r, c] = sqrt(lam[r]) * conj(V[c, r]) for r < k (V: n x ldv row-major), L: k x n
+template <typename T>
+cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_dev, int n,
+                           T* L, cudaStream_t s);
+// dst (n_elem) = identity rows r < n of an n x n matrix
+template <typename T>
+cudaError_t fill_identity(T* dst, int n, cudaStream_t s);
+// widen an input tensor to FP64 storage
+cudaError_t widen_to_f64(const void* src, int src_dtype, void* dst, int64_t n_elem,
+                         cudaStream_t s);
+// narrow FP64 storage to the requested dtype
+cudaError_t narrow_from_f64(const void* src, bool cplx, void* dst, int dst_dtype,
+                            int64_t n_elem, cudaStream_t s);
+
+}  // namespace cbc

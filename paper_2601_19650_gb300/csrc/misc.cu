@@ -1,0 +1,147 @@
+// Small element-wise kernels of the CBC pipeline: dtype widening / narrowing, the
+// per-step renormalisation with a running log scale, the m > n truncation factor
+// diag(sqrt(lambda)) V^H, and identity fill for the trivial LQ case.
+#include <algorithm>
+
+#include "kernels.cuh"
+#include "planner.h"
+
+namespace cbc {
+namespace {
+
+template <typename T>
+__global__ void sumsq_kernel(const T* x, int64_t n, double* out) {
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += ops<T>::abs2(x[i]);
+  s = warp_sum(s);
+  __shared__ double sh[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = s;
+  __syncthreads();
+  if (w == 0) {
+    s = (lane < (blockDim.x >> 5)) ? sh[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) atomicAdd(out, s);
+  }
+}
+
+template <typename T>
+__global__ void scale_kernel(T* x, int64_t n, const double* sumsq, double* log_acc, int* status) {
+  double ss = *sumsq;
+  bool ok = isfinite(ss) && ss > 0.0;
+  if (!ok) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(ss)) set_status(status, CBC_ERR_NUMERICAL);
+    return;
+  }
+  double inv = rsqrt(ss);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *log_acc += 0.5 * log(ss);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = ops<T>::scale(inv, x[i]);
+}
+
+template <typename T>
+__global__ void scaled_adjoint_kernel(const T* V, int ldv, const double* lam, const int* k_dev,
+                                      int n, T* L) {
+  int k = *k_dev;
+  int64_t total = (int64_t)k * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(t / n), c = (int)(t % n);
+    double sl = sqrt(fmax(lam[r], 0.0));
+    L[t] = ops<T>::scale(sl, ops<T>::conj(V[(int64_t)c * ldv + r]));
+  }
+}
+
+template <typename T>
+__global__ void identity_kernel(T* dst, int n) {
+  int64_t total = (int64_t)n * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int r = (int)(t / n), c = (int)(t % n);
+    dst[t] = (r == c) ? ops<T>::one() : ops<T>::zero();
+  }
+}
+
+__global__ void widen_kernel(const void* src, int dt, double* dst, int64_t n_scalar) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_scalar;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    if (dt == CBC_F32 || dt == CBC_C64)
+      v = (double)static_cast<const float*>(src)[i];
+    else
+      v = static_cast<const double*>(src)[i];
+    dst[i] = v;
+  }
+}
+
+__global__ void narrow_kernel(const double* src, void* dst, int dt, int64_t n_scalar) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_scalar;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (dt == CBC_F32 || dt == CBC_C64)
+      static_cast<float*>(dst)[i] = (float)src[i];
+    else
+      static_cast<double*>(dst)[i] = src[i];
+  }
+}
+
+int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + 255) / 256)); }
+
+}  // namespace
+
+template <typename T>
+cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, double* scratch,
+                              cudaStream_t s) {
+  cudaError_t err = cudaMemsetAsync(scratch, 0, sizeof(double), s);
+  if (err != cudaSuccess) return err;
+  int g = std::min(grid_for(n), 1024);
+  note_launches(CBC_K_AUX, 2);
+  sumsq_kernel<T><<<g, 256, 0, s>>>(x, n, scratch);
+  scale_kernel<T><<<g, 256, 0, s>>>(x, n, scratch, log_acc, status);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_dev, int n, T* L,
+                           cudaStream_t s) {
+  note_launches(CBC_K_AUX, 1);
+  scaled_adjoint_kernel<T><<<grid_for((int64_t)ldv * n), 256, 0, s>>>(V, ldv, lam, k_dev, n, L);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t fill_identity(T* dst, int n, cudaStream_t s) {
+  note_launches(CBC_K_AUX, 1);
+  identity_kernel<T><<<grid_for((int64_t)n * n), 256, 0, s>>>(dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t widen_to_f64(const void* src, int src_dtype, void* dst, int64_t n_elem,
+                         cudaStream_t s) {
+  int64_t ns = n_elem * ((src_dtype == CBC_C64 || src_dtype == CBC_C128) ? 2 : 1);
+  note_launches(CBC_K_AUX, 1);
+  widen_kernel<<<grid_for(ns), 256, 0, s>>>(src, src_dtype, static_cast<double*>(dst), ns);
+  return cudaGetLastError();
+}
+
+cudaError_t narrow_from_f64(const void* src, bool cplx, void* dst, int dst_dtype, int64_t n_elem,
+                            cudaStream_t s) {
+  int64_t ns = n_elem * (cplx ? 2 : 1);
+  note_launches(CBC_K_AUX, 1);
+  narrow_kernel<<<grid_for(ns), 256, 0, s>>>(static_cast<const double*>(src), dst, dst_dtype, ns);
+  return cudaGetLastError();
+}
+
+template cudaError_t normalize_inplace<double>(double*, int64_t, double*, int*, double*,
+                                               cudaStream_t);
+template cudaError_t normalize_inplace<zdbl>(zdbl*, int64_t, double*, int*, double*, cudaStream_t);
+template cudaError_t scaled_adjoint<double>(const double*, int, const double*, const int*, int,
+                                            double*, cudaStream_t);
+template cudaError_t scaled_adjoint<zdbl>(const zdbl*, int, const double*, const int*, int, zdbl*,
+                                          cudaStream_t);
+template cudaError_t fill_identity<double>(double*, int, cudaStream_t);
+template cudaError_t fill_identity<zdbl>(zdbl*, int, cudaStream_t);
+
+}  // namespace cbc

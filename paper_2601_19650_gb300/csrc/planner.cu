@@ -1,0 +1,318 @@
+// Sweep planners: they turn one cbc_apply into the sequence of kernel launches of
+// Sec. III A (tensor train) and Sec. III B (trees).  All arithmetic runs in the
+// kernels; the host only sizes buffers, picks leg views and reads back the rank chosen
+// on the device after each compression.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+#include "planner.h"
+
+namespace cbc {
+namespace {
+
+// stream-ordered scratch that is released when the call ends
+struct Arena {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  cudaError_t err = cudaSuccess;
+  explicit Arena(cudaStream_t st) : s(st) {}
+  template <typename T>
+  T* get(size_t n) {
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(n * sizeof(T), 256);
+    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
+      if (err == cudaSuccess) err = e;
+      return nullptr;
+    }
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Arena() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+#define CK(expr)                                         \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #expr);  \
+  } while (0)
+
+#define CKA(ptr)                                                          \
+  do {                                                                    \
+    if (!(ptr)) return cuda_fail(ar.err, "workspace allocation " #ptr);   \
+  } while (0)
+
+int status_to_rc(int st) {
+  switch (st) {
+    case CBC_ERR_NOT_POSITIVE_DEFINITE:
+      return fail(st, "cbc_apply: Cholesky met a non-positive pivot (rank-deficient S)");
+    case CBC_ERR_NUMERICAL: return fail(st, "cbc_apply: NaN or Inf in an intermediate");
+    case CBC_ERR_TIMEOUT: return fail(st, "cbc_apply: a device-side wait timed out");
+    default: return fail(st, "cbc_apply: device status %d", st);
+  }
+}
+
+// device scalars of one call
+struct Scalars {
+  int* status;
+  int* k;
+  double* log_fwd;
+  double* log_out;
+  double* scratch;
+};
+
+template <typename T>
+T host_one() {
+  T v;
+  if constexpr (ops<T>::cplx)
+    v = zdbl{1.0, 0.0};
+  else
+    v = 1.0;
+  return v;
+}
+
+// FP64 GEMM with its launch group timed; `gram` halves the algorithmic flops
+template <typename T>
+cudaError_t tgemm(bool gram, int M, int N, int K, const T* A, const View& va, bool ca, const T* B,
+                  const View& vb, bool cb, T* C, const View& vc, cudaStream_t s) {
+  double fl = (ops<T>::cplx ? 8.0 : 2.0) * (double)M * N * K * (gram ? 0.5 : 1.0);
+  KTimer t(CBC_K_GEMM_F64, s, 0, fl);
+  return gemm_f64<T>(M, N, K, 1, A, va, ca, B, vb, cb, C, vc, s);
+}
+
+template <typename T>
+double eig_flops(int m, int k) {
+  return ops<T>::cplx ? (16.0 / 3.0) * m * (double)m * m + 8.0 * m * (double)m * k
+                      : (4.0 / 3.0) * m * (double)m * m + 2.0 * m * (double)m * k;
+}
+
+// read status and k after a compression
+int read_k(const Scalars& sc, cudaStream_t s, int* k) {
+  int h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, sc.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h[0] != 0) return status_to_rc(h[0]);
+  *k = h[1];
+  return CBC_OK;
+}
+
+// Compression of the row leg of M (m x n, row-major): writes the k x n factor whose
+// Gram reproduces the rank-k truncation of M^H M (Sec. III A, text after Eq.
+// (tt_cbc_first_contraction)), normalised, and returns k.
+template <typename T>
+int compress_rows(Arena& ar, const T* M, int m, int n, int64_t max_bond, double tol,
+                  const Options& o, const Scalars& sc, cudaStream_t s, T** Lout, int* kout) {
+  const int kmax = (int)((max_bond > 0) ? std::min<int64_t>(max_bond, std::min(m, n)) : std::min(m, n));
+  const double floor_rel = o.eps_rank * o.eps_rank;
+  const int g = std::min(m, n);
+  T* K = ar.get<T>((size_t)g * g);
+  double* lam = ar.get<double>(g);
+  T* U = ar.get<T>((size_t)g * kmax);
+  char* work = ar.get<char>(eig_workspace_bytes(g, kmax, ops<T>::cplx));
+  CKA(K); CKA(lam); CKA(U); CKA(work);
+  if (m <= n) {  // K = M M^H, eigenvectors = left singular vectors
+    CK(tgemm<T>(true, m, m, n, M, View::rowmajor(n), false, M, View::transposed(n), true, K,
+                   View::rowmajor(m), s));
+  } else {       // G = M^H M, eigenvectors = right singular vectors
+    CK(tgemm<T>(true, n, n, m, M, View::transposed(n), true, M, View::rowmajor(n), false, K,
+                   View::rowmajor(n), s));
+  }
+  {
+    KTimer t(CBC_K_EIG, s, 0, eig_flops<T>(g, kmax));
+    CK(heev_top<T>(K, g, kmax, max_bond, tol, floor_rel, lam, U, sc.k, work, sc.status, num_sms(), s));
+  }
+  int k = 0;
+  int rc = read_k(sc, s, &k);
+  if (rc != CBC_OK) return rc;
+  T* L = ar.get<T>((size_t)k * n);
+  CKA(L);
+  if (m <= n) {  // L = U_k^H M
+    CK(tgemm<T>(false, k, n, m, U, View::transposed(kmax), true, M, View::rowmajor(n), false, L,
+                   View::rowmajor(n), s));
+  } else {       // L = diag(sqrt(lambda_k)) V_k^H
+    CK(scaled_adjoint<T>(U, kmax, lam, sc.k, n, L, s));
+  }
+  CK(normalize_inplace<T>(L, (int64_t)k * n, sc.log_fwd, sc.status, sc.scratch, s));
+  *Lout = L;
+  *kout = k;
+  return CBC_OK;
+}
+
+// S (m x n, row-major) -> Q with orthonormal rows spanning the row space of S, in place
+// (CholeskyQR2; Eq. (tt_cbc_qr_decomp) is the LQ on chi_{i-1}).  Requires m <= n.
+template <typename T>
+int lq_rows_inplace(Arena& ar, T* S, int m, int n, const Scalars& sc, cudaStream_t s) {
+  T* G = ar.get<T>((size_t)m * m);
+  void* bar = ar.get<GridBarrier>(1);
+  CKA(G); CKA(bar);
+  for (int rep = 0; rep < 2; ++rep) {
+    CK(tgemm<T>(true, m, m, n, S, View::rowmajor(n), false, S, View::transposed(n), true, G,
+                   View::rowmajor(m), s));
+    KTimer t(CBC_K_CHOLQR, s, 0,
+             (ops<T>::cplx ? 4.0 : 1.0) * ((double)m * m * m / 3.0 + (double)m * m * n));
+    CK(cholesky_lower<T>(G, m, sc.status, bar, num_sms(), s));
+    CK(trsm_lower_left<T>(G, S, m, n, sc.status, bar, num_sms(), s));
+  }
+  return CBC_OK;
+}
+
+// ---- tensor train (Sec. III A) ---------------------------------------------------------
+template <typename T>
+int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
+           Net* out) {
+  cudaStream_t s = st.stream;
+  const int L = st.n;
+  Arena ar(s);
+  int* d_int = ar.get<int>(4);
+  double* d_dbl = ar.get<double>(4);
+  CKA(d_int); CKA(d_dbl);
+  CK(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(d_dbl, 0, 4 * sizeof(double), s));
+  Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + 1, d_dbl + 2};
+  auto sb = [&](int i) { return i < L ? (int)st.bond[i] : 1; };  // alpha_{i-1} (site i's parent leg)
+  auto ob = [&](int i) { return i < L ? (int)op.bond[i] : 1; };
+  const T one = host_one<T>();
+
+  // forward sweep: L^[0] = 1, Eq. (tt_cbc_first_contraction), compression of (chi, sigma')
+  std::vector<T*> env(L, nullptr);
+  std::vector<int> chi(L, 1);
+  env[0] = ar.get<T>(1);
+  CKA(env[0]);
+  CK(cudaMemcpyAsync(env[0], &one, sizeof(T), cudaMemcpyHostToDevice, s));
+  for (int i = 0; i < L - 1; ++i) {
+    const int c = chi[i], b = ob(i), a = sb(i), d = (int)st.phys[i], a2 = sb(i + 1), b2 = ob(i + 1);
+    const T* Ti = static_cast<const T*>(st.data[i]);
+    const T* Wi = static_cast<const T*>(op.data[i]);
+    // F1: X[(chi b), (sigma a')] = sum_a L[(chi b), a] T[a, (sigma a')]
+    T* X = ar.get<T>((size_t)c * b * d * a2);
+    CKA(X);
+    CK(tgemm<T>(false, c * b, d * a2, a, env[i], View::rowmajor(a), false, Ti, View::rowmajor(d * a2),
+                   false, X, View::rowmajor(d * a2), s));
+    // F2: L'[chi, sigma', b', a'] = sum_{b, sigma} X[chi, b, sigma, a'] W[b, sigma', sigma, b']
+    //     as C[(sigma' b'), (chi a')] = W[(sigma' b'), (b sigma)] X[(b sigma), (chi a')]
+    T* Lp = ar.get<T>((size_t)c * d * b2 * a2);
+    CKA(Lp);
+    View vw;
+    vw.rows2(b2, (int64_t)d * b2, 1).cols2(d, (int64_t)d * d * b2, b2);
+    View vx;
+    vx.rs_in = a2;
+    vx.cols2(a2, (int64_t)b * d * a2, 1);
+    View vl;
+    vl.rs_in = a2;
+    vl.cols2(a2, (int64_t)d * b2 * a2, 1);
+    CK(tgemm<T>(false, d * b2, c * a2, b * d, Wi, vw, false, X, vx, false, Lp, vl, s));
+    // F3: compress M[(chi sigma'), (b' a')]
+    int k = 0;
+    int rc = compress_rows<T>(ar, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k);
+    if (rc != CBC_OK) return rc;
+    chi[i + 1] = k;
+  }
+
+  // backward sweep: R^[L] = 1, Eqs. (right_sweep_init_contr), (tt_cbc_qr_decomp),
+  // (tt_cbc_final_contraction)
+  out->kind = 0;
+  out->n = L;
+  out->root = 0;
+  out->parent = st.parent;
+  out->phys = st.phys;
+  out->bond.assign(L, 1);
+  out->children = st.children;
+  out->cplx = st.cplx;
+  out->stream = s;
+  out->data.assign(L, nullptr);
+  out->numel.assign(L, 0);
+  T* R = ar.get<T>(1);
+  CKA(R);
+  CK(cudaMemcpyAsync(R, &one, sizeof(T), cudaMemcpyHostToDevice, s));
+  int chiR = 1;
+  for (int i = L - 1; i >= 0; --i) {
+    const int a_in = sb(i), b_in = ob(i), d = (int)st.phys[i], a_out = sb(i + 1), b_out = ob(i + 1);
+    const int cp = chiR, c = chi[i];
+    const T* Ti = static_cast<const T*>(st.data[i]);
+    const T* Wi = static_cast<const T*>(op.data[i]);
+    // B1: Y[(a sigma), (chi' b_out)] = sum_{a_out} T[(a sigma), a_out] R[(chi' b_out), a_out]
+    T* Y = ar.get<T>((size_t)a_in * d * cp * b_out);
+    CKA(Y);
+    CK(tgemm<T>(false, a_in * d, cp * b_out, a_out, Ti, View::rowmajor(a_out), false, R,
+                   View::transposed(a_out), false, Y, View::rowmajor(cp * b_out), s));
+    // B2: Z[b_in, a, sigma', chi'] = sum_{sigma, b_out} W[b_in, sigma', sigma, b_out] Y[a, sigma, chi', b_out]
+    //     as C[(b_in sigma'), (a chi')] = W[(b_in sigma'), (sigma b_out)] Y[(sigma b_out), (a chi')]
+    T* Z = ar.get<T>((size_t)b_in * a_in * d * cp);
+    CKA(Z);
+    View vy;
+    vy.rows2(b_out, (int64_t)cp * b_out, 1).cols2(cp, (int64_t)d * cp * b_out, b_out);
+    View vz;
+    vz.rows2(d, (int64_t)a_in * d * cp, cp).cols2(cp, (int64_t)d * cp, 1);
+    CK(tgemm<T>(false, b_in * d, a_in * cp, d * b_out, Wi, View::rowmajor(d * b_out), false, Y, vy,
+                   false, Z, vz, s));
+    // B3: S[chi, (sigma' chi')] = sum_{(b a)} L^[i-1][chi, (b a)] Z[(b a), (sigma' chi')]
+    const int n = d * cp;
+    const int m = c;
+    const int cn = (m <= n) ? m : n;
+    T* node = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&node), sizeof(T) * std::max<size_t>((size_t)cn * n, (size_t)m * n), s));
+    out->data[i] = node;
+    out->numel[i] = (int64_t)cn * n;
+    if (i == 0 || m <= n) {
+      CK(tgemm<T>(false, m, n, b_in * a_in, env[i], View::rowmajor(b_in * a_in), false, Z,
+                     View::rowmajor(n), false, node, View::rowmajor(n), s));
+    }
+    if (i == 0) {  // T'^[1] = S^[1]
+      CK(normalize_inplace<T>(node, (int64_t)n, sc.log_out, sc.status, sc.scratch, s));
+      out->bond[0] = 1;
+      break;
+    }
+    // B4: S = R Q on chi_{i-1}; Q^[i] is the new tensor
+    if (m <= n) {
+      int rc = lq_rows_inplace<T>(ar, node, m, n, sc, s);
+      if (rc != CBC_OK) return rc;
+    } else {  // more rows than columns: any unitary basis of the columns; take the identity
+      CK(fill_identity<T>(node, n, s));
+    }
+    // B5: R^[i-1][chi'', (b a)] = sum_{(sigma' chi')} conj(Q[chi'', (sigma' chi')]) Z[(b a), (sigma' chi')]
+    T* Rn = ar.get<T>((size_t)cn * b_in * a_in);
+    CKA(Rn);
+    CK(tgemm<T>(false, cn, b_in * a_in, n, node, View::rowmajor(n), true, Z, View::transposed(n),
+                   false, Rn, View::rowmajor(b_in * a_in), s));
+    CK(normalize_inplace<T>(Rn, (int64_t)cn * b_in * a_in, sc.log_out, sc.status, sc.scratch, s));
+    R = Rn;
+    chiR = cn;
+    out->bond[i] = cn;
+  }
+  int h[2];
+  double hl = 0.0;
+  CK(cudaMemcpyAsync(h, sc.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hl, sc.log_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h[0] != 0) return status_to_rc(h[0]);
+  out->log_norm = hl;
+  return CBC_OK;
+}
+
+bool is_chain(const Net& t) {
+  for (int i = 0; i < t.n; ++i)
+    if (t.parent[i] != i - 1) return false;
+  return true;
+}
+
+}  // namespace
+
+int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
+            Net* out) {
+  if (st.cplx != op.cplx)
+    return fail(CBC_ERR_UNSUPPORTED, "cbc_apply: state and operator must both be real or both complex");
+  if (o.precision != CBC_PREC_FP64)
+    return fail(CBC_ERR_UNSUPPORTED, "cbc_apply: this precision is not built yet");
+  if (!is_chain(st)) return fail(CBC_ERR_UNSUPPORTED, "cbc_apply: general trees are not built yet");
+  if (st.cplx) return run_tt<zdbl>(st, op, max_bond, tol, o, out);
+  return run_tt<double>(st, op, max_bond, tol, o, out);
+}
+
+}  // namespace cbc

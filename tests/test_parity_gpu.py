@@ -1,0 +1,83 @@
+"""CUDA path (through the C ABI) against the FP64 oracle and brute force.
+
+Bar (FP64 path): relative 2-norm distance between the output states <= 1e-10.  The
+distance is measured without densifying (oracle.metrics: direct-sum network + QR
+sweep), so it resolves differences far below the bar.
+"""
+import numpy as np
+import pytest
+
+from oracle import brute, cbc, metrics
+from synth import make_problem
+
+from gpu_helpers import run_gpu
+
+pytestmark = pytest.mark.gpu
+
+FP64_BAR = 1e-10
+
+
+def _compare(prob, bar=FP64_BAR, **kw):
+    got, bonds, log_norm = run_gpu(prob, **kw)
+    mb = kw.get("max_bond", prob.max_bond)
+    tol = kw.get("tol", prob.tol)
+    ref = cbc.cbc(prob.state.parent, prob.state.tensors, prob.op.tensors, mb, tol)
+    e = metrics.rel_err(prob.state.parent, got, ref.tensors, log_norm, 0.0)
+    assert list(bonds) == list(ref.out_bonds), (bonds, ref.out_bonds)
+    assert e <= bar, (prob.name, e)
+    # output non-root tensors are isometries
+    for i, t in enumerate(got):
+        if prob.state.parent[i] < 0:
+            continue
+        q = t.reshape(t.shape[0], -1)
+        assert np.abs(q @ q.conj().T - np.eye(q.shape[0])).max() < 1e-11
+    return e
+
+
+def test_cfg1_exact_against_brute_force():
+    p = make_problem(1, max_bond=16)
+    got, bonds, log_norm = run_gpu(p)
+    ex = brute.apply_dense(p.state.parent, p.state.tensors, p.op.tensors)
+    v = brute.dense_state(p.state.parent, got) * np.exp(log_norm)
+    assert np.linalg.norm(v - ex) <= 1e-12 * np.linalg.norm(ex)
+
+
+def test_cfg1_truncated():
+    _compare(make_problem(1))
+
+
+@pytest.mark.parametrize("L,chi,D,mb,seed", [
+    (2, 4, 2, 4, 0), (1, 1, 3, 4, 1), (3, 4, 3, 3, 2), (12, 16, 4, 16, 0), (12, 16, 4, 5, 3),
+    (20, 33, 5, 40, 4), (9, 8, 3, 0, 5)])
+def test_complex_chain_small(L, chi, D, mb, seed):
+    p = make_problem(2, L=L, chi=chi, D=D, max_bond=mb, seed=seed)
+    _compare(p)
+
+
+def test_real_chain_d3():
+    p = make_problem(2, L=10, chi=12, D=4, d=3, max_bond=9, dtype=np.float64, seed=6)
+    _compare(p)
+
+
+def test_tolerance_mode():
+    p = make_problem(2, L=10, chi=16, D=4, max_bond=0, seed=7)
+    _compare(p, max_bond=0, tol=3e-2)
+    _compare(p, max_bond=12, tol=1e-3)
+
+
+def test_cfg2_full_fp64():
+    """L=64, d=2, chi=128, D=16, max_bond=128, complex64 inputs: the bench workload."""
+    _compare(make_problem(2))
+
+
+def test_topology_mismatch_is_reported():
+    from paper_2601_19650_gb300 import _cbc
+    a = make_problem(2, L=4, chi=4, D=2, max_bond=4)
+    b = make_problem(2, L=5, chi=4, D=2, max_bond=4)
+    hs = _cbc.create_from_host(a.state.parent, a.state.phys, a.state.bond, a.state.tensors, "state")
+    ho = _cbc.create_from_host(b.op.parent, b.op.phys, b.op.bond, b.op.tensors, "op")
+    with pytest.raises(_cbc.CBCError) as ei:
+        _cbc.cbc_apply(hs, ho, 4, 0.0)
+    assert ei.value.code == 2
+    _cbc.ttn_destroy(hs)
+    _cbc.ttno_destroy(ho)
