@@ -65,6 +65,10 @@ def direct_sum_difference(parent, ta, tb, scale_a: float = 1.0, scale_b: float =
     """Node tensors of the network representing ``scale_a psi_a - scale_b psi_b``."""
     parent = [int(p) for p in parent]
     out = []
+    if len(parent) == 1:                 # one node: no bond to stack along
+        a = np.asarray(ta[0], dtype=np.complex128)
+        b = np.asarray(tb[0], dtype=np.complex128)
+        return [a * scale_a - b * scale_b]
     for i in range(len(parent)):
         a = np.asarray(ta[i], dtype=np.complex128)
         b = np.asarray(tb[i], dtype=np.complex128)

@@ -79,3 +79,10 @@ def test_oracle_output_bonds_clamped():
     for i in range(1, L - 1):
         assert r.out_bonds[i] <= 2 * r.out_bonds[i + 1]
     assert r.out_bonds[L - 1] <= 2
+
+
+def test_metric_single_node():
+    """A one-site network has no bond: the distance is that of the two tensors."""
+    a = [np.array([[1.0, 2.0]])]
+    b = [np.array([[1.0, 2.5]])]
+    assert abs(metrics.rel_err([-1], a, b) - 0.5 / np.linalg.norm([1.0, 2.5])) < 1e-15
