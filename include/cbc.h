@@ -163,6 +163,45 @@ int cbc_stats_enable(int timing); /* 1: time launch groups with CUDA events, 0: 
 int cbc_stats_reset(void);
 int cbc_stats_read(cbc_stats* out); /* synchronises the recorded events              */
 
+/* Tensor-train CBC that allocates no device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (or any allocator) at the point where they need the application, e.g.
+ * code running under a framework that owns every byte of device memory through its
+ * own pool, or a real-time host loop in which allocation is forbidden after start-up.
+ * It runs the same kernels as cbc_apply for a chain (Sec. III A, precision FP64), but
+ * every intermediate lives in one library-owned scratch array of
+ * CBC_NOALLOC_SCRATCH_BYTES, a file-scope __device__ array that each GPU which loads
+ * the library holds until the process exits.
+ *
+ *   L            number of sites (chain rooted at site 0, as in ttn_create)
+ *   phys_dim     [L] host, physical dimensions
+ *   state_bond   [L] host, MPS bond of site i to site i-1 (entry 0 ignored)
+ *   op_bond      [L] host, MPO bond of site i to site i-1 (entry 0 ignored)
+ *   dtype        CBC_F64 or CBC_C128 (the caller widens lower precisions)
+ *   state_nodes  [L] host array of DEVICE pointers, canonical leg order of ttn_create
+ *   op_nodes     [L] host array of DEVICE pointers, canonical leg order of ttno_create
+ *   max_bond, tol  as for cbc_apply
+ *   out_data     DEVICE buffer of out_capacity elements of `dtype`; node i of the result
+ *                (canonical layout, bonds out_bonds) starts at element out_offsets[i]
+ *   out_offsets  [L] host, filled;  out_bonds [L] host, filled (1 at site 0)
+ *   log_norm     host, filled: the result is exp(*log_norm) times the network
+ *   cuda_stream  stream for all work (may be NULL); the call returns after it drained
+ * The first call on a device looks up the device address of the scratch array on that
+ * device (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array and keeps nothing in it that a later call relies on
+ * (it clears what must start at zero), so calls that overlap on the GPU, from several
+ * threads or streams, race: serialise them.  A problem whose intermediates do not fit,
+ * or a result larger than out_capacity, is rejected with CBC_ERR_INVALID_ARG and a
+ * message naming the size it would need; nothing is launched for a problem rejected by
+ * the up-front size check.                                                          */
+#define CBC_NOALLOC_SCRATCH_BYTES (32u << 20)
+int cbc_apply_tt_noalloc(int L, const int64_t* phys_dim, const int64_t* state_bond,
+                         const int64_t* op_bond, int dtype, const void* const* state_nodes,
+                         const void* const* op_nodes, int64_t max_bond, double tol,
+                         void* out_data, int64_t out_capacity, int64_t* out_offsets,
+                         int64_t* out_bonds, double* log_norm, void* cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* cbc_last_error(void);
 

@@ -68,6 +68,10 @@ def lib():
         L.ttn_get_node.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
         L.ttn_destroy.argtypes = [vp]
         L.ttno_destroy.argtypes = [vp]
+        L.cbc_apply_tt_noalloc.argtypes = [ctypes.c_int, P(i64), P(i64), P(i64), ctypes.c_int,
+                                           P(vp), P(vp), i64, dbl, vp, i64, P(i64), P(i64),
+                                           P(dbl), vp]
+        L.cbc_apply_tt_noalloc.restype = ctypes.c_int
         L.cbc_stats_enable.argtypes = [ctypes.c_int]
         L.cbc_stats_reset.argtypes = []
         L.cbc_stats_read.argtypes = [P(cbc_stats)]
@@ -143,6 +147,26 @@ def cbc_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options] =
     _check(lib().cbc_apply(state, op, int(max_bond), float(tol),
                            ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
     return out
+
+
+def cbc_apply_tt_noalloc(phys, state_bond, op_bond, dtype: int, state_ptrs, op_ptrs,
+                         max_bond: int, tol: float, out_ptr: int, out_capacity: int, stream=None):
+    """No-allocation tensor-train CBC: device input pointers, a caller-owned device output
+    buffer; returns (out_offsets, out_bonds, log_norm)."""
+    L = len(phys)
+    ph = (ctypes.c_int64 * L)(*[int(x) for x in phys])
+    sb = (ctypes.c_int64 * L)(*[int(x) for x in state_bond])
+    obd = (ctypes.c_int64 * L)(*[int(x) for x in op_bond])
+    sp = (ctypes.c_void_p * L)(*[ctypes.c_void_p(int(p)) for p in state_ptrs])
+    op = (ctypes.c_void_p * L)(*[ctypes.c_void_p(int(p)) for p in op_ptrs])
+    offs = (ctypes.c_int64 * L)()
+    bonds = (ctypes.c_int64 * L)()
+    ln = ctypes.c_double()
+    _check(lib().cbc_apply_tt_noalloc(L, ph, sb, obd, int(dtype), sp, op, int(max_bond),
+                                      float(tol), ctypes.c_void_p(int(out_ptr)),
+                                      int(out_capacity), offs, bonds, ctypes.byref(ln),
+                                      ctypes.c_void_p(stream or 0)))
+    return np.array(offs[:], dtype=np.int64), np.array(bonds[:], dtype=np.int64), ln.value
 
 
 def ttn_get_info(t):
