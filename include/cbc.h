@@ -138,6 +138,20 @@ int ttn_get_node(ttn_t t, int node, void* dst, int dst_on_device, int dtype);
 int ttn_destroy(ttn_t t);   /* NULL is a no-op */
 int ttno_destroy(ttno_t t); /* NULL is a no-op */
 
+/* Dense product used by every contraction of the sweeps, exposed as a building block
+ * (and for kernel-level tests): C = op(A) op(B) with row-major DEVICE matrices of
+ * dtype CBC_F64 or CBC_C128.  op(X) = X, X^T (trans), conj(X) (conj) or X^H (both).
+ *   precision  CBC_PREC_FP64: FP64 SIMT; CBC_PREC_MIXED: tensor cores with `slices`
+ *              bf16 slices per operand (2..5; 0 = 4), exact FP32 partial sums, FP64
+ *              result (see cbc_apply)
+ *   M, N, K    op(A) is M x K, op(B) is K x N, C is M x N (ldc >= N), K >= 1
+ *   lda, ldb   leading dimensions of A and B as stored
+ * Stream ordered on `stream`; allocates its workspace with cudaMallocAsync on it.
+ * Errors: CBC_ERR_INVALID_ARG, CBC_ERR_OOM, CBC_ERR_CUDA.                           */
+int cbc_gemm(int precision, int slices, int dtype, int M, int N, int K, const void* A,
+             int64_t lda, int transA, int conjA, const void* B, int64_t ldb, int transB,
+             int conjB, void* C, int64_t ldc, void* stream);
+
 /* Launch statistics per kernel class, process wide, for benchmarks and profiling.
  * Launch counts are always kept.  With timing enabled, every group of launches of one
  * class is bracketed by CUDA events on the stream it runs on; cbc_stats_read then waits

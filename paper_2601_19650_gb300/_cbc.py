@@ -72,6 +72,10 @@ def lib():
                                            P(vp), P(vp), i64, dbl, vp, i64, P(i64), P(i64),
                                            P(dbl), vp]
         L.cbc_apply_tt_noalloc.restype = ctypes.c_int
+        L.cbc_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_int, ctypes.c_int, vp, i64, ctypes.c_int, ctypes.c_int,
+                               vp, i64, ctypes.c_int, ctypes.c_int, vp, i64, vp]
+        L.cbc_gemm.restype = ctypes.c_int
         L.cbc_stats_enable.argtypes = [ctypes.c_int]
         L.cbc_stats_reset.argtypes = []
         L.cbc_stats_read.argtypes = [P(cbc_stats)]
@@ -167,6 +171,16 @@ def cbc_apply_tt_noalloc(phys, state_bond, op_bond, dtype: int, state_ptrs, op_p
                                       int(out_capacity), offs, bonds, ctypes.byref(ln),
                                       ctypes.c_void_p(stream or 0)))
     return np.array(offs[:], dtype=np.int64), np.array(bonds[:], dtype=np.int64), ln.value
+
+
+def cbc_gemm(precision: int, slices: int, dtype: int, M: int, N: int, K: int, A_ptr: int,
+             lda: int, transA: bool, conjA: bool, B_ptr: int, ldb: int, transB: bool,
+             conjB: bool, C_ptr: int, ldc: int, stream=None):
+    _check(lib().cbc_gemm(int(precision), int(slices), int(dtype), int(M), int(N), int(K),
+                          ctypes.c_void_p(int(A_ptr)), int(lda), int(bool(transA)),
+                          int(bool(conjA)), ctypes.c_void_p(int(B_ptr)), int(ldb),
+                          int(bool(transB)), int(bool(conjB)), ctypes.c_void_p(int(C_ptr)),
+                          int(ldc), ctypes.c_void_p(stream or 0)))
 
 
 def ttn_get_info(t):

@@ -269,4 +269,51 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_op
   return CBC_OK;
 }
 
+int cbc_gemm(int precision, int slices, int dtype, int M, int N, int K, const void* A,
+             int64_t lda, int transA, int conjA, const void* B, int64_t ldb, int transB,
+             int conjB, void* C, int64_t ldc, void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || ldc < N)
+    return fail(CBC_ERR_INVALID_ARG, "cbc_gemm: bad arguments");
+  if (dtype != CBC_F64 && dtype != CBC_C128)
+    return fail(CBC_ERR_INVALID_ARG, "cbc_gemm: dtype must be CBC_F64 or CBC_C128");
+  if (precision != CBC_PREC_FP64 && precision != CBC_PREC_MIXED)
+    return fail(CBC_ERR_INVALID_ARG, "cbc_gemm: bad precision");
+  if (slices == 0) slices = 4;
+  if (precision == CBC_PREC_MIXED && (slices < 2 || slices > 5))
+    return fail(CBC_ERR_INVALID_ARG, "cbc_gemm: slices must be in [2, 5]");
+  View va = transA ? View::transposed(lda) : View::rowmajor(lda);
+  View vb = transB ? View::transposed(ldb) : View::rowmajor(ldb);
+  View vc = View::rowmajor(ldc);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* status = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&status), sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cbc_gemm: alloc");
+  e = cudaMemsetAsync(status, 0, sizeof(int), s);
+  void* ws = nullptr;
+  const bool cplx = dtype == CBC_C128;
+  if (e == cudaSuccess && precision == CBC_PREC_MIXED) {
+    e = cudaMallocAsync(&ws, gemm_tc_workspace_bytes(M, N, K, cplx, slices), s);
+    if (e == cudaSuccess) {
+      e = cplx ? gemm_tc<zdbl>(M, N, K, (const zdbl*)A, va, conjA, (const zdbl*)B, vb, conjB,
+                               (zdbl*)C, vc, slices, ws, status, s)
+               : gemm_tc<double>(M, N, K, (const double*)A, va, conjA, (const double*)B, vb,
+                                 conjB, (double*)C, vc, slices, ws, status, s);
+    }
+  } else if (e == cudaSuccess) {
+    e = cplx ? gemm_f64<zdbl>(M, N, K, 1, (const zdbl*)A, va, conjA, (const zdbl*)B, vb, conjB,
+                              (zdbl*)C, vc, s)
+             : gemm_f64<double>(M, N, K, 1, (const double*)A, va, conjA, (const double*)B, vb,
+                                conjB, (double*)C, vc, s);
+  }
+  int hs = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (ws) cudaFreeAsync(ws, s);
+  cudaFreeAsync(status, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "cbc_gemm");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cbc_gemm: synchronize");
+  if (hs != 0) return fail(hs, "cbc_gemm: device status %d", hs);
+  return CBC_OK;
+}
+
 }  // extern "C"

@@ -1,0 +1,589 @@
+// Split-precision tensor-core GEMM for sm_103a (tcgen05 + TMA + TMEM).
+//
+// The contractions and Gram products of the CBC sweeps (Sec. III A/B) are dense, so
+// the mixed path runs them on the 5th-generation tensor cores.  The CBC truncation is
+// sensitive to rounding in the forward sweep (a subspace choice at every bond), so
+// plain bf16/TF32 products are not accurate enough; instead every operand element is
+// written exactly as a short sum of bf16 integers ("slices") on a fixed-point grid:
+//
+//   row (or column) exponent e with max|x| < 2^e,  x = 2^(e-7) * sum_s 2^(-8s) q_s,
+//   q_s integers in [-128, 128] (exact in bf16), s = 0 .. S-1, round to nearest.
+//
+// A product a.b then is 2^(ea+eb-14) * sum_{s,t} 2^(-8(s+t)) (q^a_s . q^b_t).  The
+// terms with s+t < S are kept; for each level g = s+t the tensor cores accumulate
+// sum_{s+t=g} q^a_s . q^b_t in FP32 over a K chunk short enough (<= 1024 / S products
+// of magnitude <= 2^14 per element) that every partial sum is an integer below 2^24,
+// hence exact.  The epilogue warps read the S level sums of a chunk from TMEM,
+// convert them to integers and fold them into one int64 per output element,
+// I += sum_g C_g << 8(S-1-g); the final value is 2^(ea+eb-14-8(S-1)) * I in FP64.
+// With S slices an operand keeps ~8S-1 bits relative to its row maximum.
+//
+// Complex operands use the real 2x2 embedding: A' = [re, im] interleaved along K
+// (M x 2K) and B' = [[br, bi], [-bi, br]] blocks (2K x 2N), so C' = A' B' holds
+// [Re C, Im C] interleaved along N: the 4 real products of a complex product in one
+// real GEMM.
+//
+// Kernel: one 128 x BN output tile per CTA (cta_group::1), 6 warps: warp 0 issues TMA
+// loads of 64-wide K atoms (S slices of A and of B per atom, 128B swizzle, two smem
+// stages), warp 1 issues tcgen05.mma (one elected thread) into S TMEM accumulators per
+// chunk, double buffered so the epilogue of chunk c overlaps the MMAs of chunk c+1,
+// warps 2-5 drain TMEM (tcgen05.ld) into int64 registers and finally write FP64.
+// Every wait is bounded (clock64); a timeout raises CBC_ERR_TIMEOUT in the status
+// word, all roles leave their loops, and TMEM is freed before the CTA exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kernels.cuh"
+#include "planner.h"
+
+namespace cbc {
+namespace tc {
+
+constexpr int BM = 128;          // rows of the output tile (TMEM lanes)
+constexpr int KA = 64;           // bf16 elements per K atom (one 128-byte swizzle row)
+constexpr int NSTAGE = 2;
+// warps: 0 TMA, 1 MMA, then 4 epilogue warps per 32 accumulator columns
+__host__ __device__ constexpr int epi_warps(int BN) { return (BN / 32) * 4; }
+__host__ __device__ constexpr int nthreads(int BN) { return 64 + 32 * epi_warps(BN); }
+constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase.  Returns false (and raises the abort flag) on
+// timeout or when another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* status) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort_flag = 1;
+      set_status(status, CBC_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int c0,
+                                            int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major tile, 128-byte swizzle, 8-row core groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;               // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;               // descriptor version of the tcgen05 family
+  d |= (uint64_t)2 << 61;               // 128-byte swizzle
+  return d;
+}
+
+// instruction descriptor: D f32, A and B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+  int M, N2;             // real-embedded output rows / columns
+  int atoms_total;       // K2_pad / 64
+  int atoms_per_split;   // multiple of atoms_per_chunk
+  int atoms_per_chunk;
+  const int* expA;       // [M_pad]
+  const int* expB;       // [N_pad] (one per complex column when cplx)
+  int cplx;
+  int atomic;
+  char* C;               // FP64 output (double or zdbl) through the view
+  View vc;
+  int* status;
+};
+
+template <int S, int BN>
+__global__ void __launch_bounds__(nthreads(BN), 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   TcArgs a) {
+  constexpr int A_BYTES = BM * KA * 2;
+  constexpr int B_BYTES = BN * KA * 2;
+  constexpr int STAGE_BYTES = S * (A_BYTES + B_BYTES);
+  constexpr uint32_t TMEM_COLS = 512;
+  static_assert(2 * S * BN <= 512, "TMEM budget");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* tfull = empty + NSTAGE;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int a_begin = blockIdx.z * a.atoms_per_split;
+  const int a_end = min(a.atoms_total, a_begin + a.atoms_per_split);
+  const int n_atoms = max(0, a_end - a_begin);
+  const int n_chunks = (n_atoms + a.atoms_per_chunk - 1) / a.atoms_per_chunk;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull + i, 1);
+      mbar_init(tempty + i, epi_warps(BN));
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
+      for (int j = 0; j < n_atoms; ++j) {
+        const int stage = j % NSTAGE, use = j / NSTAGE;
+        if (!mbar_wait(empty + stage, (use & 1) ^ 1, abort_flag, a.status)) break;
+        uint8_t* sA = smem + stage * STAGE_BYTES;
+        uint8_t* sB = sA + S * A_BYTES;
+        mbar_expect_tx(full + stage, STAGE_BYTES);
+        const int k = (a_begin + j) * KA;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          tma_load_3d(&tmA, full + stage, sA + s * A_BYTES, k, m0, s);
+          tma_load_3d(&tmB, full + stage, sB + s * B_BYTES, k, n0, s);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int j = 0;
+      for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
+        const int buf = c & 1, use = c >> 1;
+        if (!mbar_wait(tempty + buf, (use & 1) ^ 1, abort_flag, a.status)) break;
+        tc_fence_after();
+        const int j_end = min(n_atoms, j + a.atoms_per_chunk);
+        bool first = true;
+        for (; j < j_end; ++j) {
+          const int stage = j % NSTAGE, su = j / NSTAGE;
+          if (!mbar_wait(full + stage, su & 1, abort_flag, a.status)) break;
+          tc_fence_after();
+          const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t sB = sA + S * A_BYTES;
+#pragma unroll
+          for (int g = 0; g < S; ++g) {
+            const uint32_t d = tmem_base + (uint32_t)((buf * S + g) * BN);
+#pragma unroll
+            for (int s = 0; s <= g; ++s) {
+              const int t = g - s;
+#pragma unroll
+              for (int kk = 0; kk < KA / 16; ++kk) {
+                uint64_t ad = sdesc_sw128(sA + s * A_BYTES + kk * 32);
+                uint64_t bd = sdesc_sw128(sB + t * B_BYTES + kk * 32);
+                umma_bf16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
+              }
+            }
+          }
+          first = false;
+          umma_commit(empty + stage);  // smem stage free once these MMAs complete
+        }
+        umma_commit(tfull + buf);      // chunk sums ready in TMEM
+      }
+    }
+  } else {
+    // ---------------- epilogue (warps 2 ..) ----------------
+    // warp w may read TMEM lanes 32*(w%4) .. +31; warps 2-5 take accumulator columns
+    // 0-31, warps 6-9 columns 32-63 (BN = 64)
+    const int ew = warp - 2;
+    const int quarter = warp & 3;
+    const int cg = ew >> 2;
+    const int row = m0 + quarter * 32 + lane;
+    long long acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = 0;
+    bool ok = true;
+    for (int c = 0; c < n_chunks; ++c) {
+      const int buf = c & 1, use = c >> 1;
+      if (!mbar_wait(tfull + buf, use & 1, abort_flag, a.status)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int g = 0; g < S; ++g) {
+        const int shift = 8 * (S - 1 - g);
+        uint32_t r[32];
+        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                      (uint32_t)((buf * S + g) * BN + cg * 32),
+                  r);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          long long q = (long long)__float2int_rn(__uint_as_float(r[i]));
+          acc[i] += q << shift;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + buf);
+    }
+    if (ok && n_chunks > 0 && row < a.M) {
+      const int ea = a.expA[row];
+      const int bias = -14 - 8 * (S - 1);
+      const int64_t ro = a.vc.roff(row);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int col = n0 + cg * 32 + i;
+        if (col < a.N2) {
+          const int ncol = a.cplx ? (col >> 1) : col;
+          const double v = ldexp((double)acc[i], ea + a.expB[ncol] + bias);
+          double* dst;
+          if (a.cplx)
+            dst = reinterpret_cast<double*>(a.C + 16 * (ro + a.vc.coff(ncol))) + (col & 1);
+          else
+            dst = reinterpret_cast<double*>(a.C + 8 * (ro + a.vc.coff(ncol)));
+          if (a.atomic)
+            atomicAdd(dst, v);
+          else
+            *dst = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(TMEM_COLS));
+  }
+}
+
+// ---------------- operand slicing ----------------
+// One warp per logical row: a row of A (M x K), or a column of B (K x N) for the B^T
+// side.  Writes S bf16 slices into [S][rows_pad][K2_pad] and the row exponent.
+template <typename T, bool SIDE_B>
+__global__ void pack_kernel(const T* src, View v, int conj, int R, int K, int rows_pad, int K2_pad,
+                            int S, __nv_bfloat16* out, int* expo, int* status) {
+  using O = ops<T>;
+  constexpr bool CPLX = O::cplx;
+  const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nrows_logical = CPLX && SIDE_B ? rows_pad / 2 : rows_pad;
+  if (warp_g >= nrows_logical) return;
+  const int r = warp_g;
+  auto load = [&](int k) -> T {
+    T x = SIDE_B ? src[v.roff(k) + v.coff(r)] : src[v.roff(r) + v.coff(k)];
+    return conj ? O::conj(x) : x;
+  };
+  const bool live = r < R;
+  double mx = 0.0;
+  if (live)
+    for (int k = lane; k < K; k += 32) {
+      T x = load(k);
+      mx = fmax(mx, fmax(fabs(O::real(x)), fabs(O::imag(x))));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (!isfinite(mx)) {
+    if (lane == 0) set_status(status, CBC_ERR_NUMERICAL);
+    mx = 0.0;
+  }
+  int e = 0;
+  if (mx > 0.0) e = ilogb(mx) + 1;  // max|x| < 2^e
+  if (lane == 0) expo[r] = e;
+  const size_t plane = (size_t)rows_pad * K2_pad;
+  // element k of the logical row -> one (real) or two (complex) K positions
+  const int prow0 = (CPLX && SIDE_B) ? 2 * r : r;
+  for (int k = lane; k < K2_pad / (CPLX ? 2 : 1); k += 32) {
+    double vals[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // [packed row][pair position]
+    if (live && k < K) {
+      T x = load(k);
+      double xr = O::real(x), xi = O::imag(x);
+      if (!CPLX) {
+        vals[0][0] = xr;
+      } else if (!SIDE_B) {
+        vals[0][0] = xr;
+        vals[0][1] = xi;
+      } else {
+        vals[0][0] = xr;   // row 2n:   [ br, -bi ]
+        vals[0][1] = -xi;
+        vals[1][0] = xi;   // row 2n+1: [ bi,  br ]
+        vals[1][1] = xr;
+      }
+    }
+    const int nprow = (CPLX && SIDE_B) ? 2 : 1;
+    const int npos = CPLX ? 2 : 1;
+    for (int pr = 0; pr < nprow; ++pr) {
+      for (int pp = 0; pp < npos; ++pp) {
+        double t = ldexp(vals[pr][pp], 7 - e);  // |t| < 128
+        const size_t base = (size_t)(prow0 + pr) * K2_pad + (size_t)k * npos + pp;
+        for (int s = 0; s < S; ++s) {
+          double q = rint(t);
+          out[s * plane + base] = __float2bfloat16_rn((float)q);
+          t = (t - q) * 256.0;
+        }
+      }
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, void* base, int K2_pad, int rows_pad, int S, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)K2_pad, (cuuint64_t)rows_pad, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)K2_pad * 2, (cuuint64_t)rows_pad * K2_pad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)KA, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int bn_for(int S) { return S <= 4 ? 64 : 32; }
+int atoms_per_chunk_for(int S) { return std::max(1, (1024 / S) / KA); }
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Geo {
+  int Mp, N2, N2p, K2, K2p, BN;
+};
+Geo geometry(int M, int N, int K, bool cplx, int S) {
+  Geo g;
+  g.BN = bn_for(S);
+  g.Mp = (M + BM - 1) / BM * BM;
+  g.N2 = cplx ? 2 * N : N;
+  g.N2p = (g.N2 + g.BN - 1) / g.BN * g.BN;
+  g.K2 = cplx ? 2 * K : K;
+  g.K2p = (g.K2 + KA - 1) / KA * KA;
+  return g;
+}
+
+template <int S>
+size_t smem_bytes() {
+  constexpr int BN = S <= 4 ? 64 : 32;
+  return (size_t)NSTAGE * S * (BM * KA * 2 + BN * KA * 2) + 1024 + 256;
+}
+
+template <int S>
+cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args, dim3 grid,
+                   cudaStream_t s) {
+  constexpr int BN = S <= 4 ? 64 : 32;
+  static bool attr_set = false;
+  size_t sm = smem_bytes<S>();
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<S, BN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  gemm_tc_kernel<S, BN><<<grid, nthreads(BN), sm, s>>>(ma, mb, args);
+  return cudaGetLastError();
+}
+
+int g_sms = 0;
+
+}  // namespace tc
+
+size_t gemm_tc_workspace_bytes(int M, int N, int K, bool cplx, int S) {
+  using namespace tc;
+  if (M < BM && N > M) std::swap(M, N);
+  Geo g = geometry(M, N, K, cplx, S);
+  return a256((size_t)S * g.Mp * g.K2p * 2) + a256((size_t)S * g.N2p * g.K2p * 2) +
+         a256(sizeof(int) * g.Mp) + a256(sizeof(int) * g.N2p) + 1024;
+}
+
+static View transpose_view(const View& v) {
+  View t;
+  t.r_in = v.c_in;
+  t.rs_out = v.cs_out;
+  t.rs_in = v.cs_in;
+  t.c_in = v.r_in;
+  t.cs_out = v.rs_out;
+  t.cs_in = v.rs_in;
+  t.bs = v.bs;
+  return t;
+}
+
+template <typename T>
+cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA, const T* B,
+                    const View& vb, bool conjB, T* C, const View& vc, int S, void* ws,
+                    int* status, cudaStream_t s) {
+  using namespace tc;
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (S < 2 || S > 5) return cudaErrorInvalidValue;
+  // keep the long dimension on the 128-row side: C^T = B^T A^T
+  if (M < BM && N > M) {
+    return gemm_tc<T>(N, M, K, B, transpose_view(vb), conjB, A, transpose_view(va), conjA, C,
+                      transpose_view(vc), S, ws, status, s);
+  }
+  constexpr bool CPLX = ops<T>::cplx;
+  if (g_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  Geo g = geometry(M, N, K, CPLX, S);
+  char* w = static_cast<char*>(ws);
+  w = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(w) + 255) & ~uintptr_t(255));
+  __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(w);
+  w += a256((size_t)S * g.Mp * g.K2p * 2);
+  __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(w);
+  w += a256((size_t)S * g.N2p * g.K2p * 2);
+  int* ea = reinterpret_cast<int*>(w);
+  w += a256(sizeof(int) * g.Mp);
+  int* eb = reinterpret_cast<int*>(w);
+  if (K <= 0) return cudaErrorInvalidValue;
+  // slices of A (rows) and of B (columns, embedded)
+  {
+    int warps = g.Mp;
+    note_launches(CBC_K_AUX, 2);
+    pack_kernel<T, false><<<(warps * 32 + 255) / 256, 256, 0, s>>>(
+        A, va, conjA ? 1 : 0, M, K, g.Mp, g.K2p, S, sa, ea, status);
+    int wb = CPLX ? g.N2p / 2 : g.N2p;
+    pack_kernel<T, true><<<(wb * 32 + 255) / 256, 256, 0, s>>>(B, vb, conjB ? 1 : 0, N, K, g.N2p,
+                                                                g.K2p, S, sb, eb, status);
+  }
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, sa, g.K2p, g.Mp, S, BM) || !make_map(&mb, sb, g.K2p, g.N2p, S, g.BN))
+    return cudaErrorInvalidValue;
+  const int atoms = g.K2p / KA;
+  const int apc = atoms_per_chunk_for(S);
+  const int tiles = (g.Mp / BM) * (g.N2p / g.BN);
+  const int chunks = (atoms + apc - 1) / apc;
+  int splits = 1;
+  if (tiles < g_sms && chunks > 1) splits = std::min(chunks, std::max(1, g_sms / tiles));
+  const int chunks_per_split = (chunks + splits - 1) / splits;
+  splits = (chunks + chunks_per_split - 1) / chunks_per_split;
+  TcArgs args;
+  args.M = M;
+  args.N2 = g.N2;
+  args.atoms_total = atoms;
+  args.atoms_per_chunk = apc;
+  args.atoms_per_split = chunks_per_split * apc;
+  args.expA = ea;
+  args.expB = eb;
+  args.cplx = CPLX ? 1 : 0;
+  args.atomic = splits > 1 ? 1 : 0;
+  args.C = reinterpret_cast<char*>(C);
+  args.vc = vc;
+  args.status = status;
+  if (splits > 1) {
+    // the split partial sums are added into a zeroed C
+    cudaError_t e = gemm_f64<T>(M, N, 0, 1, A, va, false, B, vb, false, C, vc, s);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid(g.Mp / BM, g.N2p / g.BN, splits);
+  note_launches(CBC_K_GEMM_TC, 1);
+  switch (S) {
+    case 2: return launch<2>(ma, mb, args, grid, s);
+    case 3: return launch<3>(ma, mb, args, grid, s);
+    case 4: return launch<4>(ma, mb, args, grid, s);
+    default: return launch<5>(ma, mb, args, grid, s);
+  }
+}
+
+template cudaError_t gemm_tc<double>(int, int, int, const double*, const View&, bool,
+                                     const double*, const View&, bool, double*, const View&, int,
+                                     void*, int*, cudaStream_t);
+template cudaError_t gemm_tc<zdbl>(int, int, int, const zdbl*, const View&, bool, const zdbl*,
+                                   const View&, bool, zdbl*, const View&, int, void*, int*,
+                                   cudaStream_t);
+
+}  // namespace cbc

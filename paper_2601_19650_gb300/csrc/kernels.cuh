@@ -62,6 +62,14 @@ cudaError_t gemm_f64(int M, int N, int K, int batch, const T* A, const View& va,
                      const T* B, const View& vb, bool conjB, T* C, const View& vc,
                      cudaStream_t s);
 
+// The same product on the tensor cores with S bf16 slices per operand (gemm_tc.cu);
+// `ws` must hold gemm_tc_workspace_bytes(M, N, K, cplx, S) bytes.  batch = 1.
+size_t gemm_tc_workspace_bytes(int M, int N, int K, bool cplx, int S);
+template <typename T>
+cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA, const T* B,
+                    const View& vb, bool conjB, T* C, const View& vc, int S, void* ws,
+                    int* status, cudaStream_t s);
+
 // ---- Hermitian eigensolver (FP64): A (m x m, row-major, overwritten) -----------------
 // Finds the eigenvalues in descending order and the eigenvectors of the `k` largest,
 // where k follows the rank rule of cbc_apply: k = min(max_bond (if > 0), #{lambda_j >

@@ -78,11 +78,29 @@ T host_one() {
   return v;
 }
 
-// FP64 GEMM with its launch group timed; `gram` halves the algorithmic flops
+// One contraction or Gram product, timed as a launch group: FP64 SIMT on the plain
+// path, tensor-core slices on the mixed path (`fwd` picks the slice count of the first
+// sweep, which feeds the truncations, or of the last one).  `gram` halves the
+// algorithmic flops.
+struct Prec {
+  bool mixed = false;
+  int s_fwd = 5, s_bwd = 4;
+  Arena* ar = nullptr;
+  int* status = nullptr;
+};
+
 template <typename T>
-cudaError_t tgemm(bool gram, int M, int N, int K, const T* A, const View& va, bool ca, const T* B,
-                  const View& vb, bool cb, T* C, const View& vc, cudaStream_t s) {
+cudaError_t tgemm(const Prec& pr, bool fwd, bool gram, int M, int N, int K, const T* A,
+                  const View& va, bool ca, const T* B, const View& vb, bool cb, T* C,
+                  const View& vc, cudaStream_t s) {
   double fl = (ops<T>::cplx ? 8.0 : 2.0) * (double)M * N * K * (gram ? 0.5 : 1.0);
+  if (pr.mixed && K > 0) {
+    const int S = fwd ? pr.s_fwd : pr.s_bwd;
+    void* ws = pr.ar->get<char>(gemm_tc_workspace_bytes(M, N, K, ops<T>::cplx, S));
+    if (!ws) return pr.ar->err;
+    KTimer t(CBC_K_GEMM_TC, s, 0, fl);
+    return gemm_tc<T>(M, N, K, A, va, ca, B, vb, cb, C, vc, S, ws, pr.status, s);
+  }
   KTimer t(CBC_K_GEMM_F64, s, 0, fl);
   return gemm_f64<T>(M, N, K, 1, A, va, ca, B, vb, cb, C, vc, s);
 }
@@ -107,8 +125,9 @@ int read_k(const Scalars& sc, cudaStream_t s, int* k) {
 // Gram reproduces the rank-k truncation of M^H M (Sec. III A, text after Eq.
 // (tt_cbc_first_contraction)), normalised, and returns k.
 template <typename T>
-int compress_rows(Arena& ar, const T* M, int m, int n, int64_t max_bond, double tol,
-                  const Options& o, const Scalars& sc, cudaStream_t s, T** Lout, int* kout) {
+int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t max_bond,
+                  double tol, const Options& o, const Scalars& sc, cudaStream_t s, T** Lout,
+                  int* kout) {
   const int kmax = (int)((max_bond > 0) ? std::min<int64_t>(max_bond, std::min(m, n)) : std::min(m, n));
   const double floor_rel = o.eps_rank * o.eps_rank;
   const int g = std::min(m, n);
@@ -118,10 +137,10 @@ int compress_rows(Arena& ar, const T* M, int m, int n, int64_t max_bond, double 
   char* work = ar.get<char>(eig_workspace_bytes(g, kmax, ops<T>::cplx));
   CKA(K); CKA(lam); CKA(U); CKA(work);
   if (m <= n) {  // K = M M^H, eigenvectors = left singular vectors
-    CK(tgemm<T>(true, m, m, n, M, View::rowmajor(n), false, M, View::transposed(n), true, K,
+    CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n), false, M, View::transposed(n), true, K,
                    View::rowmajor(m), s));
   } else {       // G = M^H M, eigenvectors = right singular vectors
-    CK(tgemm<T>(true, n, n, m, M, View::transposed(n), true, M, View::rowmajor(n), false, K,
+    CK(tgemm<T>(pr, true, true, n, n, m, M, View::transposed(n), true, M, View::rowmajor(n), false, K,
                    View::rowmajor(n), s));
   }
   {
@@ -134,7 +153,7 @@ int compress_rows(Arena& ar, const T* M, int m, int n, int64_t max_bond, double 
   T* L = ar.get<T>((size_t)k * n);
   CKA(L);
   if (m <= n) {  // L = U_k^H M
-    CK(tgemm<T>(false, k, n, m, U, View::transposed(kmax), true, M, View::rowmajor(n), false, L,
+    CK(tgemm<T>(pr, true, false, k, n, m, U, View::transposed(kmax), true, M, View::rowmajor(n), false, L,
                    View::rowmajor(n), s));
   } else {       // L = diag(sqrt(lambda_k)) V_k^H
     CK(scaled_adjoint<T>(U, kmax, lam, sc.k, n, L, s));
@@ -148,12 +167,13 @@ int compress_rows(Arena& ar, const T* M, int m, int n, int64_t max_bond, double 
 // S (m x n, row-major) -> Q with orthonormal rows spanning the row space of S, in place
 // (CholeskyQR2; Eq. (tt_cbc_qr_decomp) is the LQ on chi_{i-1}).  Requires m <= n.
 template <typename T>
-int lq_rows_inplace(Arena& ar, T* S, int m, int n, const Scalars& sc, cudaStream_t s) {
+int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars& sc,
+                    cudaStream_t s) {
   T* G = ar.get<T>((size_t)m * m);
   void* bar = ar.get<GridBarrier>(1);
   CKA(G); CKA(bar);
   for (int rep = 0; rep < 2; ++rep) {
-    CK(tgemm<T>(true, m, m, n, S, View::rowmajor(n), false, S, View::transposed(n), true, G,
+    CK(tgemm<T>(pr, false, true, m, m, n, S, View::rowmajor(n), false, S, View::transposed(n), true, G,
                    View::rowmajor(m), s));
     KTimer t(CBC_K_CHOLQR, s, 0,
              (ops<T>::cplx ? 4.0 : 1.0) * ((double)m * m * m / 3.0 + (double)m * m * n));
@@ -176,6 +196,12 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
   CK(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
   CK(cudaMemsetAsync(d_dbl, 0, 4 * sizeof(double), s));
   Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + 1, d_dbl + 2};
+  Prec pr;
+  pr.mixed = (o.precision == CBC_PREC_MIXED);
+  pr.s_fwd = o.slices_fwd;
+  pr.s_bwd = o.slices_bwd;
+  pr.ar = &ar;
+  pr.status = sc.status;
   auto sb = [&](int i) { return i < L ? (int)st.bond[i] : 1; };  // alpha_{i-1} (site i's parent leg)
   auto ob = [&](int i) { return i < L ? (int)op.bond[i] : 1; };
   const T one = host_one<T>();
@@ -193,7 +219,7 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
     // F1: X[(chi b), (sigma a')] = sum_a L[(chi b), a] T[a, (sigma a')]
     T* X = ar.get<T>((size_t)c * b * d * a2);
     CKA(X);
-    CK(tgemm<T>(false, c * b, d * a2, a, env[i], View::rowmajor(a), false, Ti, View::rowmajor(d * a2),
+    CK(tgemm<T>(pr, true, false, c * b, d * a2, a, env[i], View::rowmajor(a), false, Ti, View::rowmajor(d * a2),
                    false, X, View::rowmajor(d * a2), s));
     // F2: L'[chi, sigma', b', a'] = sum_{b, sigma} X[chi, b, sigma, a'] W[b, sigma', sigma, b']
     //     as C[(sigma' b'), (chi a')] = W[(sigma' b'), (b sigma)] X[(b sigma), (chi a')]
@@ -207,10 +233,10 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
     View vl;
     vl.rs_in = a2;
     vl.cols2(a2, (int64_t)d * b2 * a2, 1);
-    CK(tgemm<T>(false, d * b2, c * a2, b * d, Wi, vw, false, X, vx, false, Lp, vl, s));
+    CK(tgemm<T>(pr, true, false, d * b2, c * a2, b * d, Wi, vw, false, X, vx, false, Lp, vl, s));
     // F3: compress M[(chi sigma'), (b' a')]
     int k = 0;
-    int rc = compress_rows<T>(ar, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k);
+    int rc = compress_rows<T>(ar, pr, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k);
     if (rc != CBC_OK) return rc;
     chi[i + 1] = k;
   }
@@ -240,7 +266,7 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
     // B1: Y[(a sigma), (chi' b_out)] = sum_{a_out} T[(a sigma), a_out] R[(chi' b_out), a_out]
     T* Y = ar.get<T>((size_t)a_in * d * cp * b_out);
     CKA(Y);
-    CK(tgemm<T>(false, a_in * d, cp * b_out, a_out, Ti, View::rowmajor(a_out), false, R,
+    CK(tgemm<T>(pr, false, false, a_in * d, cp * b_out, a_out, Ti, View::rowmajor(a_out), false, R,
                    View::transposed(a_out), false, Y, View::rowmajor(cp * b_out), s));
     // B2: Z[b_in, a, sigma', chi'] = sum_{sigma, b_out} W[b_in, sigma', sigma, b_out] Y[a, sigma, chi', b_out]
     //     as C[(b_in sigma'), (a chi')] = W[(b_in sigma'), (sigma b_out)] Y[(sigma b_out), (a chi')]
@@ -250,7 +276,7 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
     vy.rows2(b_out, (int64_t)cp * b_out, 1).cols2(cp, (int64_t)d * cp * b_out, b_out);
     View vz;
     vz.rows2(d, (int64_t)a_in * d * cp, cp).cols2(cp, (int64_t)d * cp, 1);
-    CK(tgemm<T>(false, b_in * d, a_in * cp, d * b_out, Wi, View::rowmajor(d * b_out), false, Y, vy,
+    CK(tgemm<T>(pr, false, false, b_in * d, a_in * cp, d * b_out, Wi, View::rowmajor(d * b_out), false, Y, vy,
                    false, Z, vz, s));
     // B3: S[chi, (sigma' chi')] = sum_{(b a)} L^[i-1][chi, (b a)] Z[(b a), (sigma' chi')]
     const int n = d * cp;
@@ -261,7 +287,7 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
     out->data[i] = node;
     out->numel[i] = (int64_t)cn * n;
     if (i == 0 || m <= n) {
-      CK(tgemm<T>(false, m, n, b_in * a_in, env[i], View::rowmajor(b_in * a_in), false, Z,
+      CK(tgemm<T>(pr, false, false, m, n, b_in * a_in, env[i], View::rowmajor(b_in * a_in), false, Z,
                      View::rowmajor(n), false, node, View::rowmajor(n), s));
     }
     if (i == 0) {  // T'^[1] = S^[1]
@@ -271,7 +297,7 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
     }
     // B4: S = R Q on chi_{i-1}; Q^[i] is the new tensor
     if (m <= n) {
-      int rc = lq_rows_inplace<T>(ar, node, m, n, sc, s);
+      int rc = lq_rows_inplace<T>(ar, pr, node, m, n, sc, s);
       if (rc != CBC_OK) return rc;
     } else {  // more rows than columns: any unitary basis of the columns; take the identity
       CK(fill_identity<T>(node, n, s));
@@ -279,7 +305,7 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
     // B5: R^[i-1][chi'', (b a)] = sum_{(sigma' chi')} conj(Q[chi'', (sigma' chi')]) Z[(b a), (sigma' chi')]
     T* Rn = ar.get<T>((size_t)cn * b_in * a_in);
     CKA(Rn);
-    CK(tgemm<T>(false, cn, b_in * a_in, n, node, View::rowmajor(n), true, Z, View::transposed(n),
+    CK(tgemm<T>(pr, false, false, cn, b_in * a_in, n, node, View::rowmajor(n), true, Z, View::transposed(n),
                    false, Rn, View::rowmajor(b_in * a_in), s));
     CK(normalize_inplace<T>(Rn, (int64_t)cn * b_in * a_in, sc.log_out, sc.status, sc.scratch, s));
     R = Rn;
@@ -308,8 +334,9 @@ int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Op
             Net* out) {
   if (st.cplx != op.cplx)
     return fail(CBC_ERR_UNSUPPORTED, "cbc_apply: state and operator must both be real or both complex");
-  if (o.precision != CBC_PREC_FP64)
-    return fail(CBC_ERR_UNSUPPORTED, "cbc_apply: this precision is not built yet");
+  if (o.precision == CBC_PREC_MIXED && (o.slices_fwd < 2 || o.slices_fwd > 5 || o.slices_bwd < 2 ||
+                                        o.slices_bwd > 5))
+    return fail(CBC_ERR_INVALID_ARG, "cbc_apply: slice counts must be in [2, 5]");
   if (!is_chain(st)) return fail(CBC_ERR_UNSUPPORTED, "cbc_apply: general trees are not built yet");
   if (st.cplx) return run_tt<zdbl>(st, op, max_bond, tol, o, out);
   return run_tt<double>(st, op, max_bond, tol, o, out);

@@ -81,3 +81,36 @@ def test_topology_mismatch_is_reported():
     assert ei.value.code == 2
     _cbc.ttn_destroy(hs)
     _cbc.ttno_destroy(ho)
+
+
+# ---------------------------------------------------------------------------------------
+# mixed path: tensor-core slices for contractions and Gram products, FP64 eigensolver,
+# Cholesky and triangular solves.  Bar: relative state error <= 1e-6.
+# ---------------------------------------------------------------------------------------
+MIXED_BAR = 1e-6
+
+
+def _compare_mixed(prob, **kw):
+    from paper_2601_19650_gb300 import _cbc
+    got, bonds, log_norm = run_gpu(prob, precision=_cbc.CBC_PREC_MIXED, **kw)
+    ref = cbc.cbc(prob.state.parent, prob.state.tensors, prob.op.tensors,
+                  kw.get("max_bond", prob.max_bond), kw.get("tol", prob.tol))
+    e = metrics.rel_err(prob.state.parent, got, ref.tensors, log_norm, 0.0)
+    assert list(bonds) == list(ref.out_bonds), (bonds, ref.out_bonds)
+    assert e <= MIXED_BAR, (prob.name, e)
+    return e
+
+
+def test_mixed_cfg1():
+    _compare_mixed(make_problem(1))
+
+
+@pytest.mark.parametrize("L,chi,D,mb,seed", [(2, 4, 2, 4, 0), (12, 16, 4, 16, 0),
+                                             (12, 16, 4, 5, 3), (20, 33, 5, 40, 4)])
+def test_mixed_complex_chain_small(L, chi, D, mb, seed):
+    _compare_mixed(make_problem(2, L=L, chi=chi, D=D, max_bond=mb, seed=seed))
+
+
+def test_mixed_cfg2_full():
+    """The bench workload: L=64, d=2, chi=128, D=16, max_bond=128, complex64."""
+    _compare_mixed(make_problem(2))
