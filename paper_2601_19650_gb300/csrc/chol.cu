@@ -2,11 +2,19 @@
 //
 // The backward sweep decomposes S^[i] = R Q^[i] on the leg chi_{i-1} (Eq.
 // (tt_cbc_qr_decomp); Eq. (cbc_tree_qr) on trees).  With S of m rows and n >= m columns
-// the GPU path forms G = S S^H (FP64 accumulation), factors G = C C^H, and solves
-// Q = C^{-1} S; doing it twice (CholeskyQR2) restores orthonormality to FP64 round-off.
-// Both kernels are cooperative launches over up to one CTA per SM with 32-wide column
-// blocks: a block step is a small factorisation or solve followed by a trailing
-// update spread over all CTAs, separated by bounded grid barriers.
+// the GPU path forms G = S S^H, factors G = C C^H, and solves Q = C^{-1} S; doing it
+// twice (CholeskyQR2) restores orthonormality to FP64 round-off.
+//
+// Cholesky: a cooperative launch with 32-wide column blocks.  Per block, CTA 0 factors
+// the diagonal block in shared memory, every other row of the panel is solved by one
+// warp (shuffles carry the solved entries), and the trailing lower triangle is updated
+// from a shared-memory copy of the panel; bounded grid barriers separate the phases.
+// Triangular solve: columns of S are independent, so each warp owns one column and runs
+// the forward substitution in 32-row groups without any inter-CTA synchronisation.
+// Divisions use Newton reciprocals (rcp64): long dependent chains of FP64 divisions are
+// slow on this part.
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "planner.h"
 
@@ -26,6 +34,17 @@ __device__ __forceinline__ zdbl ldg_cg<zdbl>(const zdbl* p) {
 }
 
 template <typename T>
+__device__ __forceinline__ T shfl(T v, int src);
+template <>
+__device__ __forceinline__ double shfl<double>(double v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+template <>
+__device__ __forceinline__ zdbl shfl<zdbl>(zdbl v, int src) {
+  return {__shfl_sync(0xffffffffu, v.re, src), __shfl_sync(0xffffffffu, v.im, src)};
+}
+
+template <typename T>
 struct CholArgs {
   T* G;
   int m;
@@ -37,36 +56,41 @@ struct CholArgs {
 template <typename T>
 __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
   using O = ops<T>;
-  __shared__ T blk[NB][NB + 1];
+  extern __shared__ unsigned char sm_raw[];
+  T* pan = reinterpret_cast<T*>(sm_raw);  // panel rows [b0, m) x NB, or the diag block
+  __shared__ double s_rd[NB];             // reciprocals of the diagonal of the block
   __shared__ int s_bad;
   const int m = a.m, P = gridDim.x, cta = blockIdx.x;
-  const int gtid = cta * blockDim.x + threadIdx.x, gthreads = P * blockDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int b0 = 0; b0 < m; b0 += NB) {
     const int nb = min(NB, m - b0);
     // (1) diagonal block on CTA 0
     if (cta == 0) {
-      for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
-        int i = t / nb, l = t % nb;
-        blk[i][l] = (l <= i) ? ldg_cg(a.G + (int64_t)(b0 + i) * m + b0 + l) : O::zero();
+      T* blk = pan;  // nb x NB
+      for (int t = threadIdx.x; t < nb * NB; t += blockDim.x) {
+        int i = t / NB, l = t % NB;
+        blk[t] = (l <= i && l < nb) ? ldg_cg(a.G + (int64_t)(b0 + i) * m + b0 + l) : O::zero();
       }
       if (threadIdx.x == 0) s_bad = 0;
       __syncthreads();
       for (int jj = 0; jj < nb; ++jj) {
-        double piv = O::real(blk[jj][jj]);
+        const double piv = O::real(blk[jj * NB + jj]);
         if (!(piv > 0.0) || !isfinite(piv)) {
           if (threadIdx.x == 0) s_bad = 1;
           break;
         }
-        double c = sqrt(piv);
-        __syncthreads();
-        if (threadIdx.x == 0) blk[jj][jj] = O::make(c, 0.0);
-        for (int i = jj + 1 + threadIdx.x; i < nb; i += blockDim.x)
-          blk[i][jj] = O::scale(1.0 / c, blk[i][jj]);
-        __syncthreads();
+        const double rp = rcp64(piv);
+        const double rc = sqrt(rp);  // 1 / sqrt(piv)
+        // trailing update with the unscaled column (divide by piv), then scale column
         for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
           int i = t / nb, l = t % nb;
-          if (i > jj && l > jj && l <= i) blk[i][l] = blk[i][l] - blk[i][jj] * O::conj(blk[l][jj]);
+          if (i > jj && l > jj && l <= i)
+            blk[i * NB + l] = blk[i * NB + l] -
+                              O::scale(rp, blk[i * NB + jj] * O::conj(blk[l * NB + jj]));
         }
+        __syncthreads();
+        for (int i = jj + threadIdx.x; i < nb; i += blockDim.x)
+          blk[i * NB + jj] = (i == jj) ? O::make(piv * rc, 0.0) : O::scale(rc, blk[i * NB + jj]);
         __syncthreads();
       }
       __syncthreads();
@@ -75,86 +99,104 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
       } else {
         for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
           int i = t / nb, l = t % nb;
-          if (l <= i) a.G[(int64_t)(b0 + i) * m + b0 + l] = blk[i][l];
+          if (l <= i) a.G[(int64_t)(b0 + i) * m + b0 + l] = blk[i * NB + l];
         }
       }
       __threadfence();
     }
     if (!grid_sync(a.bar, a.status)) return;
     if (*((volatile int*)a.status) != 0) return;
-    // (2) panel rows below: X = G[r, blk] C_bb^{-H}, one thread per row
-    for (int r = b0 + nb + gtid; r < m; r += gthreads) {
-      T* row = a.G + (int64_t)r * m + b0;
-      T x[NB];
-      for (int l = 0; l < nb; ++l) {
-        T s = ldg_cg(row + l);
-        for (int t = 0; t < l; ++t)
-          s = s - x[t] * O::conj(ldg_cg(a.G + (int64_t)(b0 + l) * m + b0 + t));
-        double dl = O::real(ldg_cg(a.G + (int64_t)(b0 + l) * m + b0 + l));
-        x[l] = O::scale(1.0 / dl, s);
+    // (2) panel rows below: x C_bb^H = g, one warp per row (lane l holds entry l)
+    {
+      T* cbb = pan;  // nb x NB copy of the factored block
+      for (int t = threadIdx.x; t < nb * NB; t += blockDim.x) {
+        int i = t / NB, l = t % NB;
+        cbb[t] = (l <= i && l < nb) ? ldg_cg(a.G + (int64_t)(b0 + i) * m + b0 + l) : O::zero();
       }
-      for (int l = 0; l < nb; ++l) row[l] = x[l];
+      for (int i = threadIdx.x; i < nb; i += blockDim.x)
+        s_rd[i] = rcp64(O::real(ldg_cg(a.G + (int64_t)(b0 + i) * m + b0 + i)));
+      __syncthreads();
+      for (int r = b0 + nb + cta * nw + warp; r < m; r += P * nw) {
+        T* row = a.G + (int64_t)r * m + b0;
+        T acc = (lane < nb) ? ldg_cg(row + lane) : O::zero();
+        T x = O::zero();
+        for (int t = 0; t < nb; ++t) {
+          const T xt = shfl(O::scale(s_rd[t], acc), t);  // lane t is final at step t
+          if (lane == t) x = xt;
+          if (lane > t && lane < nb) acc = acc - xt * O::conj(cbb[lane * NB + t]);
+        }
+        if (lane < nb) row[lane] = x;
+      }
     }
     if (!grid_sync(a.bar, a.status)) return;
-    // (3) trailing update of the lower triangle: G[r][c] -= sum_t X[r][t] conj(X[c][t])
+    // (3) trailing update of the lower triangle from a shared copy of the panel
     const int r0 = b0 + nb;
-    const int64_t nt = (int64_t)(m - r0) * (m - r0);
-    for (int64_t t = gtid; t < nt; t += gthreads) {
-      int r = r0 + (int)(t / (m - r0)), c = r0 + (int)(t % (m - r0));
-      if (c > r) continue;
-      const T* xr = a.G + (int64_t)r * m + b0;
-      const T* xc = a.G + (int64_t)c * m + b0;
-      T s = O::zero();
-      for (int l = 0; l < nb; ++l) s = O::fma(ldg_cg(xr + l), O::conj(ldg_cg(xc + l)), s);
-      T* g = a.G + (int64_t)r * m + c;
-      *g = ldg_cg(g) - s;
+    if (r0 < m) {
+      const int rows = m - r0;
+      for (int t = threadIdx.x; t < rows * NB; t += blockDim.x) {
+        int i = t / NB, l = t % NB;
+        pan[t] = (l < nb) ? ldg_cg(a.G + (int64_t)(r0 + i) * m + b0 + l) : O::zero();
+      }
+      __syncthreads();
+      const int64_t nt = (int64_t)rows * (rows + 1) / 2;
+      for (int64_t t = (int64_t)cta * blockDim.x + threadIdx.x; t < nt; t += (int64_t)P * blockDim.x) {
+        // t -> (i, c) with c <= i in the packed lower triangle
+        int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+        while ((int64_t)i * (i + 1) / 2 > t) --i;
+        const int c = (int)(t - (int64_t)i * (i + 1) / 2);
+        T sacc = O::zero();
+#pragma unroll 8
+        for (int l = 0; l < NB; ++l) sacc = O::fma(pan[i * NB + l], O::conj(pan[c * NB + l]), sacc);
+        T* g = a.G + (int64_t)(r0 + i) * m + r0 + c;
+        *g = ldg_cg(g) - sacc;
+      }
     }
     if (!grid_sync(a.bar, a.status)) return;
   }
 }
 
-template <typename T>
-struct TrsmArgs {
-  const T* C;
-  T* S;
-  int m, n;
-  int* status;
-  GridBarrier* bar;
-};
-
-// S (m x n) <- C^{-1} S with C lower triangular (m x m)
-template <typename T>
-__global__ void __launch_bounds__(TPB) trsm_kernel(TrsmArgs<T> a) {
+// S (m x n) <- C^{-1} S, C lower triangular (row-major m x m).  One warp per column.
+template <typename T, bool CSMEM>
+__global__ void trsm_cols_kernel(const T* C, T* S, int m, int n) {
   using O = ops<T>;
-  const int m = a.m, n = a.n, P = gridDim.x;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = P * blockDim.x;
-  for (int b0 = 0; b0 < m; b0 += NB) {
-    const int nb = min(NB, m - b0);
-    // (1) diagonal block solve, one thread per column
-    for (int c = gtid; c < n; c += gthreads) {
-      T x[NB];
-      for (int l = 0; l < nb; ++l) {
-        T s = ldg_cg(a.S + (int64_t)(b0 + l) * n + c);
-        const T* crow = a.C + (int64_t)(b0 + l) * m + b0;
-        for (int t = 0; t < l; ++t) s = s - crow[t] * x[t];
-        x[l] = O::scale(1.0 / O::real(crow[l]), s);
-      }
-      for (int l = 0; l < nb; ++l) a.S[(int64_t)(b0 + l) * n + c] = x[l];
+  extern __shared__ unsigned char sm_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T* cl = reinterpret_cast<T*>(sm_raw);  // packed lower triangle (CSMEM)
+  double* rd = reinterpret_cast<double*>(cl + (CSMEM ? (size_t)m * (m + 1) / 2 : 0));
+  T* xs = reinterpret_cast<T*>(rd + m);
+  if (CSMEM) {
+    const int64_t tot = (int64_t)m * (m + 1) / 2;
+    for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
+      int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+      while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+      while ((int64_t)i * (i + 1) / 2 > t) --i;
+      const int l = (int)(t - (int64_t)i * (i + 1) / 2);
+      cl[t] = C[(int64_t)i * m + l];
     }
-    if (!grid_sync(a.bar, a.status)) return;
-    // (2) update of the rows below
-    const int r0 = b0 + nb;
-    const int64_t nt = (int64_t)(m - r0) * n;
-    for (int64_t t = gtid; t < nt; t += gthreads) {
-      int r = r0 + (int)(t / n), c = (int)(t % n);
-      const T* crow = a.C + (int64_t)r * m + b0;
-      T s = O::zero();
-      for (int l = 0; l < nb; ++l) s = O::fma(crow[l], ldg_cg(a.S + (int64_t)(b0 + l) * n + c), s);
-      T* dst = a.S + (int64_t)r * n + c;
-      *dst = ldg_cg(dst) - s;
-    }
-    if (!grid_sync(a.bar, a.status)) return;
   }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) rd[i] = rcp64(O::real(C[(int64_t)i * m + i]));
+  __syncthreads();
+  const int c = blockIdx.x * nw + warp;
+  if (c >= n) return;
+  T* x = xs + (size_t)warp * m;
+  auto cel = [&](int i, int l) -> T {
+    return CSMEM ? cl[(int64_t)i * (i + 1) / 2 + l] : C[(int64_t)i * m + l];
+  };
+  for (int b0 = 0; b0 < m; b0 += 32) {
+    const int i = b0 + lane;
+    const bool live = i < m;
+    T acc = live ? S[(int64_t)i * n + c] : O::zero();
+    for (int l = 0; l < b0; ++l) acc = acc - (live ? cel(i, l) : O::zero()) * x[l];
+    const int gb = min(32, m - b0);
+    for (int t = 0; t < gb; ++t) {
+      const T xt = shfl(O::scale(rd[b0 + t], acc), t);
+      if (lane == t) x[i] = xt;
+      if (lane > t && live) acc = acc - cel(i, b0 + t) * xt;
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) S[(int64_t)i * n + c] = x[i];
 }
 
 }  // namespace
@@ -162,26 +204,46 @@ __global__ void __launch_bounds__(TPB) trsm_kernel(TrsmArgs<T> a) {
 template <typename T>
 cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cudaStream_t s) {
   // FP64 is scarce per SM on this part: spread the trailing updates over many SMs
-  int P = max(1, min(num_sms, (m * m) / 128));
+  int P = std::max(1, std::min(num_sms, (m * m) / 256));
   cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
   if (err != cudaSuccess) return err;
+  size_t shm = (size_t)std::max(m, NB) * NB * sizeof(T);
+  if (shm > 48 * 1024) {
+    err = cudaFuncSetAttribute(chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)shm);
+    if (err != cudaSuccess) return err;
+  }
   note_launches(CBC_K_CHOLQR, 1);
   CholArgs<T> a{G, m, status, (GridBarrier*)bar};
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)chol_kernel<T>, dim3(P), dim3(TPB), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)chol_kernel<T>, dim3(P), dim3(TPB), args, shm, s);
 }
 
 template <typename T>
 cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* bar, int num_sms,
                             cudaStream_t s) {
-  int64_t pw = ((int64_t)m * n) / 256;
-  int P = (int)(pw < 1 ? 1 : (pw > num_sms ? num_sms : pw));
-  cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
-  if (err != cudaSuccess) return err;
+  (void)status;
+  (void)bar;
+  (void)num_sms;
+  const int nw = 2;  // warps (columns) per CTA
+  const size_t tri = (size_t)m * (m + 1) / 2 * sizeof(T);
+  const size_t rest = (size_t)m * sizeof(double) + (size_t)nw * m * sizeof(T);
   note_launches(CBC_K_CHOLQR, 1);
-  TrsmArgs<T> a{C, S, m, n, status, (GridBarrier*)bar};
-  void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)trsm_kernel<T>, dim3(P), dim3(TPB), args, 0, s);
+  cudaError_t err;
+  if (tri + rest <= 200 * 1024) {
+    err = cudaFuncSetAttribute(trsm_cols_kernel<T, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(tri + rest));
+    if (err != cudaSuccess) return err;
+    trsm_cols_kernel<T, true><<<(n + nw - 1) / nw, 32 * nw, tri + rest, s>>>(C, S, m, n);
+  } else {
+    if (rest > 48 * 1024) {
+      err = cudaFuncSetAttribute(trsm_cols_kernel<T, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rest);
+      if (err != cudaSuccess) return err;
+    }
+    trsm_cols_kernel<T, false><<<(n + nw - 1) / nw, 32 * nw, rest, s>>>(C, S, m, n);
+  }
+  return cudaGetLastError();
 }
 
 template cudaError_t cholesky_lower<double>(double*, int, int*, void*, int, cudaStream_t);

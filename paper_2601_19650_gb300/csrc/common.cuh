@@ -77,39 +77,58 @@ __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
   return *((volatile const unsigned int*)p);
 }
 
-// returns false if the barrier timed out (status already set)
+// returns false if the barrier timed out (status already set).  Arrival is a release
+// add at GPU scope, waiting an acquire load of the generation word.
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    unsigned int g = ld_volatile_u32(&bar->gen);
-    __threadfence();
-    unsigned int arrived = atomicAdd(&bar->count, 1u);
+    unsigned int g, arrived;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&bar->gen) : "memory");
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;"
+                 : "=r"(arrived)
+                 : "l"(&bar->count)
+                 : "memory");
     if (arrived == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&bar->count) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->gen) : "memory");
     } else {
-      long long spins = 0;
-      while (ld_volatile_u32(&bar->gen) == g) {
-        __nanosleep(64);
-        if (++spins > (1ll << 25)) {  // ~2 s at >= 64 ns per spin
+      long long t0 = clock64();
+      unsigned int cur;
+      while (true) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
+        if (cur != g) break;
+        if (clock64() - t0 > 4000000000LL) {  // ~2 s
           set_status(status, CBC_ERR_TIMEOUT);
           ok = 0;
           break;
         }
-        if ((spins & 1023) == 0 && *((volatile int*)status) == CBC_ERR_TIMEOUT) {
+        if (*((volatile int*)status) == CBC_ERR_TIMEOUT) {
           ok = 0;
           break;
         }
       }
     }
-    __threadfence();
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     s_ok = ok;
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// 1/x for finite nonzero x by Newton-Raphson on f(r) = 1/r - x, r <- r (2 - x r),
+// started from the single-precision reciprocal of the mantissa (the exponent is split
+// off with frexp so any double works): ~23 -> 46 -> 92 correct bits.  Used where a
+// long dependent chain of FP64 divisions would otherwise dominate the latency.
+__device__ __forceinline__ double rcp64(double x) {
+  int ex;
+  double f = frexp(x, &ex);
+  double r = (double)__frcp_rn((float)f);
+  r = fma(r, fma(-f, r, 1.0), r);
+  r = fma(r, fma(-f, r, 1.0), r);
+  return ldexp(r, -ex);
 }
 
 // warp / block reductions -----------------------------------------------------------

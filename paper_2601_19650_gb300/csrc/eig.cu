@@ -9,13 +9,18 @@
 //      cooperative launch; rows of K are dealt round-robin to the CTAs so the shrinking
 //      trailing block stays balanced, two bounded grid barriers per column.  FP64 work
 //      is spread over many SMs because one GB300 SM retires only ~2 DFMA per clock.
-//   2. All eigenvalues of T by Sturm-count bisection, one thread per eigenvalue.
-//   3. The rank rule (max_bond, relative floor, tolerance) on the device.
-//   4. Eigenvectors of T for the kept eigenvalues by inverse iteration (LU with partial
-//      pivoting of T - sigma I), modified Gram-Schmidt inside clusters of close
-//      eigenvalues, Rayleigh-quotient eigenvalues.
+//   2. Estimates of all eigenvalues of T by single-precision Sturm-count multisection,
+//      one warp per eigenvalue (a dependent chain of FP64 divisions per Sturm step is
+//      slow on this part; the estimates only need to separate the eigenvalues).
+//   3. Eigenvectors of T for the candidates (the kmax largest) by FP64 inverse
+//      iteration seeded with those estimates (one LU, six solves); eigenvalues =
+//      Rayleigh quotients.
+//   4. The rank rule (max_bond, relative floor, tolerance) on the refined eigenvalues,
+//      with the discarded weight taken as trace(T) minus the kept eigenvalues.
 //   5. Back transformation u = H_0 H_1 ... H_{m-2} x, one warp per kept eigenvector.
 #include <float.h>
+
+#include <algorithm>
 
 #include "kernels.cuh"
 #include "planner.h"
@@ -94,11 +99,12 @@ __device__ void householder_col(const TriArgs<T>& a, int j, double* sh) {
   } else {
     double nrm = sqrt(ar * ar + ai * ai + xn2);
     beta = (ar >= 0.0) ? -nrm : nrm;
-    tau = O::make((beta - ar) / beta, -ai / beta);
+    const double ib = rcp64(beta);
+    tau = O::make((beta - ar) * ib, -ai * ib);
     // scale = 1 / (alpha - beta)
     double zr = ar - beta, zi = ai;
-    double den = zr * zr + zi * zi;
-    scale = O::make(zr / den, -zi / den);
+    const double iden = rcp64(zr * zr + zi * zi);
+    scale = O::make(zr * iden, -zi * iden);
   }
   T* vb = a.vbuf + (j & 1) * m;
   T* vs = a.V + (int64_t)j * m;
@@ -192,82 +198,406 @@ __global__ void __launch_bounds__(TPB) tridiag_kernel(TriArgs<T> a) {
   }
 }
 
-// ---- Sturm count: number of eigenvalues of T smaller than x -------------------------
-__device__ __forceinline__ int sturm_count(const double* d, const double* e, int m, double x,
-                                           double pivmin) {
+// ---- tridiagonalisation with the rows in shared memory -----------------------------
+// Same reduction as tridiag_kernel, for m small enough that every CTA keeps its rows
+// in shared memory.  Column j needs two exchanges: the Householder vector v_j from the
+// CTA that owns row j, and the global sum v^H p.  The first is a flag written with
+// release semantics by the owner (which updates row j first, then publishes v_j and
+// only then updates its other rows); the second is an arrival counter per column.
+// Every wait is bounded.
+template <typename T>
+struct Tri2Args {
+  T* A;
+  int m;
+  double* d;
+  double* e;
+  T* tau;
+  T* V;              // (m-1) x m, row j = v_j
+  T* p2;             // 2 x m
+  double* dot;       // m x 2
+  unsigned* cnt;     // m arrival counters
+  unsigned* vflag;   // m publication flags
+  int* status;
+};
+
+__device__ __forceinline__ bool wait_geq(const unsigned* p, unsigned target, int* status) {
+  long long t0 = clock64();
+  unsigned cur;
+  while (true) {
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(p) : "memory");
+    if (cur >= target) return true;
+    if (clock64() - t0 > 4000000000LL) {
+      set_status(status, CBC_ERR_TIMEOUT);
+      return false;
+    }
+    if (*((volatile int*)status) == CBC_ERR_TIMEOUT) return false;
+  }
+}
+
+template <typename T>
+__device__ void householder_row(const Tri2Args<T>& a, const T* row, int j, double* sh) {
+  using O = ops<T>;
+  const int m = a.m;
+  double xn2 = 0.0;
+  for (int c = j + 2 + threadIdx.x; c < m; c += blockDim.x) xn2 += O::abs2(row[c]);
+  xn2 = block_sum(xn2, sh);
+  const T alpha = O::conj(row[j + 1]);
+  const double ar = O::real(alpha), ai = O::imag(alpha);
+  T tau, scale;
+  double beta;
+  const bool trivial = (xn2 == 0.0 && ai == 0.0);
+  if (trivial) {
+    tau = O::zero();
+    beta = ar;
+    scale = O::zero();
+  } else {
+    const double nrm = sqrt(ar * ar + ai * ai + xn2);
+    beta = (ar >= 0.0) ? -nrm : nrm;
+    const double ib = rcp64(beta);
+    tau = O::make((beta - ar) * ib, -ai * ib);
+    const double zr = ar - beta, zi = ai;
+    const double iden = rcp64(zr * zr + zi * zi);
+    scale = O::make(zr * iden, -zi * iden);
+  }
+  T* vs = a.V + (int64_t)j * m;
+  for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x)
+    vs[c] = (c == j + 1) ? O::one() : (trivial ? O::zero() : O::conj(row[c]) * scale);
+  if (threadIdx.x == 0) {
+    a.tau[j] = tau;
+    a.e[j] = beta;
+    a.d[j] = O::real(row[j]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("st.release.gpu.global.u32 [%0], 1;" ::"l"(a.vflag + j) : "memory");
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a) {
+  using O = ops<T>;
+  extern __shared__ unsigned char sm_raw[];
+  __shared__ double sh[64];
+  __shared__ int s_ok;
+  const int m = a.m, P = gridDim.x, cta = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int nr = (m - cta + P - 1) / P;  // own rows r = cta + P t
+  T* rows = reinterpret_cast<T*>(sm_raw);
+  T* vsm = rows + (size_t)nr * m;
+  T* psm = vsm + m;
+  for (int t = 0; t < nr; ++t)
+    for (int c = threadIdx.x; c < m; c += blockDim.x)
+      rows[(size_t)t * m + c] = a.A[(int64_t)(cta + P * t) * m + c];
+  __syncthreads();
+  if (m == 1) {
+    if (cta == 0 && threadIdx.x == 0) a.d[0] = O::real(rows[0]);
+    return;
+  }
+  if (cta == 0) householder_row(a, rows, 0, sh);
+  for (int j = 0; j < m - 1; ++j) {
+    // v_j from its owner
+    if (threadIdx.x == 0) s_ok = wait_geq(a.vflag + j, 1u, a.status) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) return;
+    const T* vg = a.V + (int64_t)j * m;
+    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) vsm[c] = ldcg(vg + c);
+    const T tau = ldcg(a.tau + j);
+    __syncthreads();
+    // phase B: p_r = tau sum_{c>j} A[r][c] v_c for own rows r > j
+    int t0 = (j + 1 - cta + P - 1) / P;
+    if (t0 < 0) t0 = 0;
+    double dre = 0.0, dim = 0.0;
+    T* pg = a.p2 + (j & 1) * m;
+    for (int t = t0 + warp; t < nr; t += nw) {
+      const int r = cta + P * t;
+      const T* row = rows + (size_t)t * m;
+      T acc = O::zero();
+      for (int c = j + 1 + lane; c < m; c += 32) acc = O::fma(row[c], vsm[c], acc);
+      if constexpr (O::cplx) {
+        acc = zdbl{warp_sum(O::real(acc)), warp_sum(O::imag(acc))};
+      } else {
+        acc = warp_sum(acc);
+      }
+      const T pr = tau * acc;
+      if (lane == 0) {
+        pg[r] = pr;
+        const T vd = O::conj(vsm[r]) * pr;
+        dre += O::real(vd);
+        dim += O::imag(vd);
+      }
+    }
+    dre = block_sum(dre, sh);
+    if constexpr (O::cplx) dim = block_sum(dim, sh);
+    if (threadIdx.x == 0) {
+      atomicAdd(a.dot + 2 * j, dre);
+      if constexpr (O::cplx) atomicAdd(a.dot + 2 * j + 1, dim);
+      asm volatile("fence.acq_rel.gpu;" ::: "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.cnt + j) : "memory");
+      s_ok = wait_geq(a.cnt + j, (unsigned)P, a.status) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    // phase C: own rows -= v w^H + w v^H with w = p - (conj(tau)/2)(v^H p) v
+    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) psm[c] = ldcg(pg + c);
+    const T sv = O::make(__ldcg(a.dot + 2 * j), __ldcg(a.dot + 2 * j + 1));
+    const T coef = O::scale(-0.5, O::conj(tau) * sv);
+    __syncthreads();
+    auto update_row = [&](int t, int c0, int cstep) {
+      const int r = cta + P * t;
+      T* row = rows + (size_t)t * m;
+      const T vr = vsm[r];
+      const T wr = O::fma(coef, vr, psm[r]);
+      for (int c = j + 1 + c0; c < m; c += cstep) {
+        const T vc = vsm[c];
+        const T wc = O::fma(coef, vc, psm[c]);
+        row[c] = row[c] - O::fma(vr, O::conj(wc), wr * O::conj(vc));
+      }
+    };
+    int tstart = t0;
+    if (j + 1 < m - 1 && (j + 1) % P == cta) {
+      // the next column's owner: update that row with the whole CTA, publish v_{j+1}
+      update_row(t0, threadIdx.x, blockDim.x);
+      __syncthreads();
+      householder_row(a, rows + (size_t)t0 * m, j + 1, sh);
+      tstart = t0 + 1;
+    }
+    for (int t = tstart + warp; t < nr; t += nw) update_row(t, lane, 32);
+    if (j + 1 == m - 1 && (m - 1) % P == cta) {
+      __syncthreads();
+      if (threadIdx.x == 0) a.d[m - 1] = O::real(rows[(size_t)((m - 1 - cta) / P) * m + (m - 1)]);
+    }
+    __syncthreads();
+  }
+}
+
+// ---- eigenvalues of T: single-precision multisection, one warp per eigenvalue --------
+// The values only seed the shifts of the FP64 inverse iteration below, whose Rayleigh
+// quotients are the eigenvalues used for the rank rule.
+__device__ __forceinline__ int sturm32(const float* dd, const float* e2, int m, float x,
+                                       float pivmin) {
   int cnt = 0;
-  double q = d[0] - x;
-  if (q < 0.0) cnt++;
+  float q = dd[0] - x;
+  if (q < 0.f) cnt++;
   for (int i = 1; i < m; ++i) {
-    if (fabs(q) < pivmin) q = -pivmin;
-    q = (d[i] - x) - (e[i - 1] * e[i - 1]) / q;
-    if (q < 0.0) cnt++;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    q = (dd[i] - x) - __fdividef(e2[i - 1], q);
+    if (q < 0.f) cnt++;
   }
   return cnt;
 }
 
-struct BisArgs {
-  const double* d;
-  const double* e;
-  double* e2;  // scratch m
-  int m;
-  double* lam;  // out, descending
-};
-
-__global__ void bisect_kernel(BisArgs b) {
-  __shared__ double s_lo, s_hi, s_piv;
-  const int m = b.m;
+__global__ void bisect32_kernel(const double* d, const double* e, int m, float* lam32) {
+  extern __shared__ float shf[];
+  float* dd = shf;
+  float* e2 = shf + m;
+  __shared__ float s_lo, s_hi, s_piv;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    dd[i] = (float)d[i];
+    e2[i] = (i < m - 1) ? (float)(e[i] * e[i]) : 0.f;
+  }
   if (threadIdx.x == 0) {
     double lo = DBL_MAX, hi = -DBL_MAX, emax = 0.0;
     for (int i = 0; i < m; ++i) {
       double r = 0.0;
-      if (i > 0) r += fabs(b.e[i - 1]);
-      if (i < m - 1) r += fabs(b.e[i]);
-      lo = fmin(lo, b.d[i] - r);
-      hi = fmax(hi, b.d[i] + r);
-      if (i < m - 1) emax = fmax(emax, b.e[i] * b.e[i]);
+      if (i > 0) r += fabs(e[i - 1]);
+      if (i < m - 1) r += fabs(e[i]);
+      lo = fmin(lo, d[i] - r);
+      hi = fmax(hi, d[i] + r);
+      if (i < m - 1) emax = fmax(emax, e[i] * e[i]);
     }
     double span = fmax(fabs(lo), fabs(hi));
-    s_lo = lo - 1e-14 * span - DBL_MIN;
-    s_hi = hi + 1e-14 * span + DBL_MIN;
-    s_piv = DBL_MIN * fmax(1.0, emax);
+    s_lo = (float)(lo - 1e-6 * span) - FLT_MIN;
+    s_hi = (float)(hi + 1e-6 * span) + FLT_MIN;
+    s_piv = FLT_MIN * (float)fmax(1.0, emax);
   }
   __syncthreads();
-  int jj = blockIdx.x * blockDim.x + threadIdx.x;  // descending index
+  const int lane = threadIdx.x & 31;
+  const int jj = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);  // descending index
   if (jj >= m) return;
-  const int target = m - 1 - jj;                    // ascending index
-  double lo = s_lo, hi = s_hi;
-  const double span = fmax(fabs(lo), fabs(hi));
-  const double atol = 2e-12 * span + 4.0 * s_piv;
-  for (int it = 0; it < 80 && (hi - lo) > atol; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (sturm_count(b.d, b.e, m, mid, s_piv) <= target)
-      lo = mid;
-    else
-      hi = mid;
+  const int target = m - 1 - jj;
+  float lo = s_lo, hi = s_hi;
+  for (int round = 0; round < 12; ++round) {
+    const float x = lo + (hi - lo) * (float)(lane + 1) * (1.f / 33.f);
+    const int cnt = sturm32(dd, e2, m, x, s_piv);
+    const unsigned bits = __ballot_sync(0xffffffffu, cnt <= target);
+    const int nle = __popc(bits);
+    const float xl = __shfl_sync(0xffffffffu, x, max(nle - 1, 0));
+    const float xh = __shfl_sync(0xffffffffu, x, min(nle, 31));
+    if (nle > 0) lo = xl;
+    if (nle < 32) hi = xh;
+    if (hi - lo <= 2e-7f * fmaxf(fabsf(lo), fabsf(hi)) + s_piv) break;
   }
-  b.lam[jj] = 0.5 * (lo + hi);
+  if (lane == 0) lam32[jj] = 0.5f * (lo + hi);
 }
 
-// rank rule on the (descending) eigenvalues
-__global__ void rank_kernel(const double* lam, int m, int kmax, long long max_bond, double tol,
-                            double floor_rel, int* k_dev) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double l0 = lam[0];
-  int k;
-  if (!(l0 > 0.0)) {
-    k = 1;
-  } else {
+// ---- eigenvectors of T by FP64 inverse iteration ----------------------------------
+// One thread per kept candidate.  The LU of T - sigma I with partial pivoting (the
+// layout of LAPACK's tridiagonal factorisation) lives in shared memory, [i][thread],
+// with the pivots stored as reciprocals so the solves are division free.  Candidates
+// whose single-precision eigenvalues lie within 1e-5 of the spectral radius of each
+// other form a cluster that the thread of its first member computes in order, each new
+// vector orthogonalised against the earlier ones.  The eigenvalue is the FP64 Rayleigh
+// quotient of the converged vector.
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+struct InvArgs {
+  const double* d;
+  const double* e;
+  const float* lam32;  // descending
+  int m;
+  int kmax;            // candidates j < kmax
+  double* X;           // m x kmax (row i, column j)
+  double* rq;          // [kmax] Rayleigh quotients
+};
+
+__global__ void invit_kernel(InvArgs a) {
+  extern __shared__ double shd[];
+  const int tpb = blockDim.x, tid = threadIdx.x;
+  const int m = a.m, K = a.kmax;
+  double* dl = shd;
+  double* di = dl + (size_t)m * tpb;   // reciprocal pivots
+  double* du = di + (size_t)m * tpb;
+  double* du2 = du + (size_t)m * tpb;
+  double* b = du2 + (size_t)m * tpb;
+  unsigned char* piv = reinterpret_cast<unsigned char*>(b + (size_t)m * tpb);
+#define SH(arr, i) arr[(size_t)(i) * tpb + tid]
+  const int jj = blockIdx.x * tpb + tid;
+  if (jj >= K) return;
+  const double span = fmax(fabs((double)a.lam32[0]), fabs((double)a.lam32[m - 1])) + DBL_MIN;
+  // Each solve shrinks the components along eigenvectors at distance delta by about
+  // |lambda - sigma| / delta with |lambda - sigma| ~ 1e-7 span (single-precision
+  // shifts); six solves reach FP64 accuracy for delta >= 1e-5 span.  Closer pairs are
+  // handled as a cluster with explicit orthogonalisation.
+  const double ortol = 1e-5 * span;
+  if (jj > 0 && (double)a.lam32[jj - 1] - (double)a.lam32[jj] <= ortol) return;
+  int cend = jj + 1;
+  while (cend < K && (double)a.lam32[cend - 1] - (double)a.lam32[cend] <= ortol) ++cend;
+  const double eps = 2.220446049250313e-16;
+  const double tiny = eps * span;
+  double prev_sigma = 0.0;
+  for (int jc = jj; jc < cend; ++jc) {
+    double sigma = (double)a.lam32[jc];
+    if (jc > jj && prev_sigma - sigma < 1e-10 * span) sigma = prev_sigma - 1e-10 * span;
+    prev_sigma = sigma;
+    // LU with partial pivoting of T - sigma I
+    double dcur = a.d[0] - sigma;
+    double ucur = (m > 1) ? a.e[0] : 0.0;  // superdiagonal entry of the current row
+    for (int i = 0; i < m - 1; ++i) {
+      const double li = a.e[i];
+      const double dn = a.d[i + 1] - sigma;
+      const double un = (i + 1 < m - 1) ? a.e[i + 1] : 0.0;
+      if (fabs(dcur) >= fabs(li)) {
+        double dv = (fabs(dcur) < tiny) ? ((dcur < 0.0) ? -tiny : tiny) : dcur;
+        double r = rcp64(dv);
+        double f = li * r;
+        SH(piv, i) = 0;
+        SH(dl, i) = f;
+        SH(di, i) = r;
+        SH(du, i) = ucur;
+        SH(du2, i) = 0.0;
+        dcur = dn - f * ucur;
+        ucur = un;
+      } else {
+        double r = rcp64(li);
+        double f = dcur * r;
+        SH(piv, i) = 1;
+        SH(dl, i) = f;
+        SH(di, i) = r;
+        SH(du, i) = dn;
+        SH(du2, i) = un;
+        dcur = ucur - f * dn;
+        ucur = -f * un;
+      }
+    }
+    {
+      double dv = (fabs(dcur) < tiny) ? ((dcur < 0.0) ? -tiny : tiny) : dcur;
+      SH(di, m - 1) = rcp64(dv);
+    }
+    for (int i = 0; i < m; ++i) {
+      uint32_t h = hash32((uint32_t)(i * 7919 + jc * 104729 + 17));
+      SH(b, i) = ((double)(h & 0xffffff) / 16777216.0) - 0.5;
+    }
+    for (int it = 0; it < 6; ++it) {
+      // forward: L y = P b
+      double carry = SH(b, 0);
+      for (int i = 0; i < m - 1; ++i) {
+        double nxt = SH(b, i + 1);
+        if (SH(piv, i) == 0) {
+          SH(b, i) = carry;
+          carry = nxt - SH(dl, i) * carry;
+        } else {
+          SH(b, i) = nxt;
+          carry = carry - SH(dl, i) * nxt;
+        }
+      }
+      SH(b, m - 1) = carry;
+      // back: U x = y
+      double x1 = 0.0, x2 = 0.0;
+      for (int i = m - 1; i >= 0; --i) {
+        double sv = SH(b, i) - SH(du, i) * x1 - SH(du2, i) * x2;
+        if (i == m - 1) sv = SH(b, i);
+        double xi = sv * SH(di, i);
+        SH(b, i) = xi;
+        x2 = x1;
+        x1 = xi;
+      }
+      for (int q = jj; q < jc; ++q) {
+        double dotv = 0.0;
+        for (int i = 0; i < m; ++i) dotv += a.X[(size_t)i * K + q] * SH(b, i);
+        for (int i = 0; i < m; ++i) SH(b, i) -= dotv * a.X[(size_t)i * K + q];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < m; ++i) nrm += SH(b, i) * SH(b, i);
+      double inv = (nrm > 0.0) ? rcp64(sqrt(nrm)) : 0.0;
+      for (int i = 0; i < m; ++i) SH(b, i) *= inv;
+    }
+    double rqv = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double xi = SH(b, i);
+      double tx = a.d[i] * xi;
+      if (i > 0) tx += a.e[i - 1] * SH(b, i - 1);
+      if (i < m - 1) tx += a.e[i] * SH(b, i + 1);
+      rqv += xi * tx;
+      a.X[(size_t)i * K + jc] = xi;
+    }
+    a.rq[jc] = rqv;
+  }
+#undef SH
+}
+
+// rank rule on the Rayleigh quotients of the candidates; the discarded weight is the
+// exact trace of T minus the kept eigenvalues.  Writes k and the full eigenvalue list.
+__global__ void rank_kernel(const double* d, const double* rq, const float* lam32, int m,
+                            int kmax, long long max_bond, double tol, double floor_rel,
+                            int* k_dev, double* lam) {
+  __shared__ double s_tr;
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < m; ++i) tr += d[i];
+    s_tr = tr;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) lam[j] = (j < kmax) ? rq[j] : (double)lam32[j];
+  if (threadIdx.x != 0) return;
+  const double l0 = rq[0];
+  int k = 1;
+  if (l0 > 0.0) {
     k = 0;
-    while (k < m && lam[k] > floor_rel * l0) ++k;
+    while (k < kmax && rq[k] > floor_rel * l0) ++k;
     if (tol > 0.0) {
-      double total = 0.0;
-      for (int j = 0; j < m; ++j) total += fmax(lam[j], 0.0);
+      const double total = fmax(s_tr, 0.0);
       double tail = total;
       int kt = 0;
-      // smallest kt with sum_{j>=kt} <= tol^2 total
-      while (kt < m && tail > tol * tol * total) {
-        tail -= fmax(lam[kt], 0.0);
+      while (kt < kmax && tail > tol * tol * total) {
+        tail -= fmax(rq[kt], 0.0);
         ++kt;
       }
       if (kt < 1) kt = 1;
@@ -280,166 +610,77 @@ __global__ void rank_kernel(const double* lam, int m, int kmax, long long max_bo
   *k_dev = k;
 }
 
-// ---- inverse iteration for the kept eigenvalues ------------------------------------
-struct InvArgs {
-  const double* d;
-  const double* e;
-  const double* lamb;  // bisection values (read only: cluster bounds and shifts)
-  double* lam;         // out: Rayleigh quotients for kept j, bisection values otherwise
-  int m;
-  const int* k_dev;
-  double* X;    // m x kmax (row i, column jj), eigenvectors of T
-  int kmax;
-  // per-thread scratch, layout [i][jj]
-  double *dl, *dd, *du, *du2, *b;
-  unsigned char* piv;
-};
-
-__device__ __forceinline__ uint32_t hash32(uint32_t x) {
-  x ^= x >> 16;
-  x *= 0x7feb352dU;
-  x ^= x >> 15;
-  x *= 0x846ca68bU;
-  x ^= x >> 16;
-  return x;
-}
-
-__global__ void inverse_iter_kernel(InvArgs a) {
-  const int m = a.m, K = a.kmax;
-  const int k = *a.k_dev;
-  const int jj = blockIdx.x * blockDim.x + threadIdx.x;
-  if (jj >= m) return;
-  if (jj >= k) {
-    a.lam[jj] = a.lamb[jj];
-    return;
-  }
-  const double span = fmax(fabs(a.lamb[0]), fabs(a.lamb[m - 1])) + DBL_MIN;
-  const double ortol = 1e-3 * span;
-  // only the first member of a cluster works; it computes the whole cluster in order
-  if (jj > 0 && a.lamb[jj - 1] - a.lamb[jj] <= ortol) return;
-  int cend = jj + 1;
-  while (cend < k && a.lamb[cend - 1] - a.lamb[cend] <= ortol) ++cend;
-#define AT(arr, i) arr[(int64_t)(i) * K + jj]
-  const double eps = 2.220446049250313e-16;
-  for (int jc = jj; jc < cend; ++jc) {
-    double sigma = a.lamb[jc];
-    // perturb members of a cluster apart so their shifts differ
-    if (jc > jj) {
-      double prev = a.lamb[jc - 1];
-      if (prev - sigma < 10.0 * eps * span) sigma = prev - 10.0 * eps * span;
-    }
-    // LU with partial pivoting of T - sigma I (dgttrf layout)
-    for (int i = 0; i < m; ++i) {
-      AT(a.dd, i) = a.d[i] - sigma;
-      if (i < m - 1) {
-        AT(a.dl, i) = a.e[i];
-        AT(a.du, i) = a.e[i];
-      }
-    }
-    for (int i = 0; i < m - 1; ++i) {
-      double di = AT(a.dd, i), li = AT(a.dl, i);
-      if (fabs(di) >= fabs(li)) {
-        AT(a.piv, i) = 0;
-        double f = (di != 0.0) ? li / di : 0.0;
-        AT(a.dl, i) = f;
-        AT(a.dd, i + 1) -= f * AT(a.du, i);
-        if (i < m - 2) AT(a.du2, i) = 0.0;
-      } else {
-        AT(a.piv, i) = 1;
-        double f = di / li;
-        AT(a.dd, i) = li;
-        AT(a.dl, i) = f;
-        double tmp = AT(a.du, i);
-        AT(a.du, i) = AT(a.dd, i + 1);
-        AT(a.dd, i + 1) = tmp - f * AT(a.dd, i + 1);
-        if (i < m - 2) {
-          AT(a.du2, i) = AT(a.du, i + 1);
-          AT(a.du, i + 1) = -f * AT(a.du, i + 1);
-        }
-      }
-    }
-    const double tiny = eps * span;
-    for (int i = 0; i < m; ++i)
-      if (fabs(AT(a.dd, i)) < tiny) AT(a.dd, i) = (AT(a.dd, i) < 0.0) ? -tiny : tiny;
-    // start vector
-    for (int i = 0; i < m; ++i) {
-      uint32_t h = hash32((uint32_t)(i * 7919 + jc * 104729 + 17));
-      AT(a.b, i) = ((double)(h & 0xffffff) / 16777216.0) - 0.5;
-    }
-    for (int it = 0; it < 4; ++it) {
-      // forward: L y = P b (in place in b)
-      for (int i = 0; i < m - 1; ++i) {
-        if (AT(a.piv, i) == 0) {
-          AT(a.b, i + 1) -= AT(a.dl, i) * AT(a.b, i);
-        } else {
-          double t = AT(a.b, i);
-          AT(a.b, i) = AT(a.b, i + 1);
-          AT(a.b, i + 1) = t - AT(a.dl, i) * AT(a.b, i + 1);
-        }
-      }
-      // back: U x = y
-      for (int i = m - 1; i >= 0; --i) {
-        double s = AT(a.b, i);
-        if (i < m - 1) s -= AT(a.du, i) * AT(a.b, i + 1);
-        if (i < m - 2) s -= AT(a.du2, i) * AT(a.b, i + 2);
-        AT(a.b, i) = s / AT(a.dd, i);
-      }
-      // orthogonalise against earlier members of the cluster (their vectors are in X)
-      for (int q = jj; q < jc; ++q) {
-        double dotv = 0.0;
-        for (int i = 0; i < m; ++i) dotv += a.X[(int64_t)i * K + q] * AT(a.b, i);
-        for (int i = 0; i < m; ++i) AT(a.b, i) -= dotv * a.X[(int64_t)i * K + q];
-      }
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) nrm += AT(a.b, i) * AT(a.b, i);
-      nrm = sqrt(nrm);
-      double inv = (nrm > 0.0) ? 1.0 / nrm : 0.0;
-      for (int i = 0; i < m; ++i) AT(a.b, i) *= inv;
-    }
-    // store and Rayleigh quotient
-    double rq = 0.0;
-    for (int i = 0; i < m; ++i) {
-      double xi = AT(a.b, i);
-      double tx = a.d[i] * xi;
-      if (i > 0) tx += a.e[i - 1] * AT(a.b, i - 1);
-      if (i < m - 1) tx += a.e[i] * AT(a.b, i + 1);
-      rq += xi * tx;
-      a.X[(int64_t)i * K + jc] = xi;
-    }
-    a.lam[jc] = rq;
-  }
-#undef AT
-}
-
 // ---- back transformation: U[:, jj] = H_0 ... H_{m-2} X[:, jj] ------------------------
-template <typename T>
-__global__ void backtransform_kernel(const T* V, const T* tau, const double* X, int m, int kmax,
-                                     const int* k_dev, T* U) {
+// One warp per kept eigenvector, one warp per CTA so the FP64 work of the reflector
+// applications spreads over as many SMs as there are vectors.
+template <typename T, int RB>
+__global__ void __launch_bounds__(32) backtransform_kernel(const T* V, const T* tau,
+                                                           const double* X, int m, int kmax,
+                                                           const int* k_dev, T* U) {
   using O = ops<T>;
   extern __shared__ unsigned char smem_raw[];
-  T* u_all = reinterpret_cast<T*>(smem_raw);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int jj = blockIdx.x * (blockDim.x >> 5) + warp;
+  T* u = reinterpret_cast<T*>(smem_raw);
+  const int lane = threadIdx.x & 31;
+  const int jj = blockIdx.x;
   const int k = *k_dev;
   if (jj >= k) return;
-  T* u = u_all + warp * m;
   for (int i = lane; i < m; i += 32) u[i] = O::make(X[(int64_t)i * kmax + jj], 0.0);
   __syncwarp();
-  for (int j = m - 2; j >= 0; --j) {
-    const T* vj = V + (int64_t)j * m;
-    T t = tau[j];
-    if (O::real(t) == 0.0 && O::imag(t) == 0.0) continue;
-    T s = O::zero();
-    for (int r = j + 1 + lane; r < m; r += 32) s = O::fma(O::conj(vj[r]), u[r], s);
-    if constexpr (O::cplx) {
-      s = zdbl{warp_sum(O::real(s)), warp_sum(O::imag(s))};
-    } else {
-      s = warp_sum(s);
+  if constexpr (RB == 0) {  // large m: stream the reflectors from memory
+    for (int j = m - 2; j >= 0; --j) {
+      const T* vj = V + (int64_t)j * m;
+      const T t = tau[j];
+      T sacc = O::zero();
+      for (int r = j + 1 + lane; r < m; r += 32) sacc = O::fma(O::conj(vj[r]), u[r], sacc);
+      if constexpr (O::cplx) {
+        sacc = zdbl{warp_sum(O::real(sacc)), warp_sum(O::imag(sacc))};
+      } else {
+        sacc = warp_sum(sacc);
+      }
+      const T ts = t * sacc;
+      __syncwarp();
+      for (int r = j + 1 + lane; r < m; r += 32) u[r] = u[r] - vj[r] * ts;
+      __syncwarp();
     }
-    T ts = t * s;
+    for (int i = lane; i < m; i += 32) U[(int64_t)i * kmax + jj] = u[i];
+    return;
+  }
+  // each lane keeps its RB elements of the current reflector in registers and loads
+  // the next reflector while the current one is applied (m <= 32 RB)
+  constexpr int RBX = RB > 0 ? RB : 1;
+  T vcur[RBX], vnext[RBX];
+  auto load_row = [&](int j, T (&dst)[RBX]) {
+#pragma unroll
+    for (int q = 0; q < RBX; ++q) {
+      const int r = lane + 32 * q;
+      dst[q] = (j >= 0 && r > j && r < m) ? V[(int64_t)j * m + r] : O::zero();
+    }
+  };
+  load_row(m - 2, vcur);
+  for (int j = m - 2; j >= 0; --j) {
+    load_row(j - 1, vnext);
+    const T t = tau[j];
+    T sacc = O::zero();
+#pragma unroll
+    for (int q = 0; q < RBX; ++q) {
+      const int r = lane + 32 * q;
+      if (r < m) sacc = O::fma(O::conj(vcur[q]), u[r], sacc);
+    }
+    if constexpr (O::cplx) {
+      sacc = zdbl{warp_sum(O::real(sacc)), warp_sum(O::imag(sacc))};
+    } else {
+      sacc = warp_sum(sacc);
+    }
+    const T ts = t * sacc;
     __syncwarp();
-    for (int r = j + 1 + lane; r < m; r += 32) u[r] = u[r] - vj[r] * ts;
+#pragma unroll
+    for (int q = 0; q < RBX; ++q) {
+      const int r = lane + 32 * q;
+      if (r < m) u[r] = u[r] - vcur[q] * ts;
+    }
     __syncwarp();
+#pragma unroll
+    for (int q = 0; q < RBX; ++q) vcur[q] = vnext[q];
   }
   for (int i = lane; i < m; i += 32) U[(int64_t)i * kmax + jj] = u[i];
 }
@@ -454,17 +695,17 @@ size_t eig_workspace_bytes(int m, int kmax, bool cplx) {
   size_t b = 0;
   b += align256(sizeof(double) * m);                 // d
   b += align256(sizeof(double) * m);                 // e
-  b += align256(sizeof(double) * m);                 // e2
-  b += align256(sizeof(double) * m);                 // lamb
+  b += align256(sizeof(float) * m);                  // lam32
+  b += align256(sizeof(double) * m);                 // rq
   b += align256(ts * m);                             // tau
   b += align256(ts * (size_t)m * m);                 // V
   b += align256(ts * 2 * m);                         // vbuf
-  b += align256(ts * m);                             // p
+  b += align256(ts * 2 * m);                         // p (two buffers)
   b += align256(sizeof(double) * 4);                 // dot
   b += align256(sizeof(GridBarrier));                // barrier
   b += align256(sizeof(double) * (size_t)m * kmax);  // X
-  b += 5 * align256(sizeof(double) * (size_t)m * kmax);  // dl dd du du2 b
-  b += align256((size_t)m * kmax);                   // piv
+  b += align256(sizeof(double) * 2 * m);             // per-column dot accumulators
+  b += align256(sizeof(unsigned) * 2 * m);           // counters and flags
   return b;
 }
 
@@ -481,59 +722,75 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   const size_t ts = sizeof(T);
   double* d = (double*)take(sizeof(double) * m);
   double* e = (double*)take(sizeof(double) * m);
-  double* e2 = (double*)take(sizeof(double) * m);
-  double* lamb = (double*)take(sizeof(double) * m);
+  float* lam32 = (float*)take(sizeof(float) * m);
+  double* rq = (double*)take(sizeof(double) * m);
   T* tau = (T*)take(ts * m);
   T* V = (T*)take(ts * (size_t)m * m);
   T* vbuf = (T*)take(ts * 2 * m);
-  T* p = (T*)take(ts * m);
+  T* p = (T*)take(ts * 2 * m);
   double* dot = (double*)take(sizeof(double) * 4);
   GridBarrier* bar = (GridBarrier*)take(sizeof(GridBarrier));
   double* X = (double*)take(sizeof(double) * (size_t)m * kmax);
-  double* dl = (double*)take(sizeof(double) * (size_t)m * kmax);
-  double* dd = (double*)take(sizeof(double) * (size_t)m * kmax);
-  double* du = (double*)take(sizeof(double) * (size_t)m * kmax);
-  double* du2 = (double*)take(sizeof(double) * (size_t)m * kmax);
-  double* bb = (double*)take(sizeof(double) * (size_t)m * kmax);
-  unsigned char* piv = (unsigned char*)take((size_t)m * kmax);
+  double* dotc = (double*)take(sizeof(double) * 2 * m);
+  unsigned* flags = (unsigned*)take(sizeof(unsigned) * 2 * m);
 
   cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
   if (err != cudaSuccess) return err;
   err = cudaMemsetAsync(tau, 0, ts * m, s);
   if (err != cudaSuccess) return err;
-
+  if (m == 1) err = cudaMemsetAsync(e, 0, sizeof(double), s);
+  if (err != cudaSuccess) return err;
   note_launches(CBC_K_EIG, 5);
   // 1. tridiagonalisation (cooperative)
-  int P = m / 4;
-  if (P < 1) P = 1;
-  if (P > num_sms) P = num_sms;
-  TriArgs<T> ta{A, m, d, e, tau, V, vbuf, p, dot, bar, status};
-  void* args[] = {&ta};
-  err = cudaLaunchCooperativeKernel((const void*)tridiag_kernel<T>, dim3(P), dim3(TPB), args, 0,
-                                    s);
-  if (err != cudaSuccess) return err;
-  // 2. eigenvalues
-  BisArgs ba{d, e, e2, m, lamb};
-  bisect_kernel<<<(m + 63) / 64, 64, 0, s>>>(ba);
-  // 3. rank
-  rank_kernel<<<1, 32, 0, s>>>(lamb, m, kmax, (long long)max_bond, tol, floor_rel, k_dev);
-  // 4. eigenvectors of T
-  InvArgs ia{d, e, lamb, lam, m, k_dev, X, kmax, dl, dd, du, du2, bb, piv};
-  inverse_iter_kernel<<<(m + 31) / 32, 32, 0, s>>>(ia);
-  // 5. back transformation
-  int wpb = 4;
-  size_t shm = (size_t)wpb * m * ts;
-  if (shm > 200 * 1024) {
-    wpb = 1;
-    shm = (size_t)m * ts;
-  }
-  if (shm > 48 * 1024) {
-    err = cudaFuncSetAttribute(backtransform_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)shm);
+  int P = std::max(1, std::min(num_sms, m / 2));
+  const int nr = (m + P - 1) / P;
+  const size_t shm_tri = ((size_t)nr + 2) * m * ts;
+  if (shm_tri <= 160 * 1024) {
+    err = cudaMemsetAsync(dotc, 0, sizeof(double) * 2 * m, s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(flags, 0, sizeof(unsigned) * 2 * m, s);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(tridiag_smem_kernel<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_tri);
     if (err != cudaSuccess) return err;
+    Tri2Args<T> ta{A, m, d, e, tau, V, p, dotc, flags, flags + m, status};
+    void* args[] = {&ta};
+    err = cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel<T>, dim3(P), dim3(TPB),
+                                      args, shm_tri, s);
+  } else {
+    TriArgs<T> ta{A, m, d, e, tau, V, vbuf, p, dot, bar, status};
+    void* args[] = {&ta};
+    err = cudaLaunchCooperativeKernel((const void*)tridiag_kernel<T>, dim3(P), dim3(TPB), args, 0,
+                                      s);
   }
-  backtransform_kernel<T><<<(kmax + wpb - 1) / wpb, 32 * wpb, shm, s>>>(V, tau, X, m, kmax, k_dev,
-                                                                         U);
+  if (err != cudaSuccess) return err;
+  // 2. eigenvalue estimates
+  const int wpb = 8;
+  bisect32_kernel<<<(m + wpb - 1) / wpb, 32 * wpb, 2 * sizeof(float) * m, s>>>(d, e, m, lam32);
+  // 3. eigenvectors of T for the candidates, FP64
+  int tpb = 32;
+  while (tpb > 1 && (size_t)tpb * m * 41 > 180 * 1024) tpb >>= 1;
+  size_t shi = (size_t)tpb * m * 41 + 64;
+  err = cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shi);
+  if (err != cudaSuccess) return err;
+  InvArgs ia{d, e, lam32, m, kmax, X, rq};
+  invit_kernel<<<(kmax + tpb - 1) / tpb, tpb, shi, s>>>(ia);
+  // 4. rank rule on the refined eigenvalues
+  rank_kernel<<<1, 256, 0, s>>>(d, rq, lam32, m, kmax, (long long)max_bond, tol, floor_rel, k_dev,
+                                lam);
+  // 5. back transformation
+  size_t shm = (size_t)m * ts;
+  if (m <= 256) {
+    backtransform_kernel<T, 8><<<kmax, 32, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
+  } else if (m <= 512) {
+    backtransform_kernel<T, 16><<<kmax, 32, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
+  } else {
+    if (shm > 48 * 1024) {
+      err = cudaFuncSetAttribute(backtransform_kernel<T, 0>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+      if (err != cudaSuccess) return err;
+    }
+    backtransform_kernel<T, 0><<<kmax, 32, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
+  }
   return cudaGetLastError();
 }
 
