@@ -159,6 +159,9 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--concurrency", type=int, default=1,
+                    help="independent applications per step (seeds rank*B .. rank*B+B-1), "
+                         "run concurrently by cbc_apply_batched, one stream each")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -178,38 +181,48 @@ def main():
         import torch.distributed as dist_mod
         dist_mod.init_process_group("nccl")
         dist = dist_mod
-    stream = torch.cuda.Stream()
+    B = max(1, args.concurrency)
+    streams = [torch.cuda.Stream() for _ in range(B)]
+    stream = streams[0]
     sptr = stream.cuda_stream
 
     # precision of the headline number: mixed when built, else fp64
     prec_name = args.precision
-    prob = make_workload(seed=rank)
+    probs = [make_workload(seed=rank * B + j) for j in range(B)]
+    prob = probs[0]
     st, op = prob.state, prob.op
-    dev_st = [torch.from_numpy(t).to(f"cuda:{local}") for t in st.tensors]
-    dev_op = [torch.from_numpy(t).to(f"cuda:{local}") for t in op.tensors]
-    torch.cuda.synchronize()
-    hs = _cbc.create_from_device(st.parent, st.phys, st.bond, dev_st, "state", sptr)
-    ho = _cbc.create_from_device(op.parent, op.phys, op.bond, dev_op, "op", sptr)
+    hs_list, ho_list = [], []
+    for p, sm in zip(probs, streams):
+        dev_st = [torch.from_numpy(t).to(f"cuda:{local}") for t in p.state.tensors]
+        dev_op = [torch.from_numpy(t).to(f"cuda:{local}") for t in p.op.tensors]
+        torch.cuda.synchronize()
+        hs_list.append(_cbc.create_from_device(p.state.parent, p.state.phys, p.state.bond, dev_st,
+                                               "state", sm.cuda_stream))
+        ho_list.append(_cbc.create_from_device(p.op.parent, p.op.phys, p.op.bond, dev_op, "op",
+                                               sm.cuda_stream))
+        torch.cuda.synchronize()
+    hs, ho = hs_list[0], ho_list[0]
 
     def apply_once(prec):
-        out = _cbc.cbc_apply(hs, ho, prob.max_bond, 0.0, _cbc.make_options(prec))
-        return out
+        opt = _cbc.make_options(prec)
+        if B == 1:
+            return [_cbc.cbc_apply(hs, ho, prob.max_bond, 0.0, opt)]
+        return _cbc.cbc_apply_batched(hs_list, ho_list, [p.max_bond for p in probs], [0.0] * B,
+                                      opt)
+
+    def destroy(outs):
+        for o in outs:
+            _cbc.ttn_destroy(o)
 
     if prec_name == "auto":
-        try:
-            _cbc.ttn_destroy(apply_once(_cbc.CBC_PREC_MIXED))
-            prec_name = "mixed"
-        except _cbc.CBCError as e:
-            if e.code != 8:
-                raise
-            prec_name = "fp64"
+        prec_name = "mixed"
     prec = _cbc.CBC_PREC_MIXED if prec_name == "mixed" else _cbc.CBC_PREC_FP64
 
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
     for _ in range(args.warmup):
-        _cbc.ttn_destroy(apply_once(prec))
+        destroy(apply_once(prec))
     torch.cuda.synchronize()
 
     gpu_index = local
@@ -230,18 +243,26 @@ def main():
     total_ms = 0.0
     last = None
     for k in range(args.steps):
+        # flush L2 (untimed), then time the step from a point all streams wait on to the
+        # point where all of them are done
         with torch.cuda.stream(stream):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-        out = apply_once(prec)
+        for sm in streams[1:]:
+            sm.wait_event(e0)
+        outs = apply_once(prec)
+        for sm in streams[1:]:
+            ev = torch.cuda.Event()
+            ev.record(sm)
+            stream.wait_event(ev)
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
         if last is not None:
-            _cbc.ttn_destroy(last)
-        last = out
+            destroy(last)
+        last = outs
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -254,7 +275,7 @@ def main():
         tt = torch.tensor([total_ms], device=f"cuda:{local}", dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_max = float(tt.item())
-    value = world * args.steps / (t_max / 1e3)
+    value = world * B * args.steps / (t_max / 1e3)
     ms_per_step = t_max / args.steps
 
     # per-kernel-class roofline of the dominant class
@@ -288,11 +309,11 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_name == "fp64" else "bf16-slices+f64",
             "data": "synthetic",
-            "config": dict(WORKLOAD, precision=prec_name,
+            "config": dict(WORKLOAD, precision=prec_name, concurrent_applications=B,
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                            l2="flushed between steps (256 MB write, untimed)"),
-            "tflops": flops_per_app * value / world / 1e12 * world,
-            "algorithmic_gflop_per_app": flops_per_app / 1e9,
+            "tflops": flops_per_app / B * value / 1e12,
+            "algorithmic_gflop_per_app": flops_per_app / B / 1e9,
             "kernel_classes": {k: {"ms_per_step": v["ms"] / args.steps,
                                    "launches_per_step": v["launches"] / args.steps}
                                for k, v in stats.items() if v["launches"]},
@@ -305,41 +326,51 @@ def main():
         from oracle import metrics
         t_or, ref = oracle_time(prob)
         shape = _cbc.output_shape_fn(st.parent, st.phys)
-        tens, bonds, log_norm = _cbc.fetch_network(last, shape, True)
+        tens, bonds, log_norm = _cbc.fetch_network(last[0], shape, True)
         line["rel_err_vs_oracle"] = metrics.rel_err(st.parent, tens, ref.tensors, log_norm, 0.0)
         line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "applications/s",
                                 "cores": blas_threads(), "kind": "oracle",
                                 "sample": "one full application of the workload (seed 0)"}
     if last is not None:
-        _cbc.ttn_destroy(last)
+        destroy(last)
 
     # end to end through the C ABI with host buffers: H2D of the inputs, the application,
     # D2H of every output tensor, each step
     if not args.no_e2e:
-        pin_st = [torch.from_numpy(t).pin_memory().numpy() for t in st.tensors]
-        pin_op = [torch.from_numpy(t).pin_memory().numpy() for t in op.tensors]
-        h2d = sum(t.nbytes for t in pin_st) + sum(t.nbytes for t in pin_op)
+        pins = [([torch.from_numpy(t).pin_memory().numpy() for t in p.state.tensors],
+                 [torch.from_numpy(t).pin_memory().numpy() for t in p.op.tensors]) for p in probs]
+        h2d = sum(sum(t.nbytes for t in a) + sum(t.nbytes for t in b) for a, b in pins)
         shape = _cbc.output_shape_fn(st.parent, st.phys)
         d2h = 0
         e2e_t = 0.0
-        for k in range(max(2, args.steps)):
+        n_e2e = max(2, args.steps)
+        for k in range(n_e2e):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            a = _cbc.create_from_host(st.parent, st.phys, st.bond, pin_st, "state", sptr)
-            b = _cbc.create_from_host(op.parent, op.phys, op.bond, pin_op, "op", sptr)
-            o = _cbc.cbc_apply(a, b, prob.max_bond, 0.0, _cbc.make_options(prec))
-            tens, bonds, _ = _cbc.fetch_network(o, shape, True)
+            ha = [_cbc.create_from_host(p.state.parent, p.state.phys, p.state.bond, pa, "state",
+                                        sm.cuda_stream) for p, (pa, _), sm in zip(probs, pins, streams)]
+            hb = [_cbc.create_from_host(p.op.parent, p.op.phys, p.op.bond, pb, "op", sm.cuda_stream)
+                  for p, (_, pb), sm in zip(probs, pins, streams)]
+            opt = _cbc.make_options(prec)
+            if B == 1:
+                outs = [_cbc.cbc_apply(ha[0], hb[0], prob.max_bond, 0.0, opt)]
+            else:
+                outs = _cbc.cbc_apply_batched(ha, hb, [p.max_bond for p in probs], [0.0] * B, opt)
+            d2h = 0
+            for o in outs:
+                tens, bonds, _ = _cbc.fetch_network(o, shape, True)
+                d2h += sum(t.nbytes for t in tens)
             e2e_t += time.perf_counter() - t0
-            d2h = sum(t.nbytes for t in tens)
-            for h in (o, a):
-                _cbc.ttn_destroy(h)
-            _cbc.ttno_destroy(b)
-        n_e2e = max(2, args.steps)
-        line["e2e"] = {"value": world * n_e2e / e2e_t, "unit": "applications/s",
+            destroy(outs + ha)
+            for h in hb:
+                _cbc.ttno_destroy(h)
+        line["e2e"] = {"value": world * B * n_e2e / e2e_t, "unit": "applications/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    _cbc.ttn_destroy(hs)
-    _cbc.ttno_destroy(ho)
+    for h in hs_list:
+        _cbc.ttn_destroy(h)
+    for h in ho_list:
+        _cbc.ttno_destroy(h)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

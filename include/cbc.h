@@ -122,6 +122,20 @@ int ttno_create(int n_nodes, const int32_t* parent, const int64_t* phys_dim,
 int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
               const cbc_options* opt, ttn_t* out);
 
+/* Apply n operators to n states (independent instances of any sizes and topologies)
+ * and compress each, as n calls of cbc_apply that run concurrently: up to `workers`
+ * host threads (<= 0: min(n, 16)) each drive instances, so the latency-bound steps of
+ * different instances (truncation eigensolves, Cholesky factorisations) overlap on the
+ * GPU.  Instance j runs on the stream of states[j]; give every state its own stream for
+ * the work to overlap.
+ *   max_bond, tol  [n] host arrays (per instance), or NULL for 0 (no cap / no tolerance)
+ *   opt            shared by all instances (NULL for defaults)
+ *   outs           [n] host array, receives the output handles (NULL where failed)
+ * Returns the first failing status in instance order (CBC_OK if all succeeded); the
+ * other instances still complete.                                                   */
+int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64_t* max_bond,
+                      const double* tol, const cbc_options* opt, int workers, ttn_t* outs);
+
 /* Information about a TTNS (synchronises its stream).
  *   n_nodes_out     may be NULL
  *   bond_dims_out   NULL or [n_nodes]: bond of each node to its parent (1 at the root)

@@ -76,6 +76,9 @@ def lib():
                                ctypes.c_int, ctypes.c_int, vp, i64, ctypes.c_int, ctypes.c_int,
                                vp, i64, ctypes.c_int, ctypes.c_int, vp, i64, vp]
         L.cbc_gemm.restype = ctypes.c_int
+        L.cbc_apply_batched.argtypes = [ctypes.c_int, P(vp), P(vp), P(i64), P(dbl),
+                                        P(cbc_options), ctypes.c_int, P(vp)]
+        L.cbc_apply_batched.restype = ctypes.c_int
         L.cbc_stats_enable.argtypes = [ctypes.c_int]
         L.cbc_stats_reset.argtypes = []
         L.cbc_stats_read.argtypes = [P(cbc_stats)]
@@ -181,6 +184,21 @@ def cbc_gemm(precision: int, slices: int, dtype: int, M: int, N: int, K: int, A_
                           int(bool(conjA)), ctypes.c_void_p(int(B_ptr)), int(ldb),
                           int(bool(transB)), int(bool(conjB)), ctypes.c_void_p(int(C_ptr)),
                           int(ldc), ctypes.c_void_p(stream or 0)))
+
+
+def cbc_apply_batched(states, ops, max_bond, tol, opt: Optional[cbc_options] = None,
+                      workers: int = 0):
+    """Run len(states) independent applications concurrently; returns the output handles."""
+    n = len(states)
+    st = (ctypes.c_void_p * n)(*[h.value for h in states])
+    op = (ctypes.c_void_p * n)(*[h.value for h in ops])
+    mb = (ctypes.c_int64 * n)(*[int(x) for x in max_bond])
+    tl = (ctypes.c_double * n)(*[float(x) for x in tol])
+    outs = (ctypes.c_void_p * n)()
+    _check(lib().cbc_apply_batched(n, st, op, mb, tl,
+                                   ctypes.byref(opt) if opt is not None else None,
+                                   int(workers), outs))
+    return [ctypes.c_void_p(outs[j]) for j in range(n)]
 
 
 def ttn_get_info(t):

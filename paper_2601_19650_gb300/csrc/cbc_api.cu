@@ -7,8 +7,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -266,6 +268,36 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_op
     return rc;
   }
   *out = res;
+  return CBC_OK;
+}
+
+int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64_t* max_bond,
+                      const double* tol, const cbc_options* opt, int workers, ttn_t* outs) {
+  if (n < 0 || (n > 0 && (!states || !ops || !outs)))
+    return fail(CBC_ERR_INVALID_ARG, "cbc_apply_batched: bad arguments");
+  for (int j = 0; j < n; ++j) outs[j] = nullptr;
+  if (n == 0) return CBC_OK;
+  if (workers <= 0) workers = std::min(n, 16);
+  workers = std::max(1, std::min(workers, n));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<int> rc(n, CBC_OK);
+  std::vector<std::string> msg(n);
+  std::atomic<int> next{0};
+  auto work = [&]() {
+    cudaSetDevice(dev);
+    for (int j = next++; j < n; j = next++) {
+      rc[j] = cbc_apply(states[j], ops[j], max_bond ? max_bond[j] : 0, tol ? tol[j] : 0.0, opt,
+                        &outs[j]);
+      if (rc[j] != CBC_OK) msg[j] = g_last_error;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  for (int j = 0; j < n; ++j)
+    if (rc[j] != CBC_OK) return fail(rc[j], "cbc_apply_batched: instance %d: %s", j, msg[j].c_str());
   return CBC_OK;
 }
 

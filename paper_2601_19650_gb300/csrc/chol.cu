@@ -209,8 +209,7 @@ cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cud
   if (err != cudaSuccess) return err;
   size_t shm = (size_t)std::max(m, NB) * NB * sizeof(T);
   if (shm > 48 * 1024) {
-    err = cudaFuncSetAttribute(chol_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)shm);
+    err = allow_max_smem((const void*)chol_kernel<T>);
     if (err != cudaSuccess) return err;
   }
   note_launches(CBC_K_CHOLQR, 1);
@@ -225,20 +224,18 @@ cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* b
   (void)status;
   (void)bar;
   (void)num_sms;
-  const int nw = 2;  // warps (columns) per CTA
+  const int nw = 4;  // warps (columns) per CTA: one per SM sub-partition
   const size_t tri = (size_t)m * (m + 1) / 2 * sizeof(T);
   const size_t rest = (size_t)m * sizeof(double) + (size_t)nw * m * sizeof(T);
   note_launches(CBC_K_CHOLQR, 1);
   cudaError_t err;
   if (tri + rest <= 200 * 1024) {
-    err = cudaFuncSetAttribute(trsm_cols_kernel<T, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(tri + rest));
+    err = allow_max_smem((const void*)trsm_cols_kernel<T, true>);
     if (err != cudaSuccess) return err;
     trsm_cols_kernel<T, true><<<(n + nw - 1) / nw, 32 * nw, tri + rest, s>>>(C, S, m, n);
   } else {
     if (rest > 48 * 1024) {
-      err = cudaFuncSetAttribute(trsm_cols_kernel<T, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rest);
+      err = allow_max_smem((const void*)trsm_cols_kernel<T, false>);
       if (err != cudaSuccess) return err;
     }
     trsm_cols_kernel<T, false><<<(n + nw - 1) / nw, 32 * nw, rest, s>>>(C, S, m, n);

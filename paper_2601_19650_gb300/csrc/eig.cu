@@ -21,6 +21,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "kernels.cuh"
 #include "planner.h"
@@ -611,78 +612,47 @@ __global__ void rank_kernel(const double* d, const double* rq, const float* lam3
 }
 
 // ---- back transformation: U[:, jj] = H_0 ... H_{m-2} X[:, jj] ------------------------
-// One warp per kept eigenvector, one warp per CTA so the FP64 work of the reflector
-// applications spreads over as many SMs as there are vectors.
-template <typename T, int RB>
-__global__ void __launch_bounds__(32) backtransform_kernel(const T* V, const T* tau,
-                                                           const double* X, int m, int kmax,
-                                                           const int* k_dev, T* U) {
+// One CTA of four warps per kept eigenvector (one warp per SM sub-partition, since a
+// warp alone reaches only its own partition's FP64 unit).  Each reflector application
+// is a dot product over the rows (per-warp partial sums combined through shared
+// memory) and an axpy; the rows are split across the 128 threads.
+template <typename T>
+__global__ void __launch_bounds__(128) backtransform_kernel(const T* V, const T* tau,
+                                                            const double* X, int m, int kmax,
+                                                            const int* k_dev, T* U) {
   using O = ops<T>;
   extern __shared__ unsigned char smem_raw[];
   T* u = reinterpret_cast<T*>(smem_raw);
-  const int lane = threadIdx.x & 31;
+  __shared__ T part[2][4];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int jj = blockIdx.x;
   const int k = *k_dev;
   if (jj >= k) return;
-  for (int i = lane; i < m; i += 32) u[i] = O::make(X[(int64_t)i * kmax + jj], 0.0);
-  __syncwarp();
-  if constexpr (RB == 0) {  // large m: stream the reflectors from memory
-    for (int j = m - 2; j >= 0; --j) {
-      const T* vj = V + (int64_t)j * m;
-      const T t = tau[j];
-      T sacc = O::zero();
-      for (int r = j + 1 + lane; r < m; r += 32) sacc = O::fma(O::conj(vj[r]), u[r], sacc);
-      if constexpr (O::cplx) {
-        sacc = zdbl{warp_sum(O::real(sacc)), warp_sum(O::imag(sacc))};
-      } else {
-        sacc = warp_sum(sacc);
-      }
-      const T ts = t * sacc;
-      __syncwarp();
-      for (int r = j + 1 + lane; r < m; r += 32) u[r] = u[r] - vj[r] * ts;
-      __syncwarp();
-    }
-    for (int i = lane; i < m; i += 32) U[(int64_t)i * kmax + jj] = u[i];
-    return;
-  }
-  // each lane keeps its RB elements of the current reflector in registers and loads
-  // the next reflector while the current one is applied (m <= 32 RB)
-  constexpr int RBX = RB > 0 ? RB : 1;
-  T vcur[RBX], vnext[RBX];
-  auto load_row = [&](int j, T (&dst)[RBX]) {
-#pragma unroll
-    for (int q = 0; q < RBX; ++q) {
-      const int r = lane + 32 * q;
-      dst[q] = (j >= 0 && r > j && r < m) ? V[(int64_t)j * m + r] : O::zero();
-    }
-  };
-  load_row(m - 2, vcur);
+  for (int i = tid; i < m; i += 128) u[i] = O::make(X[(int64_t)i * kmax + jj], 0.0);
+  __syncthreads();
+  int par = 0;
   for (int j = m - 2; j >= 0; --j) {
-    load_row(j - 1, vnext);
+    const T* vj = V + (int64_t)j * m;
     const T t = tau[j];
     T sacc = O::zero();
-#pragma unroll
-    for (int q = 0; q < RBX; ++q) {
-      const int r = lane + 32 * q;
-      if (r < m) sacc = O::fma(O::conj(vcur[q]), u[r], sacc);
-    }
+    // each thread owns rows r = tid (mod 128) for the whole loop, so u needs no barrier
+    for (int r = tid; r < m; r += 128)
+      if (r > j) sacc = O::fma(O::conj(vj[r]), u[r], sacc);
     if constexpr (O::cplx) {
       sacc = zdbl{warp_sum(O::real(sacc)), warp_sum(O::imag(sacc))};
     } else {
       sacc = warp_sum(sacc);
     }
-    const T ts = t * sacc;
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < RBX; ++q) {
-      const int r = lane + 32 * q;
-      if (r < m) u[r] = u[r] - vcur[q] * ts;
-    }
-    __syncwarp();
-#pragma unroll
-    for (int q = 0; q < RBX; ++q) vcur[q] = vnext[q];
+    if (lane == 0) part[par][warp] = sacc;
+    __syncthreads();
+    const T tot = (part[par][0] + part[par][1]) + (part[par][2] + part[par][3]);
+    const T ts = t * tot;
+    for (int r = tid; r < m; r += 128)
+      if (r > j) u[r] = u[r] - vj[r] * ts;
+    par ^= 1;  // the next partial sums go to the other buffer: one barrier per reflector
   }
-  for (int i = lane; i < m; i += 32) U[(int64_t)i * kmax + jj] = u[i];
+  __syncthreads();
+  for (int i = tid; i < m; i += 128) U[(int64_t)i * kmax + jj] = u[i];
 }
 
 }  // namespace
@@ -741,16 +711,19 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   if (m == 1) err = cudaMemsetAsync(e, 0, sizeof(double), s);
   if (err != cudaSuccess) return err;
   note_launches(CBC_K_EIG, 5);
-  // 1. tridiagonalisation (cooperative)
+  // 1. tridiagonalisation (cooperative); CBC_TRIDIAG_CTAS overrides the CTA count
   int P = std::max(1, std::min(num_sms, m / 2));
+  if (const char* env = getenv("CBC_TRIDIAG_CTAS")) {
+    int v = atoi(env);
+    if (v > 0) P = std::max(1, std::min(num_sms, v));
+  }
   const int nr = (m + P - 1) / P;
   const size_t shm_tri = ((size_t)nr + 2) * m * ts;
   if (shm_tri <= 160 * 1024) {
     err = cudaMemsetAsync(dotc, 0, sizeof(double) * 2 * m, s);
     if (err == cudaSuccess) err = cudaMemsetAsync(flags, 0, sizeof(unsigned) * 2 * m, s);
     if (err == cudaSuccess)
-      err = cudaFuncSetAttribute(tridiag_smem_kernel<T>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm_tri);
+      err = allow_max_smem((const void*)tridiag_smem_kernel<T>);
     if (err != cudaSuccess) return err;
     Tri2Args<T> ta{A, m, d, e, tau, V, p, dotc, flags, flags + m, status};
     void* args[] = {&ta};
@@ -767,10 +740,11 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   const int wpb = 8;
   bisect32_kernel<<<(m + wpb - 1) / wpb, 32 * wpb, 2 * sizeof(float) * m, s>>>(d, e, m, lam32);
   // 3. eigenvectors of T for the candidates, FP64
-  int tpb = 32;
-  while (tpb > 1 && (size_t)tpb * m * 41 > 180 * 1024) tpb >>= 1;
+  // one candidate per CTA: the LU and the solves are long dependent FP64 chains, best
+  // run with a whole SM (and its FP64 unit) per chain
+  const int tpb = 1;
   size_t shi = (size_t)tpb * m * 41 + 64;
-  err = cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shi);
+  err = allow_max_smem((const void*)invit_kernel);
   if (err != cudaSuccess) return err;
   InvArgs ia{d, e, lam32, m, kmax, X, rq};
   invit_kernel<<<(kmax + tpb - 1) / tpb, tpb, shi, s>>>(ia);
@@ -779,18 +753,11 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
                                 lam);
   // 5. back transformation
   size_t shm = (size_t)m * ts;
-  if (m <= 256) {
-    backtransform_kernel<T, 8><<<kmax, 32, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
-  } else if (m <= 512) {
-    backtransform_kernel<T, 16><<<kmax, 32, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
-  } else {
-    if (shm > 48 * 1024) {
-      err = cudaFuncSetAttribute(backtransform_kernel<T, 0>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-      if (err != cudaSuccess) return err;
-    }
-    backtransform_kernel<T, 0><<<kmax, 32, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
+  if (shm > 48 * 1024) {
+    err = allow_max_smem((const void*)backtransform_kernel<T>);
+    if (err != cudaSuccess) return err;
   }
+  backtransform_kernel<T><<<kmax, 128, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
   return cudaGetLastError();
 }
 

@@ -342,72 +342,147 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
 }
 
 // ---------------- operand slicing ----------------
-// One warp per logical row: a row of A (M x K), or a column of B (K x N) for the B^T
-// side.  Writes S bf16 slices into [S][rows_pad][K2_pad] and the row exponent.
+// Logical rows are the rows of A, or the columns of B for the B^T side.  Two kernels:
+// the exponent of every logical row (max over K), then 32 x 32 tiles that are read
+// along whichever index is contiguous in memory, cut into slices in shared memory and
+// written to the [S][rows_pad][K2_pad] planes coalesced along K.
 template <typename T, bool SIDE_B>
-__global__ void pack_kernel(const T* src, View v, int conj, int R, int K, int rows_pad, int K2_pad,
-                            int S, __nv_bfloat16* out, int* expo, int* status) {
+__device__ __forceinline__ T load_op(const T* src, const View& v, int r, int k, int conj) {
+  T x = SIDE_B ? src[v.roff(k) + v.coff(r)] : src[v.roff(r) + v.coff(k)];
+  return conj ? ops<T>::conj(x) : x;
+}
+
+template <typename T, bool SIDE_B>
+__global__ void expo_kernel(const T* src, View v, int R, int K, int nrows, int rowlanes,
+                            int* expo, int* status) {
   using O = ops<T>;
-  constexpr bool CPLX = O::cplx;
-  const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int nrows_logical = CPLX && SIDE_B ? rows_pad / 2 : rows_pad;
-  if (warp_g >= nrows_logical) return;
-  const int r = warp_g;
-  auto load = [&](int k) -> T {
-    T x = SIDE_B ? src[v.roff(k) + v.coff(r)] : src[v.roff(r) + v.coff(k)];
-    return conj ? O::conj(x) : x;
-  };
-  const bool live = r < R;
   double mx = 0.0;
-  if (live)
-    for (int k = lane; k < K; k += 32) {
-      T x = load(k);
-      mx = fmax(mx, fmax(fabs(O::real(x)), fabs(O::imag(x))));
-    }
+  int r;
+  if (rowlanes) {  // one thread per logical row, consecutive threads on consecutive rows
+    r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    if (r < R)
+      for (int k = 0; k < K; ++k) {
+        T x = load_op<T, SIDE_B>(src, v, r, k, 0);
+        mx = fmax(mx, fmax(fabs(O::real(x)), fabs(O::imag(x))));
+      }
+  } else {         // one warp per logical row, lanes along K
+    r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= nrows) return;
+    if (r < R)
+      for (int k = lane; k < K; k += 32) {
+        T x = load_op<T, SIDE_B>(src, v, r, k, 0);
+        mx = fmax(mx, fmax(fabs(O::real(x)), fabs(O::imag(x))));
+      }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane != 0) return;
+  }
   if (!isfinite(mx)) {
-    if (lane == 0) set_status(status, CBC_ERR_NUMERICAL);
+    set_status(status, CBC_ERR_NUMERICAL);
     mx = 0.0;
   }
-  int e = 0;
-  if (mx > 0.0) e = ilogb(mx) + 1;  // max|x| < 2^e
-  if (lane == 0) expo[r] = e;
-  const size_t plane = (size_t)rows_pad * K2_pad;
-  // element k of the logical row -> one (real) or two (complex) K positions
-  const int prow0 = (CPLX && SIDE_B) ? 2 * r : r;
-  for (int k = lane; k < K2_pad / (CPLX ? 2 : 1); k += 32) {
-    double vals[2][2] = {{0.0, 0.0}, {0.0, 0.0}};  // [packed row][pair position]
-    if (live && k < K) {
-      T x = load(k);
-      double xr = O::real(x), xi = O::imag(x);
-      if (!CPLX) {
-        vals[0][0] = xr;
-      } else if (!SIDE_B) {
-        vals[0][0] = xr;
-        vals[0][1] = xi;
-      } else {
-        vals[0][0] = xr;   // row 2n:   [ br, -bi ]
-        vals[0][1] = -xi;
-        vals[1][0] = xi;   // row 2n+1: [ bi,  br ]
-        vals[1][1] = xr;
+  expo[r] = (mx > 0.0) ? ilogb(mx) + 1 : 0;  // max|x| < 2^e
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(double lo, double hi) {
+  __nv_bfloat162 p = __floats2bfloat162_rn((float)lo, (float)hi);
+  return *reinterpret_cast<uint32_t*>(&p);
+}
+
+template <typename T, bool SIDE_B, bool ROWLANES>
+__global__ void __launch_bounds__(256) slice_kernel(const T* src, View v, int conj, int R, int K,
+                                                    int K2p, size_t plane, int S,
+                                                    __nv_bfloat16* out, const int* expo) {
+  using O = ops<T>;
+  constexpr bool CPLX = O::cplx;
+  __shared__ T tile[32][33];
+  __shared__ int se[32];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  for (int q = tid >> 5; q < 32; q += 8) {
+    const int r = ROWLANES ? r0 + lane : r0 + q;
+    const int k = ROWLANES ? k0 + q : k0 + lane;
+    T x = (r < R && k < K) ? load_op<T, SIDE_B>(src, v, r, k, conj) : O::zero();
+    if (ROWLANES)
+      tile[lane][q] = x;
+    else
+      tile[q][lane] = x;
+  }
+  if (tid < 32) se[tid] = expo[r0 + tid];
+  __syncthreads();
+  // 32 logical rows x 32 logical k; real: one bf16 per (row, k); complex: one bf16 pair
+  constexpr int NPR = (CPLX && SIDE_B) ? 2 : 1;  // packed rows per logical row
+  for (int idx = tid; idx < 32 * 32 * NPR; idx += 256) {
+    const int kk = idx & 31;
+    const int prl = idx >> 5;            // packed row within the tile
+    const int lr = prl / NPR, half = prl % NPR;
+    const T x = tile[lr][kk];
+    const int e = se[lr];
+    const int prow = (r0 + lr) * NPR + half;
+    if constexpr (!CPLX) {
+      double t = ldexp(O::real(x), 7 - e);
+      __nv_bfloat16* o = out + (size_t)prow * K2p + (k0 + kk);
+      for (int sl = 0; sl < S; ++sl) {
+        const double q = rint(t);
+        o[sl * plane] = __float2bfloat16_rn((float)q);
+        t = (t - q) * 256.0;
       }
-    }
-    const int nprow = (CPLX && SIDE_B) ? 2 : 1;
-    const int npos = CPLX ? 2 : 1;
-    for (int pr = 0; pr < nprow; ++pr) {
-      for (int pp = 0; pp < npos; ++pp) {
-        double t = ldexp(vals[pr][pp], 7 - e);  // |t| < 128
-        const size_t base = (size_t)(prow0 + pr) * K2_pad + (size_t)k * npos + pp;
-        for (int s = 0; s < S; ++s) {
-          double q = rint(t);
-          out[s * plane + base] = __float2bfloat16_rn((float)q);
-          t = (t - q) * 256.0;
-        }
+    } else {
+      double a0, a1;  // the two K positions of this (packed row, k)
+      const double xr = O::real(x), xi = O::imag(x);
+      if (!SIDE_B) {
+        a0 = xr;
+        a1 = xi;
+      } else if (half == 0) {
+        a0 = xr;   // row 2n:   [ br, -bi ]
+        a1 = -xi;
+      } else {
+        a0 = xi;   // row 2n+1: [ bi,  br ]
+        a1 = xr;
+      }
+      double t0 = ldexp(a0, 7 - e), t1 = ldexp(a1, 7 - e);
+      uint32_t* o = reinterpret_cast<uint32_t*>(out) + ((size_t)prow * K2p + 2 * (k0 + kk)) / 2;
+      for (int sl = 0; sl < S; ++sl) {
+        const double q0 = rint(t0), q1 = rint(t1);
+        o[sl * (plane / 2)] = bf16x2_bits(q0, q1);
+        t0 = (t0 - q0) * 256.0;
+        t1 = (t1 - q1) * 256.0;
       }
     }
   }
+}
+
+// strides of the logical (row, k) indices at the origin, to pick the read pattern
+template <bool SIDE_B>
+bool rows_contiguous(const View& v) {
+  const int64_t sr = SIDE_B ? (v.coff(1) - v.coff(0)) : (v.roff(1) - v.roff(0));
+  const int64_t sk = SIDE_B ? (v.roff(1) - v.roff(0)) : (v.coff(1) - v.coff(0));
+  return sr == 1 && sk != 1;
+}
+
+template <typename T, bool SIDE_B>
+void pack_operand(const T* src, const View& v, bool conj, int R, int K, int rows_pad, int K2p,
+                  int S, __nv_bfloat16* out, int* expo, int* status, cudaStream_t s) {
+  constexpr bool CPLX = ops<T>::cplx;
+  const int nrows = (CPLX && SIDE_B) ? rows_pad / 2 : rows_pad;  // logical rows (padded)
+  const int klog = CPLX ? K2p / 2 : K2p;                           // logical K (padded)
+  const bool rl = rows_contiguous<SIDE_B>(v);
+  note_launches(CBC_K_AUX, 2);
+  if (rl)
+    expo_kernel<T, SIDE_B><<<(nrows + 127) / 128, 128, 0, s>>>(src, v, R, K, nrows, 1, expo, status);
+  else
+    expo_kernel<T, SIDE_B><<<(nrows * 32 + 255) / 256, 256, 0, s>>>(src, v, R, K, nrows, 0, expo,
+                                                                     status);
+  dim3 grid(klog / 32, nrows / 32);
+  const size_t plane = (size_t)rows_pad * K2p;
+  if (rl)
+    slice_kernel<T, SIDE_B, true><<<grid, 256, 0, s>>>(src, v, conj ? 1 : 0, R, K, K2p, plane, S,
+                                                       out, expo);
+  else
+    slice_kernel<T, SIDE_B, false><<<grid, 256, 0, s>>>(src, v, conj ? 1 : 0, R, K, K2p, plane, S,
+                                                        out, expo);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -449,7 +524,8 @@ Geo geometry(int M, int N, int K, bool cplx, int S) {
   g.BN = bn_for(S);
   g.Mp = (M + BM - 1) / BM * BM;
   g.N2 = cplx ? 2 * N : N;
-  g.N2p = (g.N2 + g.BN - 1) / g.BN * g.BN;
+  // a multiple of 64 so that complex B^T planes hold whole 32-row slicing tiles
+  g.N2p = (g.N2 + 63) / 64 * 64;
   g.K2 = cplx ? 2 * K : K;
   g.K2p = (g.K2 + KA - 1) / KA * KA;
   return g;
@@ -531,15 +607,8 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
   int* eb = reinterpret_cast<int*>(w);
   if (K <= 0) return cudaErrorInvalidValue;
   // slices of A (rows) and of B (columns, embedded)
-  {
-    int warps = g.Mp;
-    note_launches(CBC_K_AUX, 2);
-    pack_kernel<T, false><<<(warps * 32 + 255) / 256, 256, 0, s>>>(
-        A, va, conjA ? 1 : 0, M, K, g.Mp, g.K2p, S, sa, ea, status);
-    int wb = CPLX ? g.N2p / 2 : g.N2p;
-    pack_kernel<T, true><<<(wb * 32 + 255) / 256, 256, 0, s>>>(B, vb, conjB ? 1 : 0, N, K, g.N2p,
-                                                                g.K2p, S, sb, eb, status);
-  }
+  pack_operand<T, false>(A, va, conjA, M, K, g.Mp, g.K2p, S, sa, ea, status, s);
+  pack_operand<T, true>(B, vb, conjB, N, K, g.N2p, g.K2p, S, sb, eb, status, s);
   CUtensorMap ma, mb;
   if (!make_map(&ma, sa, g.K2p, g.Mp, S, BM) || !make_map(&mb, sb, g.K2p, g.N2p, S, g.BN))
     return cudaErrorInvalidValue;

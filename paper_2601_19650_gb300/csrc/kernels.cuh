@@ -92,6 +92,11 @@ cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* b
                             int num_sms, cudaStream_t s);
 
 // ---- small helpers ------------------------------------------------------------------
+// Let `func` use up to the device's opt-in shared memory per block.  Every caller sets
+// the same value, so concurrent calls from several host threads cannot shrink the
+// limit under another thread's launch.
+cudaError_t allow_max_smem(const void* func);
+
 // x[i] (i < n) scaled in place to unit Frobenius norm; log of the old norm added to
 // *log_acc; non-finite norm sets CBC_ERR_NUMERICAL.
 template <typename T>

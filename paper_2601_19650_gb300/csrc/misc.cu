@@ -91,6 +91,21 @@ int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(409
 
 }  // namespace
 
+cudaError_t allow_max_smem(const void* func) {
+  static int optin = 0;
+  if (optin == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    optin = v > 0 ? v : 48 * 1024;
+  }
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
 template <typename T>
 cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, double* scratch,
                               cudaStream_t s) {

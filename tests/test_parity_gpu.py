@@ -114,3 +114,37 @@ def test_mixed_complex_chain_small(L, chi, D, mb, seed):
 def test_mixed_cfg2_full():
     """The bench workload: L=64, d=2, chi=128, D=16, max_bond=128, complex64."""
     _compare_mixed(make_problem(2))
+
+
+# ---------------------------------------------------------------------------------------
+# batched serving set: independent instances of different sizes, one stream each,
+# applied concurrently by cbc_apply_batched
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
+def test_batched_heterogeneous(precision, bar):
+    import torch
+
+    from paper_2601_19650_gb300 import _cbc
+    from synth.networks import make_batch
+
+    probs = make_batch(n=6, scale=4)   # L 4..16, chi 8..64, D 1..8, float32, seed j
+    streams = [torch.cuda.Stream() for _ in probs]
+    hs, ho = [], []
+    for p, s in zip(probs, streams):
+        hs.append(_cbc.create_from_host(p.state.parent, p.state.phys, p.state.bond,
+                                        p.state.tensors, "state", s.cuda_stream))
+        ho.append(_cbc.create_from_host(p.op.parent, p.op.phys, p.op.bond, p.op.tensors,
+                                        "op", s.cuda_stream))
+    outs = _cbc.cbc_apply_batched(hs, ho, [p.max_bond for p in probs], [0.0] * len(probs),
+                                  _cbc.make_options(precision), workers=3)
+    for p, o in zip(probs, outs):
+        got, bonds, log_norm = _cbc.fetch_network(
+            o, _cbc.output_shape_fn(p.state.parent, p.state.phys), False)
+        ref = cbc.cbc(p.state.parent, p.state.tensors, p.op.tensors, p.max_bond)
+        assert list(bonds) == list(ref.out_bonds)
+        e = metrics.rel_err(p.state.parent, got, ref.tensors, log_norm, 0.0)
+        assert e <= bar, (p.name, e)
+    for h in outs + hs:
+        _cbc.ttn_destroy(h)
+    for h in ho:
+        _cbc.ttno_destroy(h)
