@@ -106,6 +106,11 @@ cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, dou
 template <typename T>
 cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_dev, int n,
                            T* L, cudaStream_t s);
+// out = in with its axes permuted: out dims are in dims[perm[0]], in dims[perm[1]], ...
+// (row-major, rank <= 8)
+template <typename T>
+cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const int* perm,
+                    cudaStream_t s);
 // dst (n_elem) = identity rows r < n of an n x n matrix
 template <typename T>
 cudaError_t fill_identity(T* dst, int n, cudaStream_t s);

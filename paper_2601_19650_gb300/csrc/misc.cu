@@ -87,6 +87,26 @@ __global__ void narrow_kernel(const double* src, void* dst, int dt, int64_t n_sc
   }
 }
 
+struct PermArgs {
+  int rank;
+  int64_t out_dims[8];
+  int64_t in_stride_of_out[8];  // stride in `in` of each output axis
+};
+
+template <typename T>
+__global__ void permute_kernel(const T* in, T* out, int64_t total, PermArgs a) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int64_t rem = t, off = 0;
+    for (int d = a.rank - 1; d >= 0; --d) {
+      const int64_t i = rem % a.out_dims[d];
+      rem /= a.out_dims[d];
+      off += i * a.in_stride_of_out[d];
+    }
+    out[t] = in[off];
+  }
+}
+
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + 255) / 256)); }
 
 }  // namespace
@@ -133,6 +153,27 @@ cudaError_t fill_identity(T* dst, int n, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const int* perm,
+                    cudaStream_t s) {
+  if (rank < 1 || rank > 8) return cudaErrorInvalidValue;
+  int64_t in_stride[8];
+  in_stride[rank - 1] = 1;
+  for (int d = rank - 2; d >= 0; --d) in_stride[d] = in_stride[d + 1] * in_dims[d + 1];
+  PermArgs a;
+  a.rank = rank;
+  int64_t total = 1;
+  for (int d = 0; d < rank; ++d) {
+    a.out_dims[d] = in_dims[perm[d]];
+    a.in_stride_of_out[d] = in_stride[perm[d]];
+    total *= a.out_dims[d];
+  }
+  if (total == 0) return cudaSuccess;
+  note_launches(CBC_K_AUX, 1);
+  permute_kernel<T><<<grid_for(total), 256, 0, s>>>(in, out, total, a);
+  return cudaGetLastError();
+}
+
 cudaError_t widen_to_f64(const void* src, int src_dtype, void* dst, int64_t n_elem,
                          cudaStream_t s) {
   int64_t ns = n_elem * ((src_dtype == CBC_C64 || src_dtype == CBC_C128) ? 2 : 1);
@@ -156,6 +197,10 @@ template cudaError_t scaled_adjoint<double>(const double*, int, const double*, c
                                             double*, cudaStream_t);
 template cudaError_t scaled_adjoint<zdbl>(const zdbl*, int, const double*, const int*, int, zdbl*,
                                           cudaStream_t);
+template cudaError_t permute<double>(const double*, double*, int, const int64_t*, const int*,
+                                     cudaStream_t);
+template cudaError_t permute<zdbl>(const zdbl*, zdbl*, int, const int64_t*, const int*,
+                                   cudaStream_t);
 template cudaError_t fill_identity<double>(double*, int, cudaStream_t);
 template cudaError_t fill_identity<zdbl>(zdbl*, int, cudaStream_t);
 

@@ -6,7 +6,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "kernels.cuh"
@@ -322,6 +324,312 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
   return CBC_OK;
 }
 
+// ---- trees (Sec. III B) ---------------------------------------------------------------
+// A device tensor with named legs, row-major in the order of `legs`.
+template <typename T>
+struct DT {
+  T* p = nullptr;
+  std::vector<int> legs;
+  std::vector<int64_t> dims;
+  int64_t size() const {
+    int64_t n = 1;
+    for (int64_t d : dims) n *= d;
+    return n;
+  }
+  int pos(int leg) const {
+    for (size_t i = 0; i < legs.size(); ++i)
+      if (legs[i] == leg) return (int)i;
+    return -1;
+  }
+};
+
+// t with its legs in `order` (a copy through the permute kernel unless already so)
+template <typename T>
+int reorder(Arena& ar, const DT<T>& t, const std::vector<int>& order, DT<T>* out, cudaStream_t s) {
+  if (order == t.legs) {
+    *out = t;
+    return CBC_OK;
+  }
+  std::vector<int> perm(order.size());
+  DT<T> r;
+  r.legs = order;
+  for (size_t i = 0; i < order.size(); ++i) {
+    perm[i] = t.pos(order[i]);
+    if (perm[i] < 0) return fail(CBC_ERR_INVALID_ARG, "tree planner: leg %d missing", order[i]);
+    r.dims.push_back(t.dims[perm[i]]);
+  }
+  r.p = ar.get<T>((size_t)t.size());
+  CKA(r.p);
+  CK(permute<T>(t.p, r.p, (int)t.legs.size(), t.dims.data(), perm.data(), s));
+  *out = r;
+  return CBC_OK;
+}
+
+// Contract A and B over every leg they share; the result has A's other legs, then B's.
+template <typename T>
+int contract(Arena& ar, const Prec& pr, bool fwd, const DT<T>& A, const DT<T>& B, DT<T>* C,
+             cudaStream_t s) {
+  std::vector<int> shared, fa, fb;
+  for (int l : A.legs) (B.pos(l) >= 0 ? shared : fa).push_back(l);
+  for (int l : B.legs)
+    if (A.pos(l) < 0) fb.push_back(l);
+  std::vector<int> oa = fa, ob = shared;
+  oa.insert(oa.end(), shared.begin(), shared.end());
+  ob.insert(ob.end(), fb.begin(), fb.end());
+  DT<T> A2, B2;
+  int rc = reorder(ar, A, oa, &A2, s);
+  if (rc != CBC_OK) return rc;
+  rc = reorder(ar, B, ob, &B2, s);
+  if (rc != CBC_OK) return rc;
+  int64_t M = 1, K = 1, N = 1;
+  DT<T> c;
+  for (int l : fa) {
+    M *= A.dims[A.pos(l)];
+    c.legs.push_back(l);
+    c.dims.push_back(A.dims[A.pos(l)]);
+  }
+  for (int l : shared) K *= A.dims[A.pos(l)];
+  for (int l : fb) {
+    N *= B.dims[B.pos(l)];
+    c.legs.push_back(l);
+    c.dims.push_back(B.dims[B.pos(l)]);
+  }
+  if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX)
+    return fail(CBC_ERR_UNSUPPORTED, "tree planner: contraction dimension beyond 2^31");
+  c.p = ar.get<T>((size_t)(M * N));
+  CKA(c.p);
+  CK(tgemm<T>(pr, fwd, false, (int)M, (int)N, (int)K, A2.p, View::rowmajor(K), false, B2.p,
+              View::rowmajor(N), false, c.p, View::rowmajor(N), s));
+  *C = c;
+  return CBC_OK;
+}
+
+// leg labels of one node contraction
+constexpr int LG_SIN = 0, LG_SOUT = 1, LG_AP = 2, LG_BP = 3, LG_XP = 4;
+inline int lg_a(int j) { return 10 + 3 * j; }
+inline int lg_b(int j) { return 11 + 3 * j; }
+inline int lg_x(int j) { return 12 + 3 * j; }
+
+template <typename T>
+int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
+             Net* out) {
+  cudaStream_t s = st.stream;
+  const int n = st.n;
+  const auto& ch = st.children;
+  Arena ar(s);
+  int* d_int = ar.get<int>(4);
+  double* d_dbl = ar.get<double>(4);
+  CKA(d_int);
+  CKA(d_dbl);
+  CK(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(d_dbl, 0, 4 * sizeof(double), s));
+  Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + 1, d_dbl + 2};
+  Prec pr;
+  pr.mixed = (o.precision == CBC_PREC_MIXED);
+  pr.s_fwd = o.slices_fwd;
+  pr.s_bwd = o.slices_bwd;
+  pr.ar = &ar;
+  pr.status = sc.status;
+  const T one = host_one<T>();
+  // post-order (children first)
+  std::vector<int> post;
+  {
+    std::vector<std::pair<int, bool>> stack{{st.root, false}};
+    while (!stack.empty()) {
+      auto [v, done] = stack.back();
+      stack.pop_back();
+      if (done) {
+        post.push_back(v);
+      } else {
+        stack.push_back({v, true});
+        for (int j = (int)ch[v].size() - 1; j >= 0; --j) stack.push_back({ch[v][j], false});
+      }
+    }
+  }
+  auto tensT = [&](int i) {
+    DT<T> t;
+    t.p = static_cast<T*>(st.data[i]);
+    t.legs = {LG_AP, LG_SIN};
+    t.dims = {st.bond[i], st.phys[i]};
+    for (size_t j = 0; j < ch[i].size(); ++j) {
+      t.legs.push_back(lg_a((int)j));
+      t.dims.push_back(st.bond[ch[i][j]]);
+    }
+    return t;
+  };
+  auto tensW = [&](int i) {
+    DT<T> t;
+    t.p = static_cast<T*>(op.data[i]);
+    t.legs = {LG_BP, LG_SOUT, LG_SIN};
+    t.dims = {op.bond[i], op.phys[i], op.phys[i]};
+    for (size_t j = 0; j < ch[i].size(); ++j) {
+      t.legs.push_back(lg_b((int)j));
+      t.dims.push_back(op.bond[ch[i][j]]);
+    }
+    return t;
+  };
+  // an environment (chi, b, a) of node c seen from its parent's child slot j (or parent)
+  auto env_on = [&](T* p, int64_t chi, int c, int x, int b, int a) {
+    DT<T> t;
+    t.p = p;
+    t.legs = {x, b, a};
+    t.dims = {chi, op.bond[c], st.bond[c]};
+    return t;
+  };
+  // T, the first environment, W, the remaining environments (pairwise, in this order)
+  auto contract_node = [&](int i, const std::vector<DT<T>>& envs, const std::vector<int>& legs_out,
+                           bool fwd, DT<T>* res) -> int {
+    DT<T> cur = tensT(i), nxt;
+    int rc;
+    size_t e = 0;
+    if (!envs.empty()) {
+      rc = contract(ar, pr, fwd, cur, envs[0], &nxt, s);
+      if (rc != CBC_OK) return rc;
+      cur = nxt;
+      e = 1;
+    }
+    rc = contract(ar, pr, fwd, cur, tensW(i), &nxt, s);
+    if (rc != CBC_OK) return rc;
+    cur = nxt;
+    for (; e < envs.size(); ++e) {
+      rc = contract(ar, pr, fwd, cur, envs[e], &nxt, s);
+      if (rc != CBC_OK) return rc;
+      cur = nxt;
+    }
+    return reorder(ar, cur, legs_out, res, s);
+  };
+
+  // ---- step 1, Eq. (cbc_tree_first_contraction): subtree environments, leaves first
+  std::vector<T*> Lsub(n, nullptr);
+  std::vector<int64_t> chi_sub(n, 1);
+  for (int i : post) {
+    if (i == st.root) continue;
+    std::vector<DT<T>> envs;
+    std::vector<int> lo{LG_SOUT};
+    int64_t m = st.phys[i];
+    for (size_t j = 0; j < ch[i].size(); ++j) {
+      const int c = ch[i][j];
+      envs.push_back(env_on(Lsub[c], chi_sub[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j)));
+      lo.push_back(lg_x((int)j));
+      m *= chi_sub[c];
+    }
+    lo.push_back(LG_BP);
+    lo.push_back(LG_AP);
+    DT<T> M;
+    int rc = contract_node(i, envs, lo, true, &M);
+    if (rc != CBC_OK) return rc;
+    int k = 0;
+    rc = compress_rows<T>(ar, pr, M.p, (int)m, (int)(op.bond[i] * st.bond[i]), max_bond, tol, o,
+                          sc, s, &Lsub[i], &k);
+    if (rc != CBC_OK) return rc;
+    chi_sub[i] = k;
+  }
+  // ---- step 2, Eq. (cbc_tree_second_contraction): complements, root first
+  std::vector<T*> Ldown(n, nullptr);
+  std::vector<int64_t> chi_down(n, 1);
+  Ldown[st.root] = ar.get<T>(1);
+  CKA(Ldown[st.root]);
+  CK(cudaMemcpyAsync(Ldown[st.root], &one, sizeof(T), cudaMemcpyHostToDevice, s));
+  for (auto it = post.rbegin(); it != post.rend(); ++it) {
+    const int i = *it;
+    for (size_t jk = 0; jk < ch[i].size(); ++jk) {
+      const int k = ch[i][jk];
+      std::vector<DT<T>> envs{env_on(Ldown[i], chi_down[i], i, LG_XP, LG_BP, LG_AP)};
+      std::vector<int> lo{LG_SOUT, LG_XP};
+      int64_t m = st.phys[i] * chi_down[i];
+      for (size_t j = 0; j < ch[i].size(); ++j) {
+        if (j == jk) continue;
+        const int c = ch[i][j];
+        envs.push_back(env_on(Lsub[c], chi_sub[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j)));
+        lo.push_back(lg_x((int)j));
+        m *= chi_sub[c];
+      }
+      lo.push_back(lg_b((int)jk));
+      lo.push_back(lg_a((int)jk));
+      DT<T> M;
+      int rc = contract_node(i, envs, lo, true, &M);
+      if (rc != CBC_OK) return rc;
+      int kk = 0;
+      rc = compress_rows<T>(ar, pr, M.p, (int)m, (int)(op.bond[k] * st.bond[k]), max_bond, tol, o,
+                            sc, s, &Ldown[k], &kk);
+      if (rc != CBC_OK) return rc;
+      chi_down[k] = kk;
+    }
+  }
+  // ---- step 3, Eqs. (cbc_tree_third_contraction), (cbc_tree_qr), (cbc_final_contraction)
+  out->kind = 0;
+  out->n = n;
+  out->root = st.root;
+  out->parent = st.parent;
+  out->phys = st.phys;
+  out->bond.assign(n, 1);
+  out->children = st.children;
+  out->cplx = st.cplx;
+  out->stream = s;
+  out->data.assign(n, nullptr);
+  out->numel.assign(n, 0);
+  std::vector<T*> R(n, nullptr);
+  std::vector<int64_t> chi_r(n, 1);
+  for (int i : post) {
+    // Z[(sigma', chi'_c...), (b_p, a_p)] = T W prod_c R^[c]; shared by S^[i] and R^[i]
+    std::vector<DT<T>> envs;
+    std::vector<int> lo{LG_SOUT};
+    int64_t nz = st.phys[i];
+    for (size_t j = 0; j < ch[i].size(); ++j) {
+      const int c = ch[i][j];
+      envs.push_back(env_on(R[c], chi_r[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j)));
+      lo.push_back(lg_x((int)j));
+      nz *= chi_r[c];
+    }
+    lo.push_back(LG_BP);
+    lo.push_back(LG_AP);
+    DT<T> Z;
+    int rc = contract_node(i, envs, lo, false, &Z);
+    if (rc != CBC_OK) return rc;
+    const int nba = (int)(op.bond[i] * st.bond[i]);
+    const int m = (int)chi_down[i];
+    const int nzi = (int)nz;
+    const int cn = (m <= nzi) ? m : nzi;
+    T* node = nullptr;
+    CK(cudaMallocAsync(reinterpret_cast<void**>(&node),
+                       sizeof(T) * std::max<size_t>((size_t)cn * nzi, (size_t)m * nzi), s));
+    out->data[i] = node;
+    out->numel[i] = (int64_t)cn * nzi;
+    // S^[i] = L^[(p_i, i)] contracted with Z over (b_p, a_p)
+    if (i == st.root || m <= nzi)
+      CK(tgemm<T>(pr, false, false, m, nzi, nba, Ldown[i], View::rowmajor(nba), false, Z.p,
+                  View::transposed(nba), false, node, View::rowmajor(nzi), s));
+    if (i == st.root) {
+      CK(normalize_inplace<T>(node, (int64_t)nzi, sc.log_out, sc.status, sc.scratch, s));
+      out->bond[i] = 1;
+      continue;
+    }
+    if (m <= nzi) {
+      rc = lq_rows_inplace<T>(ar, pr, node, m, nzi, sc, s);
+      if (rc != CBC_OK) return rc;
+    } else {
+      CK(fill_identity<T>(node, nzi, s));
+    }
+    // R^[i] = Q* Z over (sigma', chi'_c...)
+    T* Rn = ar.get<T>((size_t)cn * nba);
+    CKA(Rn);
+    CK(tgemm<T>(pr, false, false, cn, nba, nzi, node, View::rowmajor(nzi), true, Z.p,
+                View::rowmajor(nba), false, Rn, View::rowmajor(nba), s));
+    CK(normalize_inplace<T>(Rn, (int64_t)cn * nba, sc.log_out, sc.status, sc.scratch, s));
+    R[i] = Rn;
+    chi_r[i] = cn;
+    out->bond[i] = cn;
+  }
+  int h[2];
+  double hl = 0.0;
+  CK(cudaMemcpyAsync(h, sc.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hl, sc.log_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h[0] != 0) return status_to_rc(h[0]);
+  out->log_norm = hl;
+  return CBC_OK;
+}
+
 bool is_chain(const Net& t) {
   for (int i = 0; i < t.n; ++i)
     if (t.parent[i] != i - 1) return false;
@@ -337,9 +645,12 @@ int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Op
   if (o.precision == CBC_PREC_MIXED && (o.slices_fwd < 2 || o.slices_fwd > 5 || o.slices_bwd < 2 ||
                                         o.slices_bwd > 5))
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply: slice counts must be in [2, 5]");
-  if (!is_chain(st)) return fail(CBC_ERR_UNSUPPORTED, "cbc_apply: general trees are not built yet");
-  if (st.cplx) return run_tt<zdbl>(st, op, max_bond, tol, o, out);
-  return run_tt<double>(st, op, max_bond, tol, o, out);
+  if (is_chain(st)) {
+    if (st.cplx) return run_tt<zdbl>(st, op, max_bond, tol, o, out);
+    return run_tt<double>(st, op, max_bond, tol, o, out);
+  }
+  if (st.cplx) return run_tree<zdbl>(st, op, max_bond, tol, o, out);
+  return run_tree<double>(st, op, max_bond, tol, o, out);
 }
 
 }  // namespace cbc

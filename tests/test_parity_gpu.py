@@ -148,3 +148,44 @@ def test_batched_heterogeneous(precision, bar):
         _cbc.ttn_destroy(h)
     for h in ho:
         _cbc.ttno_destroy(h)
+
+
+# ---------------------------------------------------------------------------------------
+# trees (Sec. III B): binary trees with leaf-only physical legs, T-trees, fork trees
+# ---------------------------------------------------------------------------------------
+TREE_CASES = [
+    dict(L=2, chi=6, D=3, max_bond=64, dtype=np.float64),                  # exact
+    dict(L=3, chi=8, D=4, max_bond=3, dtype=np.float64, seed=1),
+    dict(L=2, chi=5, D=2, max_bond=4, d=3, dtype=np.complex128, seed=2),
+    dict(topo="ttree", L=3, d=2, chi=6, D=3, max_bond=5, dtype=np.complex128, seed=4),
+    dict(topo="ftps", L=3, d=2, chi=6, D=2, max_bond=5, dtype=np.float64, seed=5),
+    dict(L=4, chi=16, D=4, max_bond=16, dtype=np.float32, seed=0),        # config-3 family
+]
+
+
+@pytest.mark.parametrize("case", TREE_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()
+                                                                      if k != "dtype"))
+def test_tree_fp64(case):
+    _compare(make_problem(3, **case))
+
+
+@pytest.mark.parametrize("case", TREE_CASES[1:4] + TREE_CASES[5:], ids=lambda c: str(c.get("seed", 0)))
+def test_tree_mixed(case):
+    _compare_mixed(make_problem(3, **case))
+
+
+def test_tree_exact_against_brute_force():
+    p = make_problem(3, L=2, chi=6, D=3, max_bond=10 ** 6, dtype=np.float64)
+    got, bonds, log_norm = run_gpu(p)
+    ex = brute.apply_dense(p.state.parent, p.state.tensors, p.op.tensors)
+    v = brute.dense_state(p.state.parent, got) * np.exp(log_norm)
+    assert np.linalg.norm(v - ex) <= 1e-12 * np.linalg.norm(ex)
+
+
+def test_cfg3_full_fp64():
+    """Perfect binary tree of depth 6 (64 leaves, d=2), chi=64, D=8, cap 64, float32."""
+    _compare(make_problem(3))
+
+
+def test_cfg3_full_mixed():
+    _compare_mixed(make_problem(3))
