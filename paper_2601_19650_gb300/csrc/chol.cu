@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
           if (threadIdx.x == 0) s_bad = 1;
           break;
         }
-        const double rp = rcp64(piv);
-        const double rc = sqrt(rp);  // 1 / sqrt(piv)
+        const double rc = rsqrt64(piv);  // 1 / sqrt(piv)
+        const double rp = rc * rc;        // 1 / piv
         // trailing update with the unscaled column (divide by piv), then scale column
         for (int t = threadIdx.x; t < nb * nb; t += blockDim.x) {
           int i = t / nb, l = t % nb;

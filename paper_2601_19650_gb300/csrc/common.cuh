@@ -131,6 +131,24 @@ __device__ __forceinline__ double rcp64(double x) {
   return ldexp(r, -ex);
 }
 
+// 1/sqrt(x) for finite x > 0 by Newton-Raphson on f(r) = 1/r^2 - x,
+// r <- r (3 - x r^2) / 2, seeded with the single-precision reciprocal square root of
+// the mantissa (an even exponent is split off): ~23 -> 46 -> 92 correct bits in six
+// dependent FP64 operations.
+__device__ __forceinline__ double rsqrt64(double x) {
+  int ex;
+  double f = frexp(x, &ex);  // x = f 2^ex, f in [0.5, 1)
+  if (ex & 1) {              // make the exponent even
+    f *= 2.0;
+    ex -= 1;
+  }
+  double r = (double)rsqrtf((float)f);
+  double h = 0.5 * f;
+  r = r * fma(-h * r, r, 1.5);
+  r = r * fma(-h * r, r, 1.5);
+  return ldexp(r, -ex / 2);
+}
+
 // warp / block reductions -----------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -13,7 +13,7 @@
 //      one warp per eigenvalue (a dependent chain of FP64 divisions per Sturm step is
 //      slow on this part; the estimates only need to separate the eigenvalues).
 //   3. Eigenvectors of T for the candidates (the kmax largest) by FP64 inverse
-//      iteration seeded with those estimates (one LU, six solves); eigenvalues =
+//      iteration seeded with those estimates (one LU, four solves); eigenvalues =
 //      Rayleigh quotients.
 //   4. The rank rule (max_bond, relative floor, tolerance) on the refined eigenvalues,
 //      with the discarded weight taken as trace(T) minus the kept eigenvalues.
@@ -436,7 +436,7 @@ __global__ void bisect32_kernel(const double* d, const double* e, int m, float* 
 // One thread per kept candidate.  The LU of T - sigma I with partial pivoting (the
 // layout of LAPACK's tridiagonal factorisation) lives in shared memory, [i][thread],
 // with the pivots stored as reciprocals so the solves are division free.  Candidates
-// whose single-precision eigenvalues lie within 1e-5 of the spectral radius of each
+// whose single-precision eigenvalues lie within 1e-4 of the spectral radius of each
 // other form a cluster that the thread of its first member computes in order, each new
 // vector orthogonalised against the earlier ones.  The eigenvalue is the FP64 Rayleigh
 // quotient of the converged vector.
@@ -475,9 +475,9 @@ __global__ void invit_kernel(InvArgs a) {
   const double span = fmax(fabs((double)a.lam32[0]), fabs((double)a.lam32[m - 1])) + DBL_MIN;
   // Each solve shrinks the components along eigenvectors at distance delta by about
   // |lambda - sigma| / delta with |lambda - sigma| ~ 1e-7 span (single-precision
-  // shifts); six solves reach FP64 accuracy for delta >= 1e-5 span.  Closer pairs are
+  // shifts); four solves reach FP64 accuracy for delta >= 1e-4 span.  Closer pairs are
   // handled as a cluster with explicit orthogonalisation.
-  const double ortol = 1e-5 * span;
+  const double ortol = 1e-4 * span;
   if (jj > 0 && (double)a.lam32[jj - 1] - (double)a.lam32[jj] <= ortol) return;
   int cend = jj + 1;
   while (cend < K && (double)a.lam32[cend - 1] - (double)a.lam32[cend] <= ortol) ++cend;
@@ -526,7 +526,7 @@ __global__ void invit_kernel(InvArgs a) {
       uint32_t h = hash32((uint32_t)(i * 7919 + jc * 104729 + 17));
       SH(b, i) = ((double)(h & 0xffffff) / 16777216.0) - 0.5;
     }
-    for (int it = 0; it < 6; ++it) {
+    for (int it = 0; it < 4; ++it) {
       // forward: L y = P b
       double carry = SH(b, 0);
       for (int i = 0; i < m - 1; ++i) {

@@ -352,38 +352,75 @@ __device__ __forceinline__ T load_op(const T* src, const View& v, int r, int k, 
   return conj ? ops<T>::conj(x) : x;
 }
 
+// exponent of |x| (biased-exponent field) without FP64 arithmetic: max|x| < 2^e with
+// e = field - 1022 for normal numbers; 0 maps to a floor value
+__device__ __forceinline__ int expo_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  if (b == 0ull) return -2000;
+  const int f = (int)(b >> 52);
+  if (f == 0x7ff) return 0x40000000;  // Inf or NaN
+  if (f == 0) return -1021 - (__clzll((long long)b) - 12);  // subnormal: roughly
+  return f - 1022;
+}
+
+// exponent of every logical row: 32 rows x 256 k per CTA, read along the contiguous
+// index, reduced in shared memory, combined across CTAs with an integer atomicMax
 template <typename T, bool SIDE_B>
-__global__ void expo_kernel(const T* src, View v, int R, int K, int nrows, int rowlanes,
-                            int* expo, int* status) {
+__global__ void __launch_bounds__(256) expo_kernel(const T* src, View v, int R, int K,
+                                                   int rowlanes, int* expo, int* status) {
   using O = ops<T>;
-  double mx = 0.0;
-  int r;
-  if (rowlanes) {  // one thread per logical row, consecutive threads on consecutive rows
-    r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
+  __shared__ int red[32][9];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 256;
+  int best[4] = {-2000, -2000, -2000, -2000};
+  if (rowlanes) {  // lane -> row, warp -> k stripe
+    const int r = r0 + lane;
+    int b = -2000;
     if (r < R)
-      for (int k = 0; k < K; ++k) {
-        T x = load_op<T, SIDE_B>(src, v, r, k, 0);
-        mx = fmax(mx, fmax(fabs(O::real(x)), fabs(O::imag(x))));
+      for (int k = k0 + w; k < min(K, k0 + 256); k += 8) {
+        const T x = load_op<T, SIDE_B>(src, v, r, k, 0);
+        b = max(b, max(expo_bits(O::real(x)), expo_bits(O::imag(x))));
       }
-  } else {         // one warp per logical row, lanes along K
-    r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= nrows) return;
-    if (r < R)
-      for (int k = lane; k < K; k += 32) {
-        T x = load_op<T, SIDE_B>(src, v, r, k, 0);
-        mx = fmax(mx, fmax(fabs(O::real(x)), fabs(O::imag(x))));
-      }
+    red[lane][w] = b;
+  } else {         // lane -> k, warp -> row group of 4
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + w * 4 + q;
+      int b = -2000;
+      if (r < R)
+        for (int k = k0 + lane; k < min(K, k0 + 256); k += 32) {
+          const T x = load_op<T, SIDE_B>(src, v, r, k, 0);
+          b = max(b, max(expo_bits(O::real(x)), expo_bits(O::imag(x))));
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane != 0) return;
+      for (int o = 16; o > 0; o >>= 1) b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+      best[q] = b;
+    }
+    if (lane == 0)
+      for (int q = 0; q < 4; ++q) red[w * 4 + q][0] = best[q];
   }
-  if (!isfinite(mx)) {
-    set_status(status, CBC_ERR_NUMERICAL);
-    mx = 0.0;
+  __syncthreads();
+  if (tid < 32) {
+    int b = red[tid][0];
+    if (rowlanes)
+      for (int q = 1; q < 8; ++q) b = max(b, red[tid][q]);
+    if (b >= 0x40000000) set_status(status, CBC_ERR_NUMERICAL);  // Inf or NaN in the row
+    if (r0 + tid < R && b > -2000) atomicMax(expo + r0 + tid, b);
   }
-  expo[r] = (mx > 0.0) ? ilogb(mx) + 1 : 0;  // max|x| < 2^e
+}
+
+// Balanced base-256 digits of t = x 2^(7-e) (|t| < 128): N = rint(t 256^(S-1)) is formed
+// by one FP64 scaling and rounding; the digits q_{S-1} .. q_1 are the balanced
+// remainders of N by 256 (in [-128, 127]) and q_0 the remaining quotient (|q_0| <= 128),
+// so t = sum_s q_s 256^-s up to 0.5 256^-(S-1).  Integer operations only after the
+// rounding.
+__device__ __forceinline__ void digits(double x, int e, int S, int (&q)[5]) {
+  long long N = __double2ll_rn(ldexp(x, 7 + 8 * (S - 1) - e));
+  for (int sl = S - 1; sl >= 1; --sl) {
+    const long long hi = (N + 128) >> 8;  // floor((N + 128) / 256)
+    q[sl] = (int)(N - (hi << 8));
+    N = hi;
+  }
+  q[0] = (int)N;
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(double lo, double hi) {
@@ -410,7 +447,10 @@ __global__ void __launch_bounds__(256) slice_kernel(const T* src, View v, int co
     else
       tile[q][lane] = x;
   }
-  if (tid < 32) se[tid] = expo[r0 + tid];
+  if (tid < 32) {
+    const int e = expo[r0 + tid];
+    se[tid] = (e < -1100) ? 0 : e;  // all-zero (or padding) rows
+  }
   __syncthreads();
   // 32 logical rows x 32 logical k; real: one bf16 per (row, k); complex: one bf16 pair
   constexpr int NPR = (CPLX && SIDE_B) ? 2 : 1;  // packed rows per logical row
@@ -422,13 +462,10 @@ __global__ void __launch_bounds__(256) slice_kernel(const T* src, View v, int co
     const int e = se[lr];
     const int prow = (r0 + lr) * NPR + half;
     if constexpr (!CPLX) {
-      double t = ldexp(O::real(x), 7 - e);
+      int q[5];
+      digits(O::real(x), e, S, q);
       __nv_bfloat16* o = out + (size_t)prow * K2p + (k0 + kk);
-      for (int sl = 0; sl < S; ++sl) {
-        const double q = rint(t);
-        o[sl * plane] = __float2bfloat16_rn((float)q);
-        t = (t - q) * 256.0;
-      }
+      for (int sl = 0; sl < S; ++sl) o[sl * plane] = __float2bfloat16_rn((float)q[sl]);
     } else {
       double a0, a1;  // the two K positions of this (packed row, k)
       const double xr = O::real(x), xi = O::imag(x);
@@ -442,14 +479,11 @@ __global__ void __launch_bounds__(256) slice_kernel(const T* src, View v, int co
         a0 = xi;   // row 2n+1: [ bi,  br ]
         a1 = xr;
       }
-      double t0 = ldexp(a0, 7 - e), t1 = ldexp(a1, 7 - e);
+      int q0[5], q1[5];
+      digits(a0, e, S, q0);
+      digits(a1, e, S, q1);
       uint32_t* o = reinterpret_cast<uint32_t*>(out) + ((size_t)prow * K2p + 2 * (k0 + kk)) / 2;
-      for (int sl = 0; sl < S; ++sl) {
-        const double q0 = rint(t0), q1 = rint(t1);
-        o[sl * (plane / 2)] = bf16x2_bits(q0, q1);
-        t0 = (t0 - q0) * 256.0;
-        t1 = (t1 - q1) * 256.0;
-      }
+      for (int sl = 0; sl < S; ++sl) o[sl * (plane / 2)] = bf16x2_bits(q0[sl], q1[sl]);
     }
   }
 }
@@ -470,11 +504,9 @@ void pack_operand(const T* src, const View& v, bool conj, int R, int K, int rows
   const int klog = CPLX ? K2p / 2 : K2p;                           // logical K (padded)
   const bool rl = rows_contiguous<SIDE_B>(v);
   note_launches(CBC_K_AUX, 2);
-  if (rl)
-    expo_kernel<T, SIDE_B><<<(nrows + 127) / 128, 128, 0, s>>>(src, v, R, K, nrows, 1, expo, status);
-  else
-    expo_kernel<T, SIDE_B><<<(nrows * 32 + 255) / 256, 256, 0, s>>>(src, v, R, K, nrows, 0, expo,
-                                                                     status);
+  cudaMemsetAsync(expo, 0xC0, sizeof(int) * nrows, s);  // a large negative floor
+  expo_kernel<T, SIDE_B><<<dim3((K + 255) / 256, (nrows + 31) / 32), 256, 0, s>>>(
+      src, v, R, K, rl ? 1 : 0, expo, status);
   dim3 grid(klog / 32, nrows / 32);
   const size_t plane = (size_t)rows_pad * K2p;
   if (rl)
