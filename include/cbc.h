@@ -123,11 +123,15 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
               const cbc_options* opt, ttn_t* out);
 
 /* Apply n operators to n states (independent instances of any sizes and topologies)
- * and compress each, as n calls of cbc_apply that run concurrently: up to `workers`
- * host threads (<= 0: min(n, 16)) each drive instances, so the latency-bound steps of
- * different instances (truncation eigensolves, Cholesky factorisations) overlap on the
- * GPU.  Instance j runs on the stream of states[j]; give every state its own stream for
- * the work to overlap.
+ * and compress each; the results equal n calls of cbc_apply.  Tensor-train instances
+ * with identical shapes (sites, physical and bond dimensions, real/complex), max_bond
+ * and tol form groups of up to 32 that run in lockstep: every step of Sec. III A is one
+ * launch for the whole group, on the stream of the group's first state (the group waits
+ * for the other members' streams first and has finished when the call returns).  A
+ * group whose members choose different ranks at some cut is rerun member by member.
+ * Groups and the remaining instances are driven by up to `workers` host threads (<= 0:
+ * min(#tasks, 16)) so their latency-bound steps overlap on the GPU; a lone instance j
+ * runs on the stream of states[j], so give every state its own stream.
  *   max_bond, tol  [n] host arrays (per instance), or NULL for 0 (no cap / no tolerance)
  *   opt            shared by all instances (NULL for defaults)
  *   outs           [n] host array, receives the output handles (NULL where failed)

@@ -243,6 +243,18 @@ int ttn_get_node(ttn_t t, int node, void* dst, int dst_on_device, int dtype) {
   return CBC_OK;
 }
 
+static int parse_options(const cbc_options* opt, Options* o) {
+  if (opt) {
+    o->precision = opt->precision;
+    if (opt->eps_rank > 0) o->eps_rank = opt->eps_rank;
+    if (opt->slices_fwd > 0) o->slices_fwd = opt->slices_fwd;
+    if (opt->slices_bwd > 0) o->slices_bwd = opt->slices_bwd;
+  }
+  if (o->precision != CBC_PREC_FP64 && o->precision != CBC_PREC_MIXED)
+    return fail(CBC_ERR_INVALID_ARG, "cbc_apply: bad precision %d", o->precision);
+  return CBC_OK;
+}
+
 int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_options* opt,
               ttn_t* out) {
   if (!out) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: out is NULL");
@@ -253,14 +265,8 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_op
     return fail(CBC_ERR_TOPOLOGY_MISMATCH, "cbc_apply: state and operator trees differ");
   if (!std::isfinite(tol)) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: tol is not finite");
   Options o;
-  if (opt) {
-    o.precision = opt->precision;
-    if (opt->eps_rank > 0) o.eps_rank = opt->eps_rank;
-    if (opt->slices_fwd > 0) o.slices_fwd = opt->slices_fwd;
-    if (opt->slices_bwd > 0) o.slices_bwd = opt->slices_bwd;
-  }
-  if (o.precision != CBC_PREC_FP64 && o.precision != CBC_PREC_MIXED)
-    return fail(CBC_ERR_INVALID_ARG, "cbc_apply: bad precision %d", o.precision);
+  int prc = parse_options(opt, &o);
+  if (prc != CBC_OK) return prc;
   auto* res = new cbc_ttn_s();
   int rc = run_cbc(*state, *op, max_bond, tol, o, res);
   if (rc != CBC_OK) {
@@ -277,19 +283,97 @@ int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply_batched: bad arguments");
   for (int j = 0; j < n; ++j) outs[j] = nullptr;
   if (n == 0) return CBC_OK;
-  if (workers <= 0) workers = std::min(n, 16);
-  workers = std::max(1, std::min(workers, n));
+  // groups: chains with identical shapes, max_bond and tol (at most kMaxGroup each) run
+  // in lockstep, one launch per step for the whole group; the rest one by one
+  constexpr int kMaxGroup = 32;
+  std::vector<std::vector<int>> tasks;
+  {
+    std::vector<int> open_task;  // index into tasks of the open group per signature
+    std::vector<int> leader;     // first member of each open group
+    for (int j = 0; j < n; ++j) {
+      const ttn_t st = states[j];
+      const ttno_t op = ops[j];
+      int home = -1;
+      if (st && op && st->kind == 0 && op->kind == 1)
+        for (size_t q = 0; q < leader.size(); ++q) {
+          const int l = leader[q];
+          const ttn_t s2 = states[l];
+          const ttno_t o2 = ops[l];
+          if (tasks[open_task[q]].size() < (size_t)kMaxGroup && s2->cplx == st->cplx &&
+              s2->n == st->n && s2->parent == st->parent && s2->phys == st->phys &&
+              s2->bond == st->bond && o2->bond == op->bond && o2->parent == op->parent &&
+              o2->phys == op->phys && (max_bond ? max_bond[l] == max_bond[j] : true) &&
+              (tol ? tol[l] == tol[j] : true)) {
+            home = open_task[q];
+            break;
+          }
+        }
+      if (home < 0) {
+        tasks.push_back({j});
+        if (st && op && st->kind == 0 && op->kind == 1) {
+          leader.push_back(j);
+          open_task.push_back((int)tasks.size() - 1);
+        }
+      } else {
+        tasks[home].push_back(j);
+      }
+    }
+  }
+  const int nt = (int)tasks.size();
+  if (workers <= 0) workers = std::min(nt, 16);
+  workers = std::max(1, std::min(workers, nt));
   int dev = 0;
   cudaGetDevice(&dev);
   std::vector<int> rc(n, CBC_OK);
   std::vector<std::string> msg(n);
+  auto one = [&](int j) {
+    rc[j] = cbc_apply(states[j], ops[j], max_bond ? max_bond[j] : 0, tol ? tol[j] : 0.0, opt,
+                      &outs[j]);
+    if (rc[j] != CBC_OK) msg[j] = g_last_error;
+  };
+  auto group = [&](const std::vector<int>& t) {
+    const int j0 = t[0];
+    Options o;
+    int prc = parse_options(opt, &o);
+    if (prc == CBC_OK && !std::isfinite(tol ? tol[j0] : 0.0))
+      prc = fail(CBC_ERR_INVALID_ARG, "cbc_apply: tol is not finite");
+    if (prc != CBC_OK) {
+      for (int j : t) {
+        rc[j] = prc;
+        msg[j] = g_last_error;
+      }
+      return;
+    }
+    std::vector<const Net*> sv, ov;
+    std::vector<Net*> res;
+    for (int j : t) {
+      sv.push_back(states[j]);
+      ov.push_back(ops[j]);
+      res.push_back(new cbc_ttn_s());
+    }
+    const int grc = run_cbc_group(sv, ov, max_bond ? max_bond[j0] : 0, tol ? tol[j0] : 0.0, o, res);
+    if (grc == CBC_OK) {
+      for (size_t q = 0; q < t.size(); ++q) outs[t[q]] = static_cast<ttn_t>(res[q]);
+      return;
+    }
+    for (Net* r : res) delete r;
+    if (grc == kGroupSplit) {  // members chose different ranks: one by one
+      for (int j : t) one(j);
+      return;
+    }
+    for (int j : t) {
+      rc[j] = grc;
+      msg[j] = g_last_error;
+    }
+  };
   std::atomic<int> next{0};
   auto work = [&]() {
     cudaSetDevice(dev);
-    for (int j = next++; j < n; j = next++) {
-      rc[j] = cbc_apply(states[j], ops[j], max_bond ? max_bond[j] : 0, tol ? tol[j] : 0.0, opt,
-                        &outs[j]);
-      if (rc[j] != CBC_OK) msg[j] = g_last_error;
+    for (int q = next++; q < nt; q = next++) {
+      if (tasks[q].size() == 1)
+        one(tasks[q][0]);
+      else
+        group(tasks[q]);
     }
   };
   std::vector<std::thread> pool;

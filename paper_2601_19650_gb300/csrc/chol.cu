@@ -5,7 +5,8 @@
 // the GPU path forms G = S S^H, factors G = C C^H, and solves Q = C^{-1} S; doing it
 // twice (CholeskyQR2) restores orthonormality to FP64 round-off.
 //
-// Cholesky: a cooperative launch with 32-wide column blocks.  Per block, CTA 0 factors
+// Cholesky: one group of CTAs that wait on each other (a thread-block cluster of up to
+// 16 CTAs, else a cooperative launch), 32-wide column blocks.  Per block, CTA 0 factors
 // the diagonal block in shared memory, every other row of the panel is solved by one
 // warp (shuffles carry the solved entries), and the trailing lower triangle is updated
 // from a shared-memory copy of the panel; bounded grid barriers separate the phases.
@@ -50,6 +51,7 @@ struct CholArgs {
   int m;
   int* status;
   GridBarrier* bar;
+  int P;  // CTAs per matrix; CTA b works on matrix b / P (G + (b / P) m^2, bar + b / P)
 };
 
 // G (row-major m x m, Hermitian, lower triangle read) -> C (lower triangle), G = C C^H
@@ -60,7 +62,9 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
   T* pan = reinterpret_cast<T*>(sm_raw);  // panel rows [b0, m) x NB, or the diag block
   __shared__ double s_rd[NB];             // reciprocals of the diagonal of the block
   __shared__ int s_bad;
-  const int m = a.m, P = gridDim.x, cta = blockIdx.x;
+  const int m = a.m, P = a.P, cta = blockIdx.x % P;
+  a.G += (int64_t)(blockIdx.x / P) * m * m;
+  a.bar += blockIdx.x / P;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int b0 = 0; b0 < m; b0 += NB) {
     const int nb = min(NB, m - b0);
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
       }
       __threadfence();
     }
-    if (!grid_sync(a.bar, a.status)) return;
+    if (!grid_sync(a.bar, a.status, (unsigned)P)) return;
     if (*((volatile int*)a.status) != 0) return;
     // (2) panel rows below: x C_bb^H = g, one warp per row (lane l holds entry l)
     {
@@ -128,7 +132,7 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
         if (lane < nb) row[lane] = x;
       }
     }
-    if (!grid_sync(a.bar, a.status)) return;
+    if (!grid_sync(a.bar, a.status, (unsigned)P)) return;
     // (3) trailing update of the lower triangle from a shared copy of the panel
     const int r0 = b0 + nb;
     if (r0 < m) {
@@ -141,9 +145,7 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
       const int64_t nt = (int64_t)rows * (rows + 1) / 2;
       for (int64_t t = (int64_t)cta * blockDim.x + threadIdx.x; t < nt; t += (int64_t)P * blockDim.x) {
         // t -> (i, c) with c <= i in the packed lower triangle
-        int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
-        while ((int64_t)i * (i + 1) / 2 > t) --i;
+        const int i = tri_row(t);
         const int c = (int)(t - (int64_t)i * (i + 1) / 2);
         T sacc = O::zero();
 #pragma unroll 8
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
         *g = ldg_cg(g) - sacc;
       }
     }
-    if (!grid_sync(a.bar, a.status)) return;
+    if (!grid_sync(a.bar, a.status, (unsigned)P)) return;
   }
 }
 
@@ -160,6 +162,8 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
 template <typename T, bool CSMEM>
 __global__ void trsm_cols_kernel(const T* C, T* S, int m, int n) {
   using O = ops<T>;
+  C += (int64_t)blockIdx.y * m * m;  // problem blockIdx.y of a batch
+  S += (int64_t)blockIdx.y * m * n;
   extern __shared__ unsigned char sm_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   T* cl = reinterpret_cast<T*>(sm_raw);  // packed lower triangle (CSMEM)
@@ -168,9 +172,7 @@ __global__ void trsm_cols_kernel(const T* C, T* S, int m, int n) {
   if (CSMEM) {
     const int64_t tot = (int64_t)m * (m + 1) / 2;
     for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
-      int i = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-      while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
-      while ((int64_t)i * (i + 1) / 2 > t) --i;
+      const int i = tri_row(t);
       const int l = (int)(t - (int64_t)i * (i + 1) / 2);
       cl[t] = C[(int64_t)i * m + l];
     }
@@ -202,10 +204,12 @@ __global__ void trsm_cols_kernel(const T* C, T* S, int m, int n) {
 }  // namespace
 
 template <typename T>
-cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cudaStream_t s) {
-  // FP64 is scarce per SM on this part: spread the trailing updates over many SMs
-  int P = std::max(1, std::min(num_sms, (m * m) / 256));
-  cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cudaStream_t s,
+                           int nb) {
+  // FP64 is scarce per SM on this part: spread the trailing updates over several SMs,
+  // one cluster of up to 16 CTAs per matrix when it fits (concurrent with other
+  // streams' work), else a cooperative launch over more SMs per matrix
+  cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier) * nb, s);
   if (err != cudaSuccess) return err;
   size_t shm = (size_t)std::max(m, NB) * NB * sizeof(T);
   if (shm > 48 * 1024) {
@@ -213,14 +217,25 @@ cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cud
     if (err != cudaSuccess) return err;
   }
   note_launches(CBC_K_CHOLQR, 1);
-  CholArgs<T> a{G, m, status, (GridBarrier*)bar};
-  void* args[] = {&a};
-  return cudaLaunchCooperativeKernel((const void*)chol_kernel<T>, dim3(P), dim3(TPB), args, shm, s);
+  int P = std::max(1, std::min(16, (m * m) / 256));
+  if (cluster_ctas((const void*)chol_kernel<T>, P, TPB, shm) == P) {
+    CholArgs<T> a{G, m, status, (GridBarrier*)bar, P};
+    void* args[] = {&a};
+    return launch_cluster((const void*)chol_kernel<T>, P, nb * P, TPB, shm, args, s);
+  }
+  P = std::max(1, std::min(num_sms, (m * m) / 256));
+  for (int b = 0; b < nb; ++b) {
+    CholArgs<T> a{G + (int64_t)b * m * m, m, status, (GridBarrier*)bar + b, P};
+    void* args[] = {&a};
+    err = cudaLaunchCooperativeKernel((const void*)chol_kernel<T>, dim3(P), dim3(TPB), args, shm, s);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
 }
 
 template <typename T>
 cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* bar, int num_sms,
-                            cudaStream_t s) {
+                            cudaStream_t s, int nb) {
   (void)status;
   (void)bar;
   (void)num_sms;
@@ -228,26 +243,27 @@ cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* b
   const size_t tri = (size_t)m * (m + 1) / 2 * sizeof(T);
   const size_t rest = (size_t)m * sizeof(double) + (size_t)nw * m * sizeof(T);
   note_launches(CBC_K_CHOLQR, 1);
+  const dim3 grid((n + nw - 1) / nw, nb);
   cudaError_t err;
   if (tri + rest <= 200 * 1024) {
     err = allow_max_smem((const void*)trsm_cols_kernel<T, true>);
     if (err != cudaSuccess) return err;
-    trsm_cols_kernel<T, true><<<(n + nw - 1) / nw, 32 * nw, tri + rest, s>>>(C, S, m, n);
+    trsm_cols_kernel<T, true><<<grid, 32 * nw, tri + rest, s>>>(C, S, m, n);
   } else {
     if (rest > 48 * 1024) {
       err = allow_max_smem((const void*)trsm_cols_kernel<T, false>);
       if (err != cudaSuccess) return err;
     }
-    trsm_cols_kernel<T, false><<<(n + nw - 1) / nw, 32 * nw, rest, s>>>(C, S, m, n);
+    trsm_cols_kernel<T, false><<<grid, 32 * nw, rest, s>>>(C, S, m, n);
   }
   return cudaGetLastError();
 }
 
-template cudaError_t cholesky_lower<double>(double*, int, int*, void*, int, cudaStream_t);
-template cudaError_t cholesky_lower<zdbl>(zdbl*, int, int*, void*, int, cudaStream_t);
+template cudaError_t cholesky_lower<double>(double*, int, int*, void*, int, cudaStream_t, int);
+template cudaError_t cholesky_lower<zdbl>(zdbl*, int, int*, void*, int, cudaStream_t, int);
 template cudaError_t trsm_lower_left<double>(const double*, double*, int, int, int*, void*, int,
-                                             cudaStream_t);
+                                             cudaStream_t, int);
 template cudaError_t trsm_lower_left<zdbl>(const zdbl*, zdbl*, int, int, int*, void*, int,
-                                           cudaStream_t);
+                                           cudaStream_t, int);
 
 }  // namespace cbc

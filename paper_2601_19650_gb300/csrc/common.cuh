@@ -79,7 +79,9 @@ __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
 
 // returns false if the barrier timed out (status already set).  Arrival is a release
 // add at GPU scope, waiting an acquire load of the generation word.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status,
+                                          unsigned int nctas = 0) {
+  if (nctas == 0) nctas = gridDim.x;  // else: the CTAs of one group (cluster) of a batch
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -91,7 +93,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status) {
                  : "=r"(arrived)
                  : "l"(&bar->count)
                  : "memory");
-    if (arrived == gridDim.x - 1) {
+    if (arrived == nctas - 1) {
       asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&bar->count) : "memory");
       asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->gen) : "memory");
     } else {
@@ -147,6 +149,16 @@ __device__ __forceinline__ double rsqrt64(double x) {
   r = r * fma(-h * r, r, 1.5);
   r = r * fma(-h * r, r, 1.5);
   return ldexp(r, -ex / 2);
+}
+
+// Row i of entry t of a packed lower triangle (t = i (i + 1) / 2 + c, 0 <= c <= i).  The
+// estimate comes from a single-precision square root (FP64 throughput per SM is two
+// orders of magnitude below FP32 on this part) and is corrected in integer arithmetic.
+__device__ __forceinline__ int tri_row(int64_t t) {
+  int i = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+  while ((int64_t)(i + 1) * (i + 2) / 2 <= t) ++i;
+  while ((int64_t)i * (i + 1) / 2 > t) --i;
+  return i;
 }
 
 // warp / block reductions -----------------------------------------------------------

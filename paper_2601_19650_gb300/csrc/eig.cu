@@ -5,10 +5,11 @@
 // eigenvectors are the singular vectors of M and its eigenvalues the squared singular
 // values, so keeping the k largest eigenpairs keeps the same subspace as the truncated
 // SVD.  Stages:
-//   1. Householder reduction to a real symmetric tridiagonal T = Q^H K Q, one
-//      cooperative launch; rows of K are dealt round-robin to the CTAs so the shrinking
-//      trailing block stays balanced, two bounded grid barriers per column.  FP64 work
-//      is spread over many SMs because one GB300 SM retires only ~2 DFMA per clock.
+//   1. Householder reduction to a real symmetric tridiagonal T = Q^H K Q by one group
+//      of CTAs that wait on each other (a thread-block cluster when the rows fit in its
+//      shared memory, else a cooperative launch); rows of K are dealt round-robin to the
+//      CTAs so the shrinking trailing block stays balanced.  FP64 work is spread over
+//      several SMs because one GB300 SM retires only ~2 DFMA per clock.
 //   2. Estimates of all eigenvalues of T by single-precision Sturm-count multisection,
 //      one warp per eigenvalue (a dependent chain of FP64 divisions per Sturm step is
 //      slow on this part; the estimates only need to separate the eigenvalues).
@@ -30,6 +31,12 @@ namespace cbc {
 namespace {
 
 constexpr int TPB = 256;
+
+// p moved by `bytes` (the per-instance stride of a batched workspace)
+template <typename P>
+__host__ __device__ __forceinline__ P* byte_shift(P* p, size_t bytes) {
+  return reinterpret_cast<P*>(reinterpret_cast<uintptr_t>(p) + bytes);
+}
 
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p);
@@ -200,48 +207,117 @@ __global__ void __launch_bounds__(TPB) tridiag_kernel(TriArgs<T> a) {
 }
 
 // ---- tridiagonalisation with the rows in shared memory -----------------------------
-// Same reduction as tridiag_kernel, for m small enough that every CTA keeps its rows
-// in shared memory.  Column j needs two exchanges: the Householder vector v_j from the
-// CTA that owns row j, and the global sum v^H p.  The first is a flag written with
-// release semantics by the owner (which updates row j first, then publishes v_j and
-// only then updates its other rows); the second is an arrival counter per column.
-// Every wait is bounded.
+// Same reduction as tridiag_kernel, for m small enough that every CTA keeps its rows in
+// shared memory.  Column j needs two exchanges through global memory: the Householder
+// vector v_j (with tau_j) from the CTA that owns row j, and p = tau_j A v_j, one entry
+// from the owner of each row.  Both travel as plain data: the receiving buffers are
+// filled with the all-ones bit pattern before the launch, each entry is written once
+// with a relaxed store, and readers poll every entry until it differs from that
+// pattern, so no fence, counter or atomic sits on the dependency chain.  Every CTA
+// forms v^H p from the gathered p itself, in one fixed order, so all CTAs apply the
+// same rank-2 update.  Every wait is bounded.
 template <typename T>
 struct Tri2Args {
-  T* A;
+  const T* A;
   int m;
   double* d;
   double* e;
   T* tau;
-  T* V;              // (m-1) x m, row j = v_j
-  T* p2;             // 2 x m
-  double* dot;       // m x 2
-  unsigned* cnt;     // m arrival counters
-  unsigned* vflag;   // m publication flags
+  T* V;    // m x m; row j: [j] = tau_j, [j+1, m) = v_j; sentinel-filled before the launch
+  T* Pg;   // m x m; row j: [j+1, m) = tau_j A v_j;     sentinel-filled before the launch
   int* status;
+  int P;            // CTAs per matrix; CTA b handles matrix b / P of a batch
+  int64_t a_bs;     // elements between consecutive matrices A
+  size_t wb;        // bytes between the workspaces (d .. Pg) of consecutive matrices
 };
 
-__device__ __forceinline__ bool wait_geq(const unsigned* p, unsigned target, int* status) {
-  long long t0 = clock64();
-  unsigned cur;
-  while (true) {
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(p) : "memory");
-    if (cur >= target) return true;
-    if (clock64() - t0 > 4000000000LL) {
-      set_status(status, CBC_ERR_TIMEOUT);
-      return false;
-    }
-    if (*((volatile int*)status) == CBC_ERR_TIMEOUT) return false;
-  }
+constexpr long long kSentinel = -1LL;  // all bits set: a NaN that arithmetic never yields
+constexpr long long kWaitCycles = 4000000000LL;
+
+__device__ __forceinline__ double pub_value(double x) {
+  return (__double_as_longlong(x) == kSentinel) ? __longlong_as_double(0x7ff8000000000000LL) : x;
+}
+__device__ __forceinline__ void st_pub(double* p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(pub_value(v)) : "memory");
+}
+__device__ __forceinline__ void st_pub(zdbl* p, zdbl v) {
+  asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(pub_value(v.re)),
+               "d"(pub_value(v.im))
+               : "memory");
+}
+__device__ __forceinline__ bool ld_pub(const double* p, double* v) {
+  double x;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(x) : "l"(p) : "memory");
+  *v = x;
+  return __double_as_longlong(x) != kSentinel;
+}
+__device__ __forceinline__ bool ld_pub(const zdbl* p, zdbl* v) {
+  double x, y;
+  asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];" : "=d"(x), "=d"(y) : "l"(p) : "memory");
+  *v = zdbl{x, y};
+  return __double_as_longlong(x) != kSentinel && __double_as_longlong(y) != kSentinel;
 }
 
+// dst[lo, hi) <- src[lo, hi) as the entries get published.  False (for the whole CTA)
+// when a wait ran out or another CTA has reported an error.
 template <typename T>
-__device__ void householder_row(const Tri2Args<T>& a, const T* row, int j, double* sh) {
+__device__ bool gather_pub(const T* src, T* dst, int lo, int hi, int* status) {
+  bool ok = true;
+  for (int c = lo + threadIdx.x; c < hi && ok; c += blockDim.x) {
+    T v;
+    if (!ld_pub(src + c, &v)) {
+      const long long t0 = clock64();
+      while (!ld_pub(src + c, &v)) {
+        if (*((volatile int*)status) != 0) {
+          ok = false;
+          break;
+        }
+        if (clock64() - t0 > kWaitCycles) {
+          set_status(status, CBC_ERR_TIMEOUT);
+          ok = false;
+          break;
+        }
+      }
+    }
+    dst[c] = v;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
+// (sum x, sum y) over the CTA; sh holds at least 66 doubles
+__device__ __forceinline__ double2 block_sum2(double x, double y, double* sh) {
+  x = warp_sum(x);
+  y = warp_sum(y);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    sh[w] = x;
+    sh[32 + w] = y;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double a = (lane < nw) ? sh[lane] : 0.0, b = (lane < nw) ? sh[32 + lane] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (lane == 0) {
+      sh[64] = a;
+      sh[65] = b;
+    }
+  }
+  __syncthreads();
+  return make_double2(sh[64], sh[65]);
+}
+
+// Householder vector of column j from the owner's updated row j (zlarfg convention:
+// H = I - tau v v^H, H^H x = beta e_1 with beta real); written to vs (shared) and
+// published to V.
+template <typename T>
+__device__ void householder_pub(const Tri2Args<T>& a, const T* row, int j, T* vs, double* sh) {
   using O = ops<T>;
   const int m = a.m;
   double xn2 = 0.0;
   for (int c = j + 2 + threadIdx.x; c < m; c += blockDim.x) xn2 += O::abs2(row[c]);
-  xn2 = block_sum(xn2, sh);
+  xn2 = block_sum2(xn2, 0.0, sh).x;
   const T alpha = O::conj(row[j + 1]);
   const double ar = O::real(alpha), ai = O::imag(alpha);
   T tau, scale;
@@ -260,33 +336,45 @@ __device__ void householder_row(const Tri2Args<T>& a, const T* row, int j, doubl
     const double iden = rcp64(zr * zr + zi * zi);
     scale = O::make(zr * iden, -zi * iden);
   }
-  T* vs = a.V + (int64_t)j * m;
-  for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x)
-    vs[c] = (c == j + 1) ? O::one() : (trivial ? O::zero() : O::conj(row[c]) * scale);
+  T* vg = a.V + (int64_t)j * m;
+  for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) {
+    const T v = (c == j + 1) ? O::one() : (trivial ? O::zero() : O::conj(row[c]) * scale);
+    vs[c] = v;
+    st_pub(vg + c, v);
+  }
   if (threadIdx.x == 0) {
+    vs[j] = tau;
+    st_pub(vg + j, tau);
     a.tau[j] = tau;
     a.e[j] = beta;
     a.d[j] = O::real(row[j]);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
-    asm volatile("st.release.gpu.global.u32 [%0], 1;" ::"l"(a.vflag + j) : "memory");
-  }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a) {
+__global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
   using O = ops<T>;
   extern __shared__ unsigned char sm_raw[];
-  __shared__ double sh[64];
-  __shared__ int s_ok;
-  const int m = a.m, P = gridDim.x, cta = blockIdx.x;
+  __shared__ double sh[72];
+  __shared__ T part[TPB / 32];
+  const int P = a0.P, inst = blockIdx.x / P, cta = blockIdx.x % P;
+  Tri2Args<T> a = a0;
+  {
+    const size_t off = (size_t)inst * a0.wb;
+    a.A = a0.A + (int64_t)inst * a0.a_bs;
+    a.d = byte_shift(a0.d, off);
+    a.e = byte_shift(a0.e, off);
+    a.tau = byte_shift(a0.tau, off);
+    a.V = byte_shift(a0.V, off);
+    a.Pg = byte_shift(a0.Pg, off);
+  }
+  const int m = a.m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nr = (m - cta + P - 1) / P;  // own rows r = cta + P t
   T* rows = reinterpret_cast<T*>(sm_raw);
-  T* vsm = rows + (size_t)nr * m;
-  T* psm = vsm + m;
+  T* vbuf = rows + (size_t)nr * m;  // v of two consecutive columns
+  T* psm = vbuf + 2 * (size_t)m;    // p, then w
   for (int t = 0; t < nr; ++t)
     for (int c = threadIdx.x; c < m; c += blockDim.x)
       rows[(size_t)t * m + c] = a.A[(int64_t)(cta + P * t) * m + c];
@@ -295,72 +383,66 @@ __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a) {
     if (cta == 0 && threadIdx.x == 0) a.d[0] = O::real(rows[0]);
     return;
   }
-  if (cta == 0) householder_row(a, rows, 0, sh);
+  if (cta == 0) householder_pub(a, rows, 0, vbuf, sh);
   for (int j = 0; j < m - 1; ++j) {
-    // v_j from its owner
-    if (threadIdx.x == 0) s_ok = wait_geq(a.vflag + j, 1u, a.status) ? 1 : 0;
-    __syncthreads();
-    if (!s_ok) return;
-    const T* vg = a.V + (int64_t)j * m;
-    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) vsm[c] = ldcg(vg + c);
-    const T tau = ldcg(a.tau + j);
-    __syncthreads();
-    // phase B: p_r = tau sum_{c>j} A[r][c] v_c for own rows r > j
-    int t0 = (j + 1 - cta + P - 1) / P;
-    if (t0 < 0) t0 = 0;
-    double dre = 0.0, dim = 0.0;
-    T* pg = a.p2 + (j & 1) * m;
-    for (int t = t0 + warp; t < nr; t += nw) {
-      const int r = cta + P * t;
-      const T* row = rows + (size_t)t * m;
-      T acc = O::zero();
-      for (int c = j + 1 + lane; c < m; c += 32) acc = O::fma(row[c], vsm[c], acc);
-      if constexpr (O::cplx) {
-        acc = zdbl{warp_sum(O::real(acc)), warp_sum(O::imag(acc))};
-      } else {
+    T* vsm = vbuf + (size_t)(j & 1) * m;
+    // v_j and tau_j (the owner of row j computed them into vsm itself)
+    if (j % P != cta && !gather_pub(a.V + (int64_t)j * m, vsm, j, m, a.status)) return;
+    const T tau = vsm[j];
+    // phase B: p_r = tau sum_{c>j} A[r][c] v_c for own rows r > j, S warps per row
+    const int t0 = (j + 1 - cta + P - 1) / P;  // first own row beyond j
+    const int live = nr - t0;
+    T* pg = a.Pg + (int64_t)j * m;
+    if (live > 0) {
+      int S = 1;
+      while (S * 2 * live <= nw) S *= 2;
+      for (int item = warp; item < live * S; item += nw) {
+        const int t = t0 + item / S, sg = item % S;
+        const T* row = rows + (size_t)t * m;
+        T acc = O::zero();
+        for (int c = j + 1 + sg * 32 + lane; c < m; c += S * 32) acc = O::fma(row[c], vsm[c], acc);
         acc = warp_sum(acc);
+        if (S == 1) {
+          if (lane == 0) st_pub(pg + cta + P * t, tau * acc);
+        } else if (lane == 0) {
+          part[item] = acc;
+        }
       }
-      const T pr = tau * acc;
-      if (lane == 0) {
-        pg[r] = pr;
-        const T vd = O::conj(vsm[r]) * pr;
-        dre += O::real(vd);
-        dim += O::imag(vd);
+      if (S > 1) {
+        __syncthreads();
+        if (threadIdx.x < live) {
+          T s = part[threadIdx.x * S];
+          for (int q = 1; q < S; ++q) s = s + part[threadIdx.x * S + q];
+          st_pub(pg + cta + P * (t0 + threadIdx.x), tau * s);
+        }
       }
     }
-    dre = block_sum(dre, sh);
-    if constexpr (O::cplx) dim = block_sum(dim, sh);
-    if (threadIdx.x == 0) {
-      atomicAdd(a.dot + 2 * j, dre);
-      if constexpr (O::cplx) atomicAdd(a.dot + 2 * j + 1, dim);
-      asm volatile("fence.acq_rel.gpu;" ::: "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.cnt + j) : "memory");
-      s_ok = wait_geq(a.cnt + j, (unsigned)P, a.status) ? 1 : 0;
+    // all of p, then w = p - (conj(tau)/2)(v^H p) v in place
+    if (!gather_pub(pg, psm, j + 1, m, a.status)) return;
+    double dre = 0.0, dim = 0.0;
+    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) {
+      const T vd = O::conj(vsm[c]) * psm[c];
+      dre += O::real(vd);
+      dim += O::imag(vd);
     }
+    const double2 dd = block_sum2(dre, dim, sh);
+    const T coef = O::scale(-0.5, O::conj(tau) * O::make(dd.x, dd.y));
+    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) psm[c] = O::fma(coef, vsm[c], psm[c]);
     __syncthreads();
-    if (!s_ok) return;
-    // phase C: own rows -= v w^H + w v^H with w = p - (conj(tau)/2)(v^H p) v
-    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) psm[c] = ldcg(pg + c);
-    const T sv = O::make(__ldcg(a.dot + 2 * j), __ldcg(a.dot + 2 * j + 1));
-    const T coef = O::scale(-0.5, O::conj(tau) * sv);
-    __syncthreads();
+    // phase C: own rows r > j: A[r][c] -= v_r conj(w_c) + w_r conj(v_c), c > j
     auto update_row = [&](int t, int c0, int cstep) {
       const int r = cta + P * t;
       T* row = rows + (size_t)t * m;
-      const T vr = vsm[r];
-      const T wr = O::fma(coef, vr, psm[r]);
-      for (int c = j + 1 + c0; c < m; c += cstep) {
-        const T vc = vsm[c];
-        const T wc = O::fma(coef, vc, psm[c]);
-        row[c] = row[c] - O::fma(vr, O::conj(wc), wr * O::conj(vc));
-      }
+      const T vr = vsm[r], wr = psm[r];
+      for (int c = j + 1 + c0; c < m; c += cstep)
+        row[c] = row[c] - O::fma(vr, O::conj(psm[c]), wr * O::conj(vsm[c]));
     };
     int tstart = t0;
     if (j + 1 < m - 1 && (j + 1) % P == cta) {
       // the next column's owner: update that row with the whole CTA, publish v_{j+1}
       update_row(t0, threadIdx.x, blockDim.x);
       __syncthreads();
-      householder_row(a, rows + (size_t)t0 * m, j + 1, sh);
+      householder_pub(a, rows + (size_t)t0 * m, j + 1, vbuf + (size_t)((j + 1) & 1) * m, sh);
       tstart = t0 + 1;
     }
     for (int t = tstart + warp; t < nr; t += nw) update_row(t, lane, 32);
@@ -388,8 +470,12 @@ __device__ __forceinline__ int sturm32(const float* dd, const float* e2, int m, 
   return cnt;
 }
 
-__global__ void bisect32_kernel(const double* d, const double* e, int m, float* lam32) {
+__global__ void bisect32_kernel(const double* d, const double* e, int m, float* lam32,
+                                size_t wb) {
   extern __shared__ float shf[];
+  d = byte_shift(d, blockIdx.y * wb);  // matrix blockIdx.y of a batch
+  e = byte_shift(e, blockIdx.y * wb);
+  lam32 = byte_shift(lam32, blockIdx.y * wb);
   float* dd = shf;
   float* e2 = shf + m;
   __shared__ float s_lo, s_hi, s_piv;
@@ -457,10 +543,19 @@ struct InvArgs {
   int kmax;            // candidates j < kmax
   double* X;           // m x kmax (row i, column j)
   double* rq;          // [kmax] Rayleigh quotients
+  size_t wb;           // workspace bytes between the matrices of a batch (blockIdx.y)
 };
 
 __global__ void invit_kernel(InvArgs a) {
   extern __shared__ double shd[];
+  {
+    const size_t off = blockIdx.y * a.wb;
+    a.d = byte_shift(a.d, off);
+    a.e = byte_shift(a.e, off);
+    a.lam32 = byte_shift(a.lam32, off);
+    a.X = byte_shift(a.X, off);
+    a.rq = byte_shift(a.rq, off);
+  }
   const int tpb = blockDim.x, tid = threadIdx.x;
   const int m = a.m, K = a.kmax;
   double* dl = shd;
@@ -578,8 +673,14 @@ __global__ void invit_kernel(InvArgs a) {
 // exact trace of T minus the kept eigenvalues.  Writes k and the full eigenvalue list.
 __global__ void rank_kernel(const double* d, const double* rq, const float* lam32, int m,
                             int kmax, long long max_bond, double tol, double floor_rel,
-                            int* k_dev, double* lam) {
+                            int* k_dev, double* lam, size_t wb) {
   __shared__ double s_tr;
+  // matrix blockIdx.x of a batch
+  d = byte_shift(d, blockIdx.x * wb);
+  rq = byte_shift(rq, blockIdx.x * wb);
+  lam32 = byte_shift(lam32, blockIdx.x * wb);
+  k_dev += blockIdx.x;
+  lam += (size_t)blockIdx.x * m;
   if (threadIdx.x == 0) {
     double tr = 0.0;
     for (int i = 0; i < m; ++i) tr += d[i];
@@ -619,11 +720,17 @@ __global__ void rank_kernel(const double* d, const double* rq, const float* lam3
 template <typename T>
 __global__ void __launch_bounds__(128) backtransform_kernel(const T* V, const T* tau,
                                                             const double* X, int m, int kmax,
-                                                            const int* k_dev, T* U) {
+                                                            const int* k_dev, T* U, size_t wb) {
   using O = ops<T>;
   extern __shared__ unsigned char smem_raw[];
   T* u = reinterpret_cast<T*>(smem_raw);
   __shared__ T part[2][4];
+  // matrix blockIdx.y of a batch
+  V = byte_shift(V, blockIdx.y * wb);
+  tau = byte_shift(tau, blockIdx.y * wb);
+  X = byte_shift(X, blockIdx.y * wb);
+  k_dev += blockIdx.y;
+  U += (size_t)blockIdx.y * m * kmax;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int jj = blockIdx.x;
   const int k = *k_dev;
@@ -674,15 +781,14 @@ size_t eig_workspace_bytes(int m, int kmax, bool cplx) {
   b += align256(sizeof(double) * 4);                 // dot
   b += align256(sizeof(GridBarrier));                // barrier
   b += align256(sizeof(double) * (size_t)m * kmax);  // X
-  b += align256(sizeof(double) * 2 * m);             // per-column dot accumulators
-  b += align256(sizeof(unsigned) * 2 * m);           // counters and flags
+  b += align256(ts * (size_t)m * m);                 // p of every column (exchange)
   return b;
 }
 
 template <typename T>
 cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double floor_rel,
                      double* lam, T* U, int* k_dev, void* work, int* status, int num_sms,
-                     cudaStream_t s) {
+                     cudaStream_t s, int nb, bool prefer_cluster) {
   char* w = static_cast<char*>(work);
   auto take = [&](size_t bytes) {
     char* p = w;
@@ -690,6 +796,7 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
     return p;
   };
   const size_t ts = sizeof(T);
+  const size_t wb = eig_workspace_bytes(m, kmax, ops<T>::cplx);  // per matrix
   double* d = (double*)take(sizeof(double) * m);
   double* e = (double*)take(sizeof(double) * m);
   float* lam32 = (float*)take(sizeof(float) * m);
@@ -701,44 +808,74 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   double* dot = (double*)take(sizeof(double) * 4);
   GridBarrier* bar = (GridBarrier*)take(sizeof(GridBarrier));
   double* X = (double*)take(sizeof(double) * (size_t)m * kmax);
-  double* dotc = (double*)take(sizeof(double) * 2 * m);
-  unsigned* flags = (unsigned*)take(sizeof(unsigned) * 2 * m);
+  T* Pg = (T*)take(ts * (size_t)m * m);
 
-  cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
-  if (err != cudaSuccess) return err;
-  err = cudaMemsetAsync(tau, 0, ts * m, s);
-  if (err != cudaSuccess) return err;
-  if (m == 1) err = cudaMemsetAsync(e, 0, sizeof(double), s);
+  cudaError_t err = cudaSuccess;
+  for (int b = 0; b < nb && err == cudaSuccess; ++b) {
+    const size_t off = (size_t)b * wb;
+    err = cudaMemsetAsync(byte_shift(bar, off), 0, sizeof(GridBarrier), s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(byte_shift(tau, off), 0, ts * m, s);
+    if (err == cudaSuccess && m == 1) err = cudaMemsetAsync(byte_shift(e, off), 0, sizeof(double), s);
+  }
   if (err != cudaSuccess) return err;
   note_launches(CBC_K_EIG, 5);
-  // 1. tridiagonalisation (cooperative); CBC_TRIDIAG_CTAS overrides the CTA count
-  int P = std::max(1, std::min(num_sms, m / 2));
-  if (const char* env = getenv("CBC_TRIDIAG_CTAS")) {
-    int v = atoi(env);
-    if (v > 0) P = std::max(1, std::min(num_sms, v));
-  }
-  const int nr = (m + P - 1) / P;
-  const size_t shm_tri = ((size_t)nr + 2) * m * ts;
-  if (shm_tri <= 160 * 1024) {
-    err = cudaMemsetAsync(dotc, 0, sizeof(double) * 2 * m, s);
-    if (err == cudaSuccess) err = cudaMemsetAsync(flags, 0, sizeof(unsigned) * 2 * m, s);
-    if (err == cudaSuccess)
-      err = allow_max_smem((const void*)tridiag_smem_kernel<T>);
+  // 1. tridiagonalisation.  Rows in shared memory when they fit: one thread-block
+  // cluster of up to 16 CTAs per matrix for a batch or when `prefer_cluster`
+  // (co-scheduled and, unlike cooperative launches, concurrent with other streams'
+  // work), else a cooperative launch over ~m/4 CTAs per matrix (the fastest single
+  // reduction); rows in global memory beyond that.  CBC_TRIDIAG_CTAS overrides the CTA
+  // count (1..16 selects a cluster).
+  int Pw = 0;
+  if (const char* env = getenv("CBC_TRIDIAG_CTAS")) Pw = std::max(0, std::min(num_sms, atoi(env)));
+  auto shm_for = [&](int P) { return ((size_t)((m + P - 1) / P) + 3) * m * ts; };
+  const size_t shm_cap = 160 * 1024;
+  int P = Pw > 0 ? Pw : std::max(1, std::min(16, m / 2));
+  bool cluster = false;
+  if ((Pw > 0 || prefer_cluster || nb > 1) && P <= 16 && shm_for(P) <= shm_cap) {
+    err = allow_max_smem((const void*)tridiag_smem_kernel<T>);
     if (err != cudaSuccess) return err;
-    Tri2Args<T> ta{A, m, d, e, tau, V, p, dotc, flags, flags + m, status};
+    cluster = cluster_ctas((const void*)tridiag_smem_kernel<T>, P, TPB, shm_for(P)) == P;
+  }
+  if (!cluster && Pw <= 0) P = std::max(1, std::min(num_sms, m / 4));
+  const bool in_smem = cluster || shm_for(P) <= shm_cap;
+  if (in_smem) {
+    // the exchange buffers start as all-ones bit patterns (the "not yet written" mark)
+    for (int b = 0; b < nb && err == cudaSuccess; ++b) {
+      err = cudaMemsetAsync(byte_shift(V, b * wb), 0xff, ts * (size_t)m * m, s);
+      if (err == cudaSuccess) err = cudaMemsetAsync(byte_shift(Pg, b * wb), 0xff, ts * (size_t)m * m, s);
+    }
+    if (err == cudaSuccess) err = allow_max_smem((const void*)tridiag_smem_kernel<T>);
+    if (err != cudaSuccess) return err;
+  }
+  if (cluster) {
+    Tri2Args<T> ta{A, m, d, e, tau, V, Pg, status, P, (int64_t)m * m, wb};
     void* args[] = {&ta};
-    err = cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel<T>, dim3(P), dim3(TPB),
-                                      args, shm_tri, s);
+    err = launch_cluster((const void*)tridiag_smem_kernel<T>, P, nb * P, TPB, shm_for(P), args, s);
   } else {
-    TriArgs<T> ta{A, m, d, e, tau, V, vbuf, p, dot, bar, status};
-    void* args[] = {&ta};
-    err = cudaLaunchCooperativeKernel((const void*)tridiag_kernel<T>, dim3(P), dim3(TPB), args, 0,
-                                      s);
+    for (int b = 0; b < nb && err == cudaSuccess; ++b) {
+      const size_t off = (size_t)b * wb;
+      T* Ab = A + (int64_t)b * m * m;
+      if (in_smem) {
+        Tri2Args<T> ta{Ab, m, byte_shift(d, off), byte_shift(e, off), byte_shift(tau, off),
+                       byte_shift(V, off), byte_shift(Pg, off), status, P, 0, 0};
+        void* args[] = {&ta};
+        err = cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel<T>, dim3(P), dim3(TPB),
+                                          args, shm_for(P), s);
+      } else {
+        TriArgs<T> ta{Ab, m, byte_shift(d, off), byte_shift(e, off), byte_shift(tau, off),
+                      byte_shift(V, off), byte_shift(vbuf, off), byte_shift(p, off),
+                      byte_shift(dot, off), byte_shift(bar, off), status};
+        void* args[] = {&ta};
+        err = cudaLaunchCooperativeKernel((const void*)tridiag_kernel<T>, dim3(P), dim3(TPB), args,
+                                          0, s);
+      }
+    }
   }
   if (err != cudaSuccess) return err;
   // 2. eigenvalue estimates
   const int wpb = 8;
-  bisect32_kernel<<<(m + wpb - 1) / wpb, 32 * wpb, 2 * sizeof(float) * m, s>>>(d, e, m, lam32);
+  bisect32_kernel<<<dim3((m + wpb - 1) / wpb, nb), 32 * wpb, 2 * sizeof(float) * m, s>>>(
+      d, e, m, lam32, wb);
   // 3. eigenvectors of T for the candidates, FP64
   // one candidate per CTA: the LU and the solves are long dependent FP64 chains, best
   // run with a whole SM (and its FP64 unit) per chain
@@ -746,24 +883,24 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   size_t shi = (size_t)tpb * m * 41 + 64;
   err = allow_max_smem((const void*)invit_kernel);
   if (err != cudaSuccess) return err;
-  InvArgs ia{d, e, lam32, m, kmax, X, rq};
-  invit_kernel<<<(kmax + tpb - 1) / tpb, tpb, shi, s>>>(ia);
+  InvArgs ia{d, e, lam32, m, kmax, X, rq, wb};
+  invit_kernel<<<dim3((kmax + tpb - 1) / tpb, nb), tpb, shi, s>>>(ia);
   // 4. rank rule on the refined eigenvalues
-  rank_kernel<<<1, 256, 0, s>>>(d, rq, lam32, m, kmax, (long long)max_bond, tol, floor_rel, k_dev,
-                                lam);
+  rank_kernel<<<nb, 256, 0, s>>>(d, rq, lam32, m, kmax, (long long)max_bond, tol, floor_rel,
+                                 k_dev, lam, wb);
   // 5. back transformation
   size_t shm = (size_t)m * ts;
   if (shm > 48 * 1024) {
     err = allow_max_smem((const void*)backtransform_kernel<T>);
     if (err != cudaSuccess) return err;
   }
-  backtransform_kernel<T><<<kmax, 128, shm, s>>>(V, tau, X, m, kmax, k_dev, U);
+  backtransform_kernel<T><<<dim3(kmax, nb), 128, shm, s>>>(V, tau, X, m, kmax, k_dev, U, wb);
   return cudaGetLastError();
 }
 
 template cudaError_t heev_top<double>(double*, int, int, int64_t, double, double, double*,
-                                      double*, int*, void*, int*, int, cudaStream_t);
+                                      double*, int*, void*, int*, int, cudaStream_t, int, bool);
 template cudaError_t heev_top<zdbl>(zdbl*, int, int, int64_t, double, double, double*, zdbl*,
-                                    int*, void*, int*, int, cudaStream_t);
+                                    int*, void*, int*, int, cudaStream_t, int, bool);
 
 }  // namespace cbc

@@ -163,8 +163,11 @@ struct TcArgs {
   int cplx;
   int atomic;
   char* C;               // FP64 output (double or zdbl) through the view
-  View vc;
+  View vc;               // vc.bs: elements between the outputs of consecutive problems
   int* status;
+  int splits;            // K splits per problem; blockIdx.z = problem * splits + split
+  int Mp, N2p;           // packed rows of one problem in the A and B planes
+  int ebsB;              // entries of expB per problem
 };
 
 template <int S, int BN>
@@ -189,7 +192,8 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM;
   const int n0 = blockIdx.y * BN;
-  const int a_begin = blockIdx.z * a.atoms_per_split;
+  const int prob = blockIdx.z / a.splits;
+  const int a_begin = (blockIdx.z % a.splits) * a.atoms_per_split;
   const int a_end = min(a.atoms_total, a_begin + a.atoms_per_split);
   const int n_atoms = max(0, a_end - a_begin);
   const int n_chunks = (n_atoms + a.atoms_per_chunk - 1) / a.atoms_per_chunk;
@@ -231,8 +235,8 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
         const int k = (a_begin + j) * KA;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          tma_load_3d(&tmA, full + stage, sA + s * A_BYTES, k, m0, s);
-          tma_load_3d(&tmB, full + stage, sB + s * B_BYTES, k, n0, s);
+          tma_load_3d(&tmA, full + stage, sA + s * A_BYTES, k, prob * a.Mp + m0, s);
+          tma_load_3d(&tmB, full + stage, sB + s * B_BYTES, k, prob * a.N2p + n0, s);
         }
       }
     }
@@ -310,7 +314,9 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
       if (lane == 0) mbar_arrive(tempty + buf);
     }
     if (ok && n_chunks > 0 && row < a.M) {
-      const int ea = a.expA[row];
+      const int ea = a.expA[prob * a.Mp + row];
+      const int* expB = a.expB + (int64_t)prob * a.ebsB;
+      char* Cp = a.C + (int64_t)prob * a.vc.bs * (a.cplx ? 16 : 8);
       const int bias = -14 - 8 * (S - 1);
       const int64_t ro = a.vc.roff(row);
 #pragma unroll
@@ -318,12 +324,12 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
         const int col = n0 + cg * 32 + i;
         if (col < a.N2) {
           const int ncol = a.cplx ? (col >> 1) : col;
-          const double v = ldexp((double)acc[i], ea + a.expB[ncol] + bias);
+          const double v = ldexp((double)acc[i], ea + expB[ncol] + bias);
           double* dst;
           if (a.cplx)
-            dst = reinterpret_cast<double*>(a.C + 16 * (ro + a.vc.coff(ncol))) + (col & 1);
+            dst = reinterpret_cast<double*>(Cp + 16 * (ro + a.vc.coff(ncol))) + (col & 1);
           else
-            dst = reinterpret_cast<double*>(a.C + 8 * (ro + a.vc.coff(ncol)));
+            dst = reinterpret_cast<double*>(Cp + 8 * (ro + a.vc.coff(ncol)));
           if (a.atomic)
             atomicAdd(dst, v);
           else
@@ -367,9 +373,11 @@ __device__ __forceinline__ int expo_bits(double x) {
 // index, reduced in shared memory, combined across CTAs with an integer atomicMax
 template <typename T, bool SIDE_B>
 __global__ void __launch_bounds__(256) expo_kernel(const T* src, View v, int R, int K,
-                                                   int rowlanes, int* expo, int* status) {
+                                                   int rowlanes, int* expo, int ebs, int* status) {
   using O = ops<T>;
   __shared__ int red[32][9];
+  src += (int64_t)blockIdx.z * v.bs;  // problem blockIdx.z of a batch
+  expo += (int64_t)blockIdx.z * ebs;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 256;
   int best[4] = {-2000, -2000, -2000, -2000};
@@ -431,9 +439,14 @@ __device__ __forceinline__ uint32_t bf16x2_bits(double lo, double hi) {
 template <typename T, bool SIDE_B, bool ROWLANES>
 __global__ void __launch_bounds__(256) slice_kernel(const T* src, View v, int conj, int R, int K,
                                                     int K2p, size_t plane, int S,
-                                                    __nv_bfloat16* out, const int* expo) {
+                                                    __nv_bfloat16* out, const int* expo, int ebs,
+                                                    int rows_pad) {
   using O = ops<T>;
   constexpr bool CPLX = O::cplx;
+  // problem blockIdx.z of a batch: its source, exponents and packed rows
+  src += (int64_t)blockIdx.z * v.bs;
+  expo += (int64_t)blockIdx.z * ebs;
+  out += (size_t)blockIdx.z * rows_pad * K2p;
   __shared__ T tile[32][33];
   __shared__ int se[32];
   const int tid = threadIdx.x, lane = tid & 31;
@@ -496,25 +509,26 @@ bool rows_contiguous(const View& v) {
   return sr == 1 && sk != 1;
 }
 
+// nb problems (sources v.bs elements apart) go to consecutive row blocks of the planes
 template <typename T, bool SIDE_B>
 void pack_operand(const T* src, const View& v, bool conj, int R, int K, int rows_pad, int K2p,
-                  int S, __nv_bfloat16* out, int* expo, int* status, cudaStream_t s) {
+                  int S, __nv_bfloat16* out, int* expo, int* status, cudaStream_t s, int nb) {
   constexpr bool CPLX = ops<T>::cplx;
   const int nrows = (CPLX && SIDE_B) ? rows_pad / 2 : rows_pad;  // logical rows (padded)
   const int klog = CPLX ? K2p / 2 : K2p;                           // logical K (padded)
   const bool rl = rows_contiguous<SIDE_B>(v);
   note_launches(CBC_K_AUX, 2);
-  cudaMemsetAsync(expo, 0xC0, sizeof(int) * nrows, s);  // a large negative floor
-  expo_kernel<T, SIDE_B><<<dim3((K + 255) / 256, (nrows + 31) / 32), 256, 0, s>>>(
-      src, v, R, K, rl ? 1 : 0, expo, status);
-  dim3 grid(klog / 32, nrows / 32);
-  const size_t plane = (size_t)rows_pad * K2p;
+  cudaMemsetAsync(expo, 0xC0, sizeof(int) * nrows * nb, s);  // a large negative floor
+  expo_kernel<T, SIDE_B><<<dim3((K + 255) / 256, (nrows + 31) / 32, nb), 256, 0, s>>>(
+      src, v, R, K, rl ? 1 : 0, expo, nrows, status);
+  dim3 grid(klog / 32, nrows / 32, nb);
+  const size_t plane = (size_t)nb * rows_pad * K2p;
   if (rl)
     slice_kernel<T, SIDE_B, true><<<grid, 256, 0, s>>>(src, v, conj ? 1 : 0, R, K, K2p, plane, S,
-                                                       out, expo);
+                                                       out, expo, nrows, rows_pad);
   else
     slice_kernel<T, SIDE_B, false><<<grid, 256, 0, s>>>(src, v, conj ? 1 : 0, R, K, K2p, plane, S,
-                                                        out, expo);
+                                                        out, expo, nrows, rows_pad);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -589,12 +603,13 @@ int g_sms = 0;
 
 }  // namespace tc
 
-size_t gemm_tc_workspace_bytes(int M, int N, int K, bool cplx, int S) {
+size_t gemm_tc_workspace_bytes(int M, int N, int K, bool cplx, int S, int nb) {
   using namespace tc;
   if (M < BM && N > M) std::swap(M, N);
   Geo g = geometry(M, N, K, cplx, S);
-  return a256((size_t)S * g.Mp * g.K2p * 2) + a256((size_t)S * g.N2p * g.K2p * 2) +
-         a256(sizeof(int) * g.Mp) + a256(sizeof(int) * g.N2p) + 1024;
+  const size_t b = (size_t)std::max(nb, 1);
+  return a256(b * S * g.Mp * g.K2p * 2) + a256(b * S * g.N2p * g.K2p * 2) +
+         a256(b * sizeof(int) * g.Mp) + a256(b * sizeof(int) * g.N2p) + 1024;
 }
 
 static View transpose_view(const View& v) {
@@ -612,14 +627,14 @@ static View transpose_view(const View& v) {
 template <typename T>
 cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA, const T* B,
                     const View& vb, bool conjB, T* C, const View& vc, int S, void* ws,
-                    int* status, cudaStream_t s) {
+                    int* status, cudaStream_t s, int nb) {
   using namespace tc;
-  if (M <= 0 || N <= 0) return cudaSuccess;
+  if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
   if (S < 2 || S > 5) return cudaErrorInvalidValue;
   // keep the long dimension on the 128-row side: C^T = B^T A^T
   if (M < BM && N > M) {
     return gemm_tc<T>(N, M, K, B, transpose_view(vb), conjB, A, transpose_view(va), conjA, C,
-                      transpose_view(vc), S, ws, status, s);
+                      transpose_view(vc), S, ws, status, s, nb);
   }
   constexpr bool CPLX = ops<T>::cplx;
   if (g_sms == 0) {
@@ -630,23 +645,24 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
   Geo g = geometry(M, N, K, CPLX, S);
   char* w = static_cast<char*>(ws);
   w = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(w) + 255) & ~uintptr_t(255));
+  const size_t b = (size_t)nb;
   __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(w);
-  w += a256((size_t)S * g.Mp * g.K2p * 2);
+  w += a256(b * S * g.Mp * g.K2p * 2);
   __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(w);
-  w += a256((size_t)S * g.N2p * g.K2p * 2);
+  w += a256(b * S * g.N2p * g.K2p * 2);
   int* ea = reinterpret_cast<int*>(w);
-  w += a256(sizeof(int) * g.Mp);
+  w += a256(b * sizeof(int) * g.Mp);
   int* eb = reinterpret_cast<int*>(w);
   if (K <= 0) return cudaErrorInvalidValue;
-  // slices of A (rows) and of B (columns, embedded)
-  pack_operand<T, false>(A, va, conjA, M, K, g.Mp, g.K2p, S, sa, ea, status, s);
-  pack_operand<T, true>(B, vb, conjB, N, K, g.N2p, g.K2p, S, sb, eb, status, s);
+  // slices of A (rows) and of B (columns, embedded); problem p owns row block p
+  pack_operand<T, false>(A, va, conjA, M, K, g.Mp, g.K2p, S, sa, ea, status, s, nb);
+  pack_operand<T, true>(B, vb, conjB, N, K, g.N2p, g.K2p, S, sb, eb, status, s, nb);
   CUtensorMap ma, mb;
-  if (!make_map(&ma, sa, g.K2p, g.Mp, S, BM) || !make_map(&mb, sb, g.K2p, g.N2p, S, g.BN))
+  if (!make_map(&ma, sa, g.K2p, nb * g.Mp, S, BM) || !make_map(&mb, sb, g.K2p, nb * g.N2p, S, g.BN))
     return cudaErrorInvalidValue;
   const int atoms = g.K2p / KA;
   const int apc = atoms_per_chunk_for(S);
-  const int tiles = (g.Mp / BM) * (g.N2p / g.BN);
+  const int tiles = (g.Mp / BM) * (g.N2p / g.BN) * nb;
   const int chunks = (atoms + apc - 1) / apc;
   int splits = 1;
   if (tiles < g_sms && chunks > 1) splits = std::min(chunks, std::max(1, g_sms / tiles));
@@ -665,12 +681,16 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
   args.C = reinterpret_cast<char*>(C);
   args.vc = vc;
   args.status = status;
+  args.splits = splits;
+  args.Mp = g.Mp;
+  args.N2p = g.N2p;
+  args.ebsB = CPLX ? g.N2p / 2 : g.N2p;
   if (splits > 1) {
     // the split partial sums are added into a zeroed C
-    cudaError_t e = gemm_f64<T>(M, N, 0, 1, A, va, false, B, vb, false, C, vc, s);
+    cudaError_t e = gemm_f64<T>(M, N, 0, nb, A, va, false, B, vb, false, C, vc, s);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(g.Mp / BM, g.N2p / g.BN, splits);
+  dim3 grid(g.Mp / BM, g.N2p / g.BN, splits * nb);
   note_launches(CBC_K_GEMM_TC, 1);
   switch (S) {
     case 2: return launch<2>(ma, mb, args, grid, s);
@@ -682,9 +702,9 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
 
 template cudaError_t gemm_tc<double>(int, int, int, const double*, const View&, bool,
                                      const double*, const View&, bool, double*, const View&, int,
-                                     void*, int*, cudaStream_t);
+                                     void*, int*, cudaStream_t, int);
 template cudaError_t gemm_tc<zdbl>(int, int, int, const zdbl*, const View&, bool, const zdbl*,
                                    const View&, bool, zdbl*, const View&, int, void*, int*,
-                                   cudaStream_t);
+                                   cudaStream_t, int);
 
 }  // namespace cbc

@@ -63,12 +63,13 @@ cudaError_t gemm_f64(int M, int N, int K, int batch, const T* A, const View& va,
                      cudaStream_t s);
 
 // The same product on the tensor cores with S bf16 slices per operand (gemm_tc.cu);
-// `ws` must hold gemm_tc_workspace_bytes(M, N, K, cplx, S) bytes.  batch = 1.
-size_t gemm_tc_workspace_bytes(int M, int N, int K, bool cplx, int S);
+// `ws` must hold gemm_tc_workspace_bytes(M, N, K, cplx, S, nb) bytes.  nb problems of
+// one shape, their operands va.bs / vb.bs / vc.bs elements apart, in one launch.
+size_t gemm_tc_workspace_bytes(int M, int N, int K, bool cplx, int S, int nb = 1);
 template <typename T>
 cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA, const T* B,
                     const View& vb, bool conjB, T* C, const View& vc, int S, void* ws,
-                    int* status, cudaStream_t s);
+                    int* status, cudaStream_t s, int nb = 1);
 
 // ---- Hermitian eigensolver (FP64): A (m x m, row-major, overwritten) -----------------
 // Finds the eigenvalues in descending order and the eigenvectors of the `k` largest,
@@ -81,31 +82,41 @@ size_t eig_workspace_bytes(int m, int kmax, bool cplx);
 template <typename T>
 cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double floor_rel,
                      double* lam, T* U, int* k_dev, void* work, int* status, int num_sms,
-                     cudaStream_t s);
+                     cudaStream_t s, int nb = 1, bool prefer_cluster = false);
 
 // ---- Cholesky QR (FP64) ------------------------------------------------------------
 // Q = C^{-1} S with G = S S^H = C C^H, S: m x n (m <= n), row-major, in place on S.
+// nb problems: G, C m*m and S m*n elements apart; `bar` holds nb GridBarriers.
 template <typename T>
-cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cudaStream_t s);
+cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cudaStream_t s,
+                           int nb = 1);
 template <typename T>
 cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* bar,
-                            int num_sms, cudaStream_t s);
+                            int num_sms, cudaStream_t s, int nb = 1);
 
 // ---- small helpers ------------------------------------------------------------------
 // Let `func` use up to the device's opt-in shared memory per block.  Every caller sets
 // the same value, so concurrent calls from several host threads cannot shrink the
 // limit under another thread's launch.
 cudaError_t allow_max_smem(const void* func);
+// Largest feasible single-cluster size <= want (<= 16) for func; 0 if none.
+int cluster_ctas(const void* func, int want, int threads, size_t smem);
+// Launch func over `grid` CTAs in clusters of `cluster` CTAs (each cluster co-scheduled;
+// clusters are concurrent with other streams' work).
+cudaError_t launch_cluster(const void* func, int cluster, int grid, int threads, size_t smem,
+                           void** args, cudaStream_t s);
 
 // x[i] (i < n) scaled in place to unit Frobenius norm; log of the old norm added to
-// *log_acc; non-finite norm sets CBC_ERR_NUMERICAL.
+// *log_acc; non-finite norm sets CBC_ERR_NUMERICAL.  nb problems: x n elements apart,
+// log_acc and scratch one double apart.
 template <typename T>
 cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, double* scratch,
-                              cudaStream_t s);
-// L[r, c] = sqrt(lam[r]) * conj(V[c, r]) for r < k (V: n x ldv row-major), L: k x n
+                              cudaStream_t s, int nb = 1);
+// L[r, c] = sqrt(lam[r]) * conj(V[c, r]) for r < k (V: n x ldv row-major), L: k x n;
+// nb problems: V n*ldv, lam n, k_dev 1 and L l_bs elements apart
 template <typename T>
 cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_dev, int n,
-                           T* L, cudaStream_t s);
+                           T* L, cudaStream_t s, int nb = 1, int64_t l_bs = 0);
 // out = in with its axes permuted: out dims are in dims[perm[0]], in dims[perm[1]], ...
 // (row-major, rank <= 8)
 template <typename T>
@@ -113,7 +124,7 @@ cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const
                     cudaStream_t s);
 // dst (n_elem) = identity rows r < n of an n x n matrix
 template <typename T>
-cudaError_t fill_identity(T* dst, int n, cudaStream_t s);
+cudaError_t fill_identity(T* dst, int n, cudaStream_t s, int nb = 1);
 // widen an input tensor to FP64 storage
 cudaError_t widen_to_f64(const void* src, int src_dtype, void* dst, int64_t n_elem,
                          cudaStream_t s);

@@ -2,6 +2,8 @@
 // per-step renormalisation with a running log scale, the m > n truncation factor
 // diag(sqrt(lambda)) V^H, and identity fill for the trivial LQ case.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "kernels.cuh"
 #include "planner.h"
@@ -9,8 +11,11 @@
 namespace cbc {
 namespace {
 
+// batched kernels: problem blockIdx.y, its data n (or k x n) elements apart
 template <typename T>
 __global__ void sumsq_kernel(const T* x, int64_t n, double* out) {
+  x += (int64_t)blockIdx.y * n;
+  out += blockIdx.y;
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -29,6 +34,9 @@ __global__ void sumsq_kernel(const T* x, int64_t n, double* out) {
 
 template <typename T>
 __global__ void scale_kernel(T* x, int64_t n, const double* sumsq, double* log_acc, int* status) {
+  x += (int64_t)blockIdx.y * n;
+  sumsq += blockIdx.y;
+  log_acc += blockIdx.y;
   double ss = *sumsq;
   bool ok = isfinite(ss) && ss > 0.0;
   if (!ok) {
@@ -44,7 +52,11 @@ __global__ void scale_kernel(T* x, int64_t n, const double* sumsq, double* log_a
 
 template <typename T>
 __global__ void scaled_adjoint_kernel(const T* V, int ldv, const double* lam, const int* k_dev,
-                                      int n, T* L) {
+                                      int n, T* L, int64_t l_bs) {
+  V += (int64_t)blockIdx.y * n * ldv;
+  lam += (int64_t)blockIdx.y * n;
+  k_dev += blockIdx.y;
+  L += (int64_t)blockIdx.y * l_bs;
   int k = *k_dev;
   int64_t total = (int64_t)k * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -57,6 +69,7 @@ __global__ void scaled_adjoint_kernel(const T* V, int ldv, const double* lam, co
 
 template <typename T>
 __global__ void identity_kernel(T* dst, int n) {
+  dst += (int64_t)blockIdx.y * n * n;
   int64_t total = (int64_t)n * n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -126,12 +139,68 @@ cudaError_t allow_max_smem(const void* func) {
                               optin - (int)fa.sharedSizeBytes);
 }
 
+// Largest cluster size <= want (at most 16) for which one cluster of `func` with this
+// block and shared-memory size fits on the GPU; 0 if none.  Cached per (func, smem).
+int cluster_ctas(const void* func, int want, int threads, size_t smem) {
+  struct Entry {
+    const void* f;
+    size_t smem;
+    int threads, want, got;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry& e : cache)
+      if (e.f == func && e.smem == smem && e.threads == threads && e.want == want) return e.got;
+  }
+  want = std::max(1, std::min(want, 16));
+  int got = 0;
+  if (cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(want);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    int maxc = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&maxc, func, &cfg) == cudaSuccess) {
+      got = std::min(want, maxc);
+      // the cluster size must divide the grid, which is one cluster
+      while (got > 1 && (got & (got - 1))) --got;
+    }
+  }
+  cudaGetLastError();  // a refused query leaves no sticky error
+  std::lock_guard<std::mutex> lk(mu);
+  cache.push_back({func, smem, threads, want, got});
+  return got;
+}
+
+// `grid` CTAs running `func` in thread-block clusters of `cluster` CTAs.  The CTAs of a
+// cluster are co-scheduled, so they may wait on each other; unlike cooperative launches,
+// clusters issued from different streams run concurrently.
+cudaError_t launch_cluster(const void* func, int cluster, int grid, int threads, size_t smem,
+                           void** args, cudaStream_t s) {
+  const int ctas = cluster;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = ctas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, func, args);
+}
+
 template <typename T>
 cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, double* scratch,
-                              cudaStream_t s) {
-  cudaError_t err = cudaMemsetAsync(scratch, 0, sizeof(double), s);
+                              cudaStream_t s, int nb) {
+  cudaError_t err = cudaMemsetAsync(scratch, 0, sizeof(double) * nb, s);
   if (err != cudaSuccess) return err;
-  int g = std::min(grid_for(n), 1024);
+  const dim3 g(std::min(grid_for(n), std::max(1, 1024 / nb)), nb);
   note_launches(CBC_K_AUX, 2);
   sumsq_kernel<T><<<g, 256, 0, s>>>(x, n, scratch);
   scale_kernel<T><<<g, 256, 0, s>>>(x, n, scratch, log_acc, status);
@@ -140,16 +209,17 @@ cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, dou
 
 template <typename T>
 cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_dev, int n, T* L,
-                           cudaStream_t s) {
+                           cudaStream_t s, int nb, int64_t l_bs) {
   note_launches(CBC_K_AUX, 1);
-  scaled_adjoint_kernel<T><<<grid_for((int64_t)ldv * n), 256, 0, s>>>(V, ldv, lam, k_dev, n, L);
+  scaled_adjoint_kernel<T><<<dim3(grid_for((int64_t)ldv * n), nb), 256, 0, s>>>(V, ldv, lam, k_dev,
+                                                                              n, L, l_bs);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t fill_identity(T* dst, int n, cudaStream_t s) {
+cudaError_t fill_identity(T* dst, int n, cudaStream_t s, int nb) {
   note_launches(CBC_K_AUX, 1);
-  identity_kernel<T><<<grid_for((int64_t)n * n), 256, 0, s>>>(dst, n);
+  identity_kernel<T><<<dim3(grid_for((int64_t)n * n), nb), 256, 0, s>>>(dst, n);
   return cudaGetLastError();
 }
 
@@ -191,17 +261,18 @@ cudaError_t narrow_from_f64(const void* src, bool cplx, void* dst, int dst_dtype
 }
 
 template cudaError_t normalize_inplace<double>(double*, int64_t, double*, int*, double*,
-                                               cudaStream_t);
-template cudaError_t normalize_inplace<zdbl>(zdbl*, int64_t, double*, int*, double*, cudaStream_t);
+                                               cudaStream_t, int);
+template cudaError_t normalize_inplace<zdbl>(zdbl*, int64_t, double*, int*, double*, cudaStream_t,
+                                             int);
 template cudaError_t scaled_adjoint<double>(const double*, int, const double*, const int*, int,
-                                            double*, cudaStream_t);
+                                            double*, cudaStream_t, int, int64_t);
 template cudaError_t scaled_adjoint<zdbl>(const zdbl*, int, const double*, const int*, int, zdbl*,
-                                          cudaStream_t);
+                                          cudaStream_t, int, int64_t);
 template cudaError_t permute<double>(const double*, double*, int, const int64_t*, const int*,
                                      cudaStream_t);
 template cudaError_t permute<zdbl>(const zdbl*, zdbl*, int, const int64_t*, const int*,
                                    cudaStream_t);
-template cudaError_t fill_identity<double>(double*, int, cudaStream_t);
-template cudaError_t fill_identity<zdbl>(zdbl*, int, cudaStream_t);
+template cudaError_t fill_identity<double>(double*, int, cudaStream_t, int);
+template cudaError_t fill_identity<zdbl>(zdbl*, int, cudaStream_t, int);
 
 }  // namespace cbc

@@ -35,10 +35,29 @@ struct Arena {
     ptrs.push_back(p);
     return static_cast<T*>(p);
   }
+  // scopes: release() frees (stream-ordered) everything allocated after mark()
+  size_t mark() const { return ptrs.size(); }
+  void release(size_t mk) {
+    while (ptrs.size() > mk) {
+      cudaFreeAsync(ptrs.back(), s);
+      ptrs.pop_back();
+    }
+  }
+  // frees one allocation early
+  void drop(void* p) {
+    for (size_t i = 0; i < ptrs.size(); ++i)
+      if (ptrs[i] == p) {
+        cudaFreeAsync(p, s);
+        ptrs.erase(ptrs.begin() + i);
+        return;
+      }
+  }
   ~Arena() {
     for (void* p : ptrs) cudaFreeAsync(p, s);
   }
 };
+
+
 
 #define CK(expr)                                         \
   do {                                                   \
@@ -61,7 +80,8 @@ int status_to_rc(int st) {
   }
 }
 
-// device scalars of one call
+// device scalars of one call: one status word; k, the two log scales and the
+// reduction scratch per instance of a group
 struct Scalars {
   int* status;
   int* k;
@@ -84,27 +104,36 @@ T host_one() {
 // path, tensor-core slices on the mixed path (`fwd` picks the slice count of the first
 // sweep, which feeds the truncations, or of the last one).  `gram` halves the
 // algorithmic flops.
+// `nb` instances of one shape run in lockstep: every operand of every call is then nb
+// copies, View::bs elements apart.
 struct Prec {
   bool mixed = false;
   int s_fwd = 5, s_bwd = 4;
   Arena* ar = nullptr;
   int* status = nullptr;
+  int nb = 1;
 };
 
 template <typename T>
 cudaError_t tgemm(const Prec& pr, bool fwd, bool gram, int M, int N, int K, const T* A,
                   const View& va, bool ca, const T* B, const View& vb, bool cb, T* C,
                   const View& vc, cudaStream_t s) {
-  double fl = (ops<T>::cplx ? 8.0 : 2.0) * (double)M * N * K * (gram ? 0.5 : 1.0);
+  double fl = (ops<T>::cplx ? 8.0 : 2.0) * (double)M * N * K * (gram ? 0.5 : 1.0) * pr.nb;
   if (pr.mixed && K > 0) {
     const int S = fwd ? pr.s_fwd : pr.s_bwd;
-    void* ws = pr.ar->get<char>(gemm_tc_workspace_bytes(M, N, K, ops<T>::cplx, S));
+    const size_t mk = pr.ar->mark();
+    void* ws = pr.ar->get<char>(gemm_tc_workspace_bytes(M, N, K, ops<T>::cplx, S, pr.nb));
     if (!ws) return pr.ar->err;
-    KTimer t(CBC_K_GEMM_TC, s, 0, fl);
-    return gemm_tc<T>(M, N, K, A, va, ca, B, vb, cb, C, vc, S, ws, pr.status, s);
+    cudaError_t e;
+    {
+      KTimer t(CBC_K_GEMM_TC, s, 0, fl);
+      e = gemm_tc<T>(M, N, K, A, va, ca, B, vb, cb, C, vc, S, ws, pr.status, s, pr.nb);
+    }
+    pr.ar->release(mk);  // the slices are dead once the launch is queued
+    return e;
   }
   KTimer t(CBC_K_GEMM_F64, s, 0, fl);
-  return gemm_f64<T>(M, N, K, 1, A, va, ca, B, vb, cb, C, vc, s);
+  return gemm_f64<T>(M, N, K, pr.nb, A, va, ca, B, vb, cb, C, vc, s);
 }
 
 template <typename T>
@@ -113,12 +142,15 @@ double eig_flops(int m, int k) {
                       : (4.0 / 3.0) * m * (double)m * m + 2.0 * m * (double)m * k;
 }
 
-// read status and k after a compression
-int read_k(const Scalars& sc, cudaStream_t s, int* k) {
-  int h[2] = {0, 0};
-  CK(cudaMemcpyAsync(h, sc.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+// read status and k after a compression (k of every instance of a group: they must
+// agree, else kGroupSplit)
+int read_k(const Scalars& sc, cudaStream_t s, int nb, int* k) {
+  std::vector<int> h(1 + nb, 0);
+  CK(cudaMemcpyAsync(h.data(), sc.status, (1 + nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (h[0] != 0) return status_to_rc(h[0]);
+  for (int b = 1; b < nb; ++b)
+    if (h[1 + b] != h[1]) return kGroupSplit;
   *k = h[1];
   return CBC_OK;
 }
@@ -126,41 +158,49 @@ int read_k(const Scalars& sc, cudaStream_t s, int* k) {
 // Compression of the row leg of M (m x n, row-major): writes the k x n factor whose
 // Gram reproduces the rank-k truncation of M^H M (Sec. III A, text after Eq.
 // (tt_cbc_first_contraction)), normalised, and returns k.
+// L (k x n per instance) comes from `keep` (default: ar); the rest is released on
+// return.
 template <typename T>
 int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t max_bond,
                   double tol, const Options& o, const Scalars& sc, cudaStream_t s, T** Lout,
-                  int* kout) {
+                  int* kout, Arena* keep = nullptr) {
   const int kmax = (int)((max_bond > 0) ? std::min<int64_t>(max_bond, std::min(m, n)) : std::min(m, n));
   const double floor_rel = o.eps_rank * o.eps_rank;
   const int g = std::min(m, n);
-  T* K = ar.get<T>((size_t)g * g);
-  double* lam = ar.get<double>(g);
-  T* U = ar.get<T>((size_t)g * kmax);
-  char* work = ar.get<char>(eig_workspace_bytes(g, kmax, ops<T>::cplx));
+  const int nb = pr.nb;
+  const int64_t mbs = (int64_t)m * n;  // M of consecutive instances
+  const size_t mk = ar.mark();
+  T* K = ar.get<T>((size_t)nb * g * g);
+  double* lam = ar.get<double>((size_t)nb * g);
+  T* U = ar.get<T>((size_t)nb * g * kmax);
+  char* work = ar.get<char>(nb * eig_workspace_bytes(g, kmax, ops<T>::cplx));
   CKA(K); CKA(lam); CKA(U); CKA(work);
   if (m <= n) {  // K = M M^H, eigenvectors = left singular vectors
-    CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n), false, M, View::transposed(n), true, K,
-                   View::rowmajor(m), s));
+    CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n, mbs), false, M,
+                View::transposed(n, mbs), true, K, View::rowmajor(m, (int64_t)g * g), s));
   } else {       // G = M^H M, eigenvectors = right singular vectors
-    CK(tgemm<T>(pr, true, true, n, n, m, M, View::transposed(n), true, M, View::rowmajor(n), false, K,
-                   View::rowmajor(n), s));
+    CK(tgemm<T>(pr, true, true, n, n, m, M, View::transposed(n, mbs), true, M,
+                View::rowmajor(n, mbs), false, K, View::rowmajor(n, (int64_t)g * g), s));
   }
   {
-    KTimer t(CBC_K_EIG, s, 0, eig_flops<T>(g, kmax));
-    CK(heev_top<T>(K, g, kmax, max_bond, tol, floor_rel, lam, U, sc.k, work, sc.status, num_sms(), s));
+    KTimer t(CBC_K_EIG, s, 0, eig_flops<T>(g, kmax) * nb);
+    CK(heev_top<T>(K, g, kmax, max_bond, tol, floor_rel, lam, U, sc.k, work, sc.status, num_sms(),
+                   s, nb));
   }
   int k = 0;
-  int rc = read_k(sc, s, &k);
+  int rc = read_k(sc, s, nb, &k);
   if (rc != CBC_OK) return rc;
-  T* L = ar.get<T>((size_t)k * n);
-  CKA(L);
+  T* L = (keep ? keep : &ar)->get<T>((size_t)nb * k * n);
+  if (!L) return cuda_fail((keep ? keep : &ar)->err, "workspace allocation L");
+  const int64_t lbs = (int64_t)k * n;
   if (m <= n) {  // L = U_k^H M
-    CK(tgemm<T>(pr, true, false, k, n, m, U, View::transposed(kmax), true, M, View::rowmajor(n), false, L,
-                   View::rowmajor(n), s));
+    CK(tgemm<T>(pr, true, false, k, n, m, U, View::transposed(kmax, (int64_t)g * kmax), true, M,
+                View::rowmajor(n, mbs), false, L, View::rowmajor(n, lbs), s));
   } else {       // L = diag(sqrt(lambda_k)) V_k^H
-    CK(scaled_adjoint<T>(U, kmax, lam, sc.k, n, L, s));
+    CK(scaled_adjoint<T>(U, kmax, lam, sc.k, n, L, s, nb, lbs));
   }
-  CK(normalize_inplace<T>(L, (int64_t)k * n, sc.log_fwd, sc.status, sc.scratch, s));
+  CK(normalize_inplace<T>(L, lbs, sc.log_fwd, sc.status, sc.scratch, s, nb));
+  if (keep) ar.release(mk);
   *Lout = L;
   *kout = k;
   return CBC_OK;
@@ -168,160 +208,253 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
 
 // S (m x n, row-major) -> Q with orthonormal rows spanning the row space of S, in place
 // (CholeskyQR2; Eq. (tt_cbc_qr_decomp) is the LQ on chi_{i-1}).  Requires m <= n.
+// (nb instances: S m*n elements apart.)
 template <typename T>
 int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars& sc,
                     cudaStream_t s) {
-  T* G = ar.get<T>((size_t)m * m);
-  void* bar = ar.get<GridBarrier>(1);
+  const int nb = pr.nb;
+  const size_t mk = ar.mark();
+  T* G = ar.get<T>((size_t)nb * m * m);
+  void* bar = ar.get<GridBarrier>(nb);
   CKA(G); CKA(bar);
+  const int64_t sbs = (int64_t)m * n;
   for (int rep = 0; rep < 2; ++rep) {
-    CK(tgemm<T>(pr, false, true, m, m, n, S, View::rowmajor(n), false, S, View::transposed(n), true, G,
-                   View::rowmajor(m), s));
+    CK(tgemm<T>(pr, false, true, m, m, n, S, View::rowmajor(n, sbs), false, S,
+                View::transposed(n, sbs), true, G, View::rowmajor(m, (int64_t)m * m), s));
     KTimer t(CBC_K_CHOLQR, s, 0,
-             (ops<T>::cplx ? 4.0 : 1.0) * ((double)m * m * m / 3.0 + (double)m * m * n));
-    CK(cholesky_lower<T>(G, m, sc.status, bar, num_sms(), s));
-    CK(trsm_lower_left<T>(G, S, m, n, sc.status, bar, num_sms(), s));
+             nb * (ops<T>::cplx ? 4.0 : 1.0) * ((double)m * m * m / 3.0 + (double)m * m * n));
+    CK(cholesky_lower<T>(G, m, sc.status, bar, num_sms(), s, nb));
+    CK(trsm_lower_left<T>(G, S, m, n, sc.status, bar, num_sms(), s, nb));
   }
+  ar.release(mk);
   return CBC_OK;
 }
 
 // ---- tensor train (Sec. III A) ---------------------------------------------------------
+// One call runs nb instances of identical shapes in lockstep (nb = 1 for cbc_apply):
+// every contraction, Gram product, eigensolve, CholeskyQR and normalisation below is one
+// launch over the whole group.  Returns kGroupSplit when the instances stop agreeing on
+// a rank (their outputs would differ in shape).
 template <typename T>
-int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
-           Net* out) {
+int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net*>& opv,
+                 int64_t max_bond, double tol, const Options& o, const std::vector<Net*>& outs) {
+  const Net& st = *sts[0];
+  const Net& op = *opv[0];
+  const int nb = (int)sts.size();
   cudaStream_t s = st.stream;
   const int L = st.n;
-  Arena ar(s);
-  int* d_int = ar.get<int>(4);
-  double* d_dbl = ar.get<double>(4);
+  // the group runs on the first instance's stream, after the others' pending work
+  for (int b = 0; b < nb; ++b)
+    for (cudaStream_t o2 : {sts[b]->stream, opv[b]->stream})
+      if (o2 != s) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, o2));
+        CK(cudaStreamWaitEvent(s, ev, 0));
+        cudaEventDestroy(ev);
+      }
+  Arena ar(s);   // scalars, environments: the whole call
+  Arena tmp(s);  // per-site temporaries, released after each site
+  int* d_int = ar.get<int>(std::max(4, 1 + nb));
+  double* d_dbl = ar.get<double>(std::max(4, 3 * nb));
   CKA(d_int); CKA(d_dbl);
-  CK(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
-  CK(cudaMemsetAsync(d_dbl, 0, 4 * sizeof(double), s));
-  Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + 1, d_dbl + 2};
+  CK(cudaMemsetAsync(d_int, 0, std::max(4, 1 + nb) * sizeof(int), s));
+  CK(cudaMemsetAsync(d_dbl, 0, std::max(4, 3 * nb) * sizeof(double), s));
+  Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + nb, d_dbl + 2 * nb};
   Prec pr;
   pr.mixed = (o.precision == CBC_PREC_MIXED);
   pr.s_fwd = o.slices_fwd;
   pr.s_bwd = o.slices_bwd;
-  pr.ar = &ar;
+  pr.ar = &tmp;
   pr.status = sc.status;
+  pr.nb = nb;
   auto sb = [&](int i) { return i < L ? (int)st.bond[i] : 1; };  // alpha_{i-1} (site i's parent leg)
   auto ob = [&](int i) { return i < L ? (int)op.bond[i] : 1; };
-  const T one = host_one<T>();
+  const std::vector<T> ones(nb, host_one<T>());
+  // node tensor i of every instance, consecutive (a gather into `tmp` when nb > 1)
+  auto site_in = [&](int i, bool opside, const T** p) -> int {
+    const Net& ref = opside ? op : st;
+    if (nb == 1) {
+      *p = static_cast<const T*>(ref.data[i]);
+      return CBC_OK;
+    }
+    const int64_t ne = ref.numel[i];
+    T* g = tmp.get<T>((size_t)nb * ne);
+    if (!g) return cuda_fail(tmp.err, "workspace allocation (gathered inputs)");
+    for (int b = 0; b < nb; ++b)
+      CK(cudaMemcpyAsync(g + b * ne, (opside ? opv[b] : sts[b])->data[i], sizeof(T) * ne,
+                         cudaMemcpyDeviceToDevice, s));
+    *p = g;
+    return CBC_OK;
+  };
 
   // forward sweep: L^[0] = 1, Eq. (tt_cbc_first_contraction), compression of (chi, sigma')
   std::vector<T*> env(L, nullptr);
   std::vector<int> chi(L, 1);
-  env[0] = ar.get<T>(1);
+  env[0] = ar.get<T>(nb);
   CKA(env[0]);
-  CK(cudaMemcpyAsync(env[0], &one, sizeof(T), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(env[0], ones.data(), sizeof(T) * nb, cudaMemcpyHostToDevice, s));
   for (int i = 0; i < L - 1; ++i) {
     const int c = chi[i], b = ob(i), a = sb(i), d = (int)st.phys[i], a2 = sb(i + 1), b2 = ob(i + 1);
-    const T* Ti = static_cast<const T*>(st.data[i]);
-    const T* Wi = static_cast<const T*>(op.data[i]);
+    const size_t mk = tmp.mark();
+    const T *Ti = nullptr, *Wi = nullptr;
+    int rc = site_in(i, false, &Ti);
+    if (rc == CBC_OK) rc = site_in(i, true, &Wi);
+    if (rc != CBC_OK) return rc;
+    const int64_t tbs = (int64_t)a * d * a2, wbs = (int64_t)b * d * d * b2;
+    const int64_t xbs = (int64_t)c * b * d * a2, lbs = (int64_t)c * d * b2 * a2;
     // F1: X[(chi b), (sigma a')] = sum_a L[(chi b), a] T[a, (sigma a')]
-    T* X = ar.get<T>((size_t)c * b * d * a2);
-    CKA(X);
-    CK(tgemm<T>(pr, true, false, c * b, d * a2, a, env[i], View::rowmajor(a), false, Ti, View::rowmajor(d * a2),
-                   false, X, View::rowmajor(d * a2), s));
+    T* X = tmp.get<T>((size_t)nb * xbs);
+    if (!X) return cuda_fail(tmp.err, "workspace allocation X");
+    CK(tgemm<T>(pr, true, false, c * b, d * a2, a, env[i], View::rowmajor(a, (int64_t)c * b * a),
+                false, Ti, View::rowmajor(d * a2, tbs), false, X, View::rowmajor(d * a2, xbs), s));
     // F2: L'[chi, sigma', b', a'] = sum_{b, sigma} X[chi, b, sigma, a'] W[b, sigma', sigma, b']
     //     as C[(sigma' b'), (chi a')] = W[(sigma' b'), (b sigma)] X[(b sigma), (chi a')]
-    T* Lp = ar.get<T>((size_t)c * d * b2 * a2);
-    CKA(Lp);
+    T* Lp = tmp.get<T>((size_t)nb * lbs);
+    if (!Lp) return cuda_fail(tmp.err, "workspace allocation L'");
     View vw;
     vw.rows2(b2, (int64_t)d * b2, 1).cols2(d, (int64_t)d * d * b2, b2);
+    vw.bs = wbs;
     View vx;
     vx.rs_in = a2;
     vx.cols2(a2, (int64_t)b * d * a2, 1);
+    vx.bs = xbs;
     View vl;
     vl.rs_in = a2;
     vl.cols2(a2, (int64_t)d * b2 * a2, 1);
+    vl.bs = lbs;
     CK(tgemm<T>(pr, true, false, d * b2, c * a2, b * d, Wi, vw, false, X, vx, false, Lp, vl, s));
     // F3: compress M[(chi sigma'), (b' a')]
     int k = 0;
-    int rc = compress_rows<T>(ar, pr, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k);
+    rc = compress_rows<T>(tmp, pr, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k,
+                          &ar);
     if (rc != CBC_OK) return rc;
     chi[i + 1] = k;
+    tmp.release(mk);
   }
 
   // backward sweep: R^[L] = 1, Eqs. (right_sweep_init_contr), (tt_cbc_qr_decomp),
   // (tt_cbc_final_contraction)
-  out->kind = 0;
-  out->n = L;
-  out->root = 0;
-  out->parent = st.parent;
-  out->phys = st.phys;
-  out->bond.assign(L, 1);
-  out->children = st.children;
-  out->cplx = st.cplx;
-  out->stream = s;
-  out->data.assign(L, nullptr);
-  out->numel.assign(L, 0);
-  T* R = ar.get<T>(1);
+  for (int b = 0; b < nb; ++b) {
+    Net* out = outs[b];
+    out->kind = 0;
+    out->n = L;
+    out->root = 0;
+    out->parent = sts[b]->parent;
+    out->phys = sts[b]->phys;
+    out->bond.assign(L, 1);
+    out->children = sts[b]->children;
+    out->cplx = sts[b]->cplx;
+    out->stream = (nb == 1) ? s : sts[b]->stream;
+    out->data.assign(L, nullptr);
+    out->numel.assign(L, 0);
+  }
+  T* R = ar.get<T>(nb);
   CKA(R);
-  CK(cudaMemcpyAsync(R, &one, sizeof(T), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(R, ones.data(), sizeof(T) * nb, cudaMemcpyHostToDevice, s));
   int chiR = 1;
   for (int i = L - 1; i >= 0; --i) {
     const int a_in = sb(i), b_in = ob(i), d = (int)st.phys[i], a_out = sb(i + 1), b_out = ob(i + 1);
     const int cp = chiR, c = chi[i];
-    const T* Ti = static_cast<const T*>(st.data[i]);
-    const T* Wi = static_cast<const T*>(op.data[i]);
+    const size_t mk = tmp.mark();
+    const T *Ti = nullptr, *Wi = nullptr;
+    int rc = site_in(i, false, &Ti);
+    if (rc == CBC_OK) rc = site_in(i, true, &Wi);
+    if (rc != CBC_OK) return rc;
+    const int64_t tbs = (int64_t)a_in * d * a_out, wbs = (int64_t)b_in * d * d * b_out;
+    const int64_t rbs = (int64_t)cp * b_out * a_out, ybs = (int64_t)a_in * d * cp * b_out;
+    const int64_t zbs = (int64_t)b_in * a_in * d * cp;
     // B1: Y[(a sigma), (chi' b_out)] = sum_{a_out} T[(a sigma), a_out] R[(chi' b_out), a_out]
-    T* Y = ar.get<T>((size_t)a_in * d * cp * b_out);
-    CKA(Y);
-    CK(tgemm<T>(pr, false, false, a_in * d, cp * b_out, a_out, Ti, View::rowmajor(a_out), false, R,
-                   View::transposed(a_out), false, Y, View::rowmajor(cp * b_out), s));
+    T* Y = tmp.get<T>((size_t)nb * ybs);
+    if (!Y) return cuda_fail(tmp.err, "workspace allocation Y");
+    CK(tgemm<T>(pr, false, false, a_in * d, cp * b_out, a_out, Ti, View::rowmajor(a_out, tbs), false,
+                R, View::transposed(a_out, rbs), false, Y, View::rowmajor(cp * b_out, ybs), s));
     // B2: Z[b_in, a, sigma', chi'] = sum_{sigma, b_out} W[b_in, sigma', sigma, b_out] Y[a, sigma, chi', b_out]
     //     as C[(b_in sigma'), (a chi')] = W[(b_in sigma'), (sigma b_out)] Y[(sigma b_out), (a chi')]
-    T* Z = ar.get<T>((size_t)b_in * a_in * d * cp);
-    CKA(Z);
+    T* Z = tmp.get<T>((size_t)nb * zbs);
+    if (!Z) return cuda_fail(tmp.err, "workspace allocation Z");
     View vy;
     vy.rows2(b_out, (int64_t)cp * b_out, 1).cols2(cp, (int64_t)d * cp * b_out, b_out);
+    vy.bs = ybs;
     View vz;
     vz.rows2(d, (int64_t)a_in * d * cp, cp).cols2(cp, (int64_t)d * cp, 1);
-    CK(tgemm<T>(pr, false, false, b_in * d, a_in * cp, d * b_out, Wi, View::rowmajor(d * b_out), false, Y, vy,
-                   false, Z, vz, s));
+    vz.bs = zbs;
+    CK(tgemm<T>(pr, false, false, b_in * d, a_in * cp, d * b_out, Wi, View::rowmajor(d * b_out, wbs),
+                false, Y, vy, false, Z, vz, s));
     // B3: S[chi, (sigma' chi')] = sum_{(b a)} L^[i-1][chi, (b a)] Z[(b a), (sigma' chi')]
     const int n = d * cp;
     const int m = c;
     const int cn = (m <= n) ? m : n;
+    const bool formed = (i == 0 || m <= n);            // else Q is the identity
+    const int64_t nbs = formed ? (int64_t)m * n : (int64_t)n * n;  // node stride in the group
     T* node = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&node), sizeof(T) * std::max<size_t>((size_t)cn * n, (size_t)m * n), s));
-    out->data[i] = node;
-    out->numel[i] = (int64_t)cn * n;
-    if (i == 0 || m <= n) {
-      CK(tgemm<T>(pr, false, false, m, n, b_in * a_in, env[i], View::rowmajor(b_in * a_in), false, Z,
-                     View::rowmajor(n), false, node, View::rowmajor(n), s));
+    if (nb == 1) {  // built in the output tensor itself
+      CK(cudaMallocAsync(reinterpret_cast<void**>(&node), sizeof(T) * std::max<size_t>((size_t)cn * n, (size_t)m * n), s));
+      outs[0]->data[i] = node;
+    } else {
+      node = tmp.get<T>((size_t)nb * nbs);
+      if (!node) return cuda_fail(tmp.err, "workspace allocation S");
     }
+    for (int b = 0; b < nb; ++b) outs[b]->numel[i] = (int64_t)cn * n;
+    if (formed) {
+      CK(tgemm<T>(pr, false, false, m, n, b_in * a_in, env[i], View::rowmajor(b_in * a_in, (int64_t)m * b_in * a_in),
+                  false, Z, View::rowmajor(n, zbs), false, node, View::rowmajor(n, nbs), s));
+    }
+    // publishes the group's node tensors into the per-instance outputs
+    auto emit = [&]() -> int {
+      if (nb == 1) return CBC_OK;
+      for (int b = 0; b < nb; ++b) {
+        void* dst = nullptr;
+        CK(cudaMallocAsync(&dst, sizeof(T) * (size_t)cn * n, s));
+        outs[b]->data[i] = dst;
+        CK(cudaMemcpyAsync(dst, node + b * nbs, sizeof(T) * (size_t)cn * n, cudaMemcpyDeviceToDevice, s));
+      }
+      return CBC_OK;
+    };
     if (i == 0) {  // T'^[1] = S^[1]
-      CK(normalize_inplace<T>(node, (int64_t)n, sc.log_out, sc.status, sc.scratch, s));
-      out->bond[0] = 1;
+      CK(normalize_inplace<T>(node, (int64_t)n, sc.log_out, sc.status, sc.scratch, s, nb));
+      for (int b = 0; b < nb; ++b) outs[b]->bond[0] = 1;
+      rc = emit();
+      if (rc != CBC_OK) return rc;
+      tmp.release(mk);
       break;
     }
     // B4: S = R Q on chi_{i-1}; Q^[i] is the new tensor
     if (m <= n) {
-      int rc = lq_rows_inplace<T>(ar, pr, node, m, n, sc, s);
+      rc = lq_rows_inplace<T>(tmp, pr, node, m, n, sc, s);
       if (rc != CBC_OK) return rc;
     } else {  // more rows than columns: any unitary basis of the columns; take the identity
-      CK(fill_identity<T>(node, n, s));
+      CK(fill_identity<T>(node, n, s, nb));
     }
     // B5: R^[i-1][chi'', (b a)] = sum_{(sigma' chi')} conj(Q[chi'', (sigma' chi')]) Z[(b a), (sigma' chi')]
-    T* Rn = ar.get<T>((size_t)cn * b_in * a_in);
+    const int64_t rnbs = (int64_t)cn * b_in * a_in;
+    T* Rn = ar.get<T>((size_t)nb * rnbs);
     CKA(Rn);
-    CK(tgemm<T>(pr, false, false, cn, b_in * a_in, n, node, View::rowmajor(n), true, Z, View::transposed(n),
-                   false, Rn, View::rowmajor(b_in * a_in), s));
-    CK(normalize_inplace<T>(Rn, (int64_t)cn * b_in * a_in, sc.log_out, sc.status, sc.scratch, s));
+    CK(tgemm<T>(pr, false, false, cn, b_in * a_in, n, node, View::rowmajor(n, nbs), true, Z,
+                View::transposed(n, zbs), false, Rn, View::rowmajor(b_in * a_in, rnbs), s));
+    CK(normalize_inplace<T>(Rn, rnbs, sc.log_out, sc.status, sc.scratch, s, nb));
+    ar.drop(R);
     R = Rn;
     chiR = cn;
-    out->bond[i] = cn;
+    for (int b = 0; b < nb; ++b) outs[b]->bond[i] = cn;
+    rc = emit();
+    if (rc != CBC_OK) return rc;
+    tmp.release(mk);
   }
-  int h[2];
-  double hl = 0.0;
-  CK(cudaMemcpyAsync(h, sc.status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&hl, sc.log_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  std::vector<int> h(1, 0);
+  std::vector<double> hl(nb, 0.0);
+  CK(cudaMemcpyAsync(h.data(), sc.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hl.data(), sc.log_out, sizeof(double) * nb, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (h[0] != 0) return status_to_rc(h[0]);
-  out->log_norm = hl;
+  for (int b = 0; b < nb; ++b) outs[b]->log_norm = hl[b];
   return CBC_OK;
+}
+
+template <typename T>
+int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
+           Net* out) {
+  return run_tt_group<T>({&st}, {&op}, max_bond, tol, o, {out});
 }
 
 // ---- trees (Sec. III B) ---------------------------------------------------------------
@@ -637,6 +770,25 @@ bool is_chain(const Net& t) {
 }
 
 }  // namespace
+
+int run_cbc_group(const std::vector<const Net*>& sts, const std::vector<const Net*>& ops,
+                  int64_t max_bond, double tol, const Options& o, const std::vector<Net*>& outs) {
+  if (sts.empty() || sts.size() != ops.size() || sts.size() != outs.size())
+    return fail(CBC_ERR_INVALID_ARG, "run_cbc_group: bad group");
+  if (sts.size() == 1) return run_cbc(*sts[0], *ops[0], max_bond, tol, o, outs[0]);
+  const Net& st = *sts[0];
+  if (!is_chain(st)) return kGroupSplit;  // trees run one by one
+  for (size_t b = 0; b < sts.size(); ++b)
+    if (sts[b]->cplx != st.cplx || ops[b]->cplx != st.cplx || sts[b]->n != st.n ||
+        sts[b]->phys != st.phys || sts[b]->bond != st.bond || ops[b]->bond != ops[0]->bond ||
+        !is_chain(*sts[b]))
+      return kGroupSplit;
+  if (o.precision == CBC_PREC_MIXED && (o.slices_fwd < 2 || o.slices_fwd > 5 || o.slices_bwd < 2 ||
+                                        o.slices_bwd > 5))
+    return fail(CBC_ERR_INVALID_ARG, "cbc_apply: slice counts must be in [2, 5]");
+  if (st.cplx) return run_tt_group<zdbl>(sts, ops, max_bond, tol, o, outs);
+  return run_tt_group<double>(sts, ops, max_bond, tol, o, outs);
+}
 
 int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
             Net* out) {

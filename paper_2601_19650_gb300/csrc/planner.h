@@ -37,6 +37,15 @@ struct Options {
 int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
             Net* out);
 
+// A group (see run_cbc_group) that cannot run in lockstep: shapes differ, a tree, or the
+// instances chose different ranks at some cut.  The caller runs the members one by one.
+constexpr int kGroupSplit = -77;
+
+// nb instances with identical chain shapes, max_bond and tol, in lockstep: one launch
+// per step for the whole group.  Returns CBC_OK, an error, or kGroupSplit.
+int run_cbc_group(const std::vector<const Net*>& sts, const std::vector<const Net*>& ops,
+                  int64_t max_bond, double tol, const Options& o, const std::vector<Net*>& outs);
+
 // launch statistics (cbc_stats_* in cbc.h)
 struct KTimer {
   int cls;

@@ -151,6 +151,88 @@ def test_batched_heterogeneous(precision, bar):
 
 
 # ---------------------------------------------------------------------------------------
+# lockstep groups: cbc_apply_batched runs instances of one shape as one launch per step
+# ---------------------------------------------------------------------------------------
+def _apply_batched(probs, precision, workers=1):
+    """All instances through cbc_apply_batched (one stream each); host outputs and the
+    launch statistics of the call."""
+    import torch
+
+    from paper_2601_19650_gb300 import _cbc
+
+    streams = [torch.cuda.Stream() for _ in probs]
+    hs, ho = [], []
+    for p, s in zip(probs, streams):
+        hs.append(_cbc.create_from_host(p.state.parent, p.state.phys, p.state.bond,
+                                        p.state.tensors, "state", s.cuda_stream))
+        ho.append(_cbc.create_from_host(p.op.parent, p.op.phys, p.op.bond, p.op.tensors,
+                                        "op", s.cuda_stream))
+    torch.cuda.synchronize()
+    _cbc.cbc_stats_reset()
+    _cbc.cbc_stats_enable(True)
+    try:
+        outs = _cbc.cbc_apply_batched(hs, ho, [p.max_bond for p in probs],
+                                      [p.tol for p in probs], _cbc.make_options(precision),
+                                      workers=workers)
+    finally:
+        stats = _cbc.cbc_stats_read()
+        _cbc.cbc_stats_enable(False)
+    res = []
+    for p, o in zip(probs, outs):
+        cplx = np.iscomplexobj(p.state.tensors[0])
+        res.append(_cbc.fetch_network(o, _cbc.output_shape_fn(p.state.parent, p.state.phys),
+                                      cplx))
+    for h in outs + hs:
+        _cbc.ttn_destroy(h)
+    for h in ho:
+        _cbc.ttno_destroy(h)
+    return res, stats
+
+
+def _check_against_oracle(probs, res, bar):
+    refs = []
+    for p, (got, bonds, log_norm) in zip(probs, res):
+        ref = cbc.cbc(p.state.parent, p.state.tensors, p.op.tensors, p.max_bond, p.tol)
+        assert list(bonds) == list(ref.out_bonds), (p.name, bonds, ref.out_bonds)
+        e = metrics.rel_err(p.state.parent, got, ref.tensors, log_norm, 0.0)
+        assert e <= bar, (p.name, p.seed, e)
+        refs.append(ref)
+    return refs
+
+
+@pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
+def test_group_lockstep(precision, bar):
+    L = 9
+    probs = [make_problem(2, seed=20 + j, L=L, chi=16, D=4, max_bond=12) for j in range(4)]
+    res, stats = _apply_batched(probs, precision)
+    _check_against_oracle(probs, res, bar)
+    # one eigensolver launch group per cut for the whole group, not one per instance
+    assert stats["eig"]["groups"] == L - 1, stats["eig"]
+
+
+def test_group_mixed_shapes_and_real():
+    # two shapes interleaved (two groups) plus a real-valued group
+    probs = [make_problem(2, seed=30 + j, L=7 + (j % 2), chi=12, D=3, max_bond=10)
+             for j in range(4)]
+    probs += [make_problem(2, seed=40 + j, L=6, chi=10, D=3, d=3, max_bond=8,
+                           dtype=np.float64) for j in range(3)]
+    res, _ = _apply_batched(probs, 0, workers=2)
+    _check_against_oracle(probs, res, FP64_BAR)
+
+
+def test_group_rank_disagreement_reruns_members():
+    # tolerance truncation: ranks depend on each instance's spectrum; when they differ
+    # the group is rerun member by member, with the same results as single calls
+    L = 8
+    probs = [make_problem(2, seed=50 + j, tol=3e-2, L=L, chi=12, D=3, max_bond=0)
+             for j in range(3)]
+    res, stats = _apply_batched(probs, 0)
+    refs = _check_against_oracle(probs, res, FP64_BAR)
+    if len({tuple(r.out_bonds) for r in refs}) > 1:
+        assert stats["eig"]["groups"] > L - 1, stats["eig"]
+
+
+# ---------------------------------------------------------------------------------------
 # trees (Sec. III B): binary trees with leaf-only physical legs, T-trees, fork trees
 # ---------------------------------------------------------------------------------------
 TREE_CASES = [
