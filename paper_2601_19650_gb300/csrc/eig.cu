@@ -762,6 +762,81 @@ __global__ void __launch_bounds__(128) backtransform_kernel(const T* V, const T*
   for (int i = tid; i < m; i += 128) U[(int64_t)i * kmax + jj] = u[i];
 }
 
+// Same back transformation with the lanes on the eigenvectors: a CTA takes 32 vectors
+// (one per lane, held in shared memory as u[row][lane]) and 8 warps split the rows.
+// Per reflector every lane sums conj(v_r) u_r over its warp's rows, the 8 partial sums
+// meet in shared memory (one barrier), and every lane updates its rows.  No shuffle
+// reductions and no half-empty warps: about a quarter of the FP64 instructions of the
+// one-vector-per-CTA form.  u needs m * 32 elements of shared memory.
+constexpr int BT_WARPS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
+    const T* V, const T* tau, const double* X, int m, int kmax, const int* k_dev, T* U,
+    size_t wb) {
+  using O = ops<T>;
+  extern __shared__ unsigned char smem_raw[];
+  T* u = reinterpret_cast<T*>(smem_raw);  // [m][32]
+  T* vs = u + (size_t)m * 32;             // [3][m]: v_j in slot j % 3 (staged one ahead)
+  __shared__ T part[2][BT_WARPS][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // matrix blockIdx.y of a batch
+  V = byte_shift(V, blockIdx.y * wb);
+  tau = byte_shift(tau, blockIdx.y * wb);
+  X = byte_shift(X, blockIdx.y * wb);
+  k_dev += blockIdx.y;
+  U += (size_t)blockIdx.y * m * kmax;
+  const int k = *k_dev;
+  const int c0 = blockIdx.x * 32;
+  if (c0 >= k) return;
+  const int col = c0 + lane;
+  const bool live = col < k;
+  const int rb = (m + BT_WARPS - 1) / BT_WARPS;
+  const int r0 = warp * rb, r1 = min(m, r0 + rb);
+  for (int r = r0; r < r1; ++r) u[(size_t)r * 32 + lane] = O::make(live ? X[(int64_t)r * kmax + col] : 0.0, 0.0);
+  if (m >= 2) {  // v_{m-2}: rows > m - 2
+    const T* vg = V + (int64_t)(m - 2) * m;
+    T* v0 = vs + (size_t)((m - 2) % 3) * m;
+    for (int q = m - 1 + (int)threadIdx.x; q < m; q += blockDim.x) v0[q] = vg[q];
+  }
+  __syncthreads();
+  int par = 0;
+  for (int j = m - 2; j >= 0; --j) {
+    const T* v = vs + (size_t)(j % 3) * m;
+    // partial dot over this warp's rows r > j, four independent accumulators
+    const int rs = max(r0, j + 1);
+    T a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
+    int r = rs;
+    for (; r + 3 < r1; r += 4) {
+      a0 = O::fma(O::conj(v[r]), u[(size_t)r * 32 + lane], a0);
+      a1 = O::fma(O::conj(v[r + 1]), u[(size_t)(r + 1) * 32 + lane], a1);
+      a2 = O::fma(O::conj(v[r + 2]), u[(size_t)(r + 2) * 32 + lane], a2);
+      a3 = O::fma(O::conj(v[r + 3]), u[(size_t)(r + 3) * 32 + lane], a3);
+    }
+    for (; r < r1; ++r) a0 = O::fma(O::conj(v[r]), u[(size_t)r * 32 + lane], a0);
+    part[par][warp][lane] = (a0 + a1) + (a2 + a3);
+    // stage the next reflector's vector (rows > j - 1).  Its slot last held v_{j+2},
+    // whose readers all finished before the barrier this warp passed last.
+    if (j >= 1) {
+      const T* vg = V + (int64_t)(j - 1) * m;
+      T* vn = vs + (size_t)((j - 1) % 3) * m;
+      for (int q = j + threadIdx.x; q < m; q += blockDim.x) vn[q] = vg[q];
+    }
+    __syncthreads();
+    if (rs < r1) {
+      T tot = part[par][0][lane];
+#pragma unroll
+      for (int w = 1; w < BT_WARPS; ++w) tot = tot + part[par][w][lane];
+      const T cf = tau[j] * tot;
+      for (int q = rs; q < r1; ++q) u[(size_t)q * 32 + lane] = u[(size_t)q * 32 + lane] - v[q] * cf;
+    }
+    par ^= 1;
+  }
+  __syncthreads();
+  if (live)
+    for (int r = r0; r < r1; ++r) U[(int64_t)r * kmax + col] = u[(size_t)r * 32 + lane];
+}
+
 }  // namespace
 
 // workspace layout (all 256-byte aligned)
@@ -888,7 +963,17 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   // 4. rank rule on the refined eigenvalues
   rank_kernel<<<nb, 256, 0, s>>>(d, rq, lam32, m, kmax, (long long)max_bond, tol, floor_rel,
                                  k_dev, lam, wb);
-  // 5. back transformation
+  // 5. back transformation: 32 vectors per CTA (fewer FP64 instructions) when u fits in
+  // shared memory and the batch gives enough CTAs to spread the FP64 work over the SMs;
+  // else one vector per CTA
+  const size_t shm32 = ((size_t)m * 32 + 3 * (size_t)m) * ts;
+  if (shm32 <= 200 * 1024 && (size_t)nb * ((kmax + 31) / 32) * 2 >= (size_t)num_sms) {
+    err = allow_max_smem((const void*)backtransform32_kernel<T>);
+    if (err != cudaSuccess) return err;
+    backtransform32_kernel<T><<<dim3((kmax + 31) / 32, nb), 32 * BT_WARPS, shm32, s>>>(
+        V, tau, X, m, kmax, k_dev, U, wb);
+    return cudaGetLastError();
+  }
   size_t shm = (size_t)m * ts;
   if (shm > 48 * 1024) {
     err = allow_max_smem((const void*)backtransform_kernel<T>);

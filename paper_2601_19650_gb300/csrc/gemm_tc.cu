@@ -170,6 +170,36 @@ struct TcArgs {
   int ebsB;              // entries of expB per problem
 };
 
+// ldexp((double)a, e) formed with integer operations: the int64 is rounded to 53 bits
+// (round to nearest, ties to even, as the conversion instruction does) and the exponent
+// field written directly, so the epilogue keeps off the narrow FP64 pipe of this part.
+// Results outside the normal range take the FP64 route.
+__device__ __forceinline__ double i64_ldexp(long long a, int e) {
+  if (a == 0) return 0.0;
+  const unsigned long long neg = a < 0 ? 1ull : 0ull;
+  const unsigned long long m = neg ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  int top = 63 - __clzll((long long)m);
+  unsigned long long mant;
+  if (top > 52) {
+    const int sh = top - 52;
+    const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    mant = m >> sh;
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++top;
+      }
+    }
+  } else {
+    mant = m << (52 - top);
+  }
+  const int E = top + e + 1023;
+  if (E <= 0 || E >= 2047) return ldexp((double)a, e);
+  return __longlong_as_double((long long)((neg << 63) | ((unsigned long long)E << 52) |
+                                          (mant & ((1ull << 52) - 1ull))));
+}
+
 template <int S, int BN>
 __global__ void __launch_bounds__(nthreads(BN), 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -324,7 +354,7 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
         const int col = n0 + cg * 32 + i;
         if (col < a.N2) {
           const int ncol = a.cplx ? (col >> 1) : col;
-          const double v = ldexp((double)acc[i], ea + expB[ncol] + bias);
+          const double v = i64_ldexp(acc[i], ea + expB[ncol] + bias);
           double* dst;
           if (a.cplx)
             dst = reinterpret_cast<double*>(Cp + 16 * (ro + a.vc.coff(ncol))) + (col & 1);
@@ -692,6 +722,7 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
   }
   dim3 grid(g.Mp / BM, g.N2p / g.BN, splits * nb);
   note_launches(CBC_K_GEMM_TC, 1);
+  note_flops(CBC_K_TC_ISSUED, 2.0 * g.Mp * g.N2p * g.K2p * (S * (S + 1) / 2) * nb);
   switch (S) {
     case 2: return launch<2>(ma, mb, args, grid, s);
     case 3: return launch<3>(ma, mb, args, grid, s);

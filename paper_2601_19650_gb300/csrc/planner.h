@@ -56,6 +56,7 @@ struct KTimer {
 };
 
 void note_launches(int cls, int n);
+void note_flops(int cls, double flops);
 
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);

@@ -23,6 +23,11 @@ void note_launches(int cls, int n) {
   g_stats.launches[cls] += n;
 }
 
+void note_flops(int cls, double flops) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_stats.flops[cls] += flops;
+}
+
 KTimer::KTimer(int cls_, cudaStream_t s_, int64_t launches, double flops) : cls(cls_), s(s_) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_stats.launches[cls] += launches;
