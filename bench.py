@@ -98,9 +98,10 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------------------
-def make_workload(seed: int):
+def make_workload(seed: int, sites: int = 0):
+    """The MPO-on-MPS workload (L=64 unless `sites` shortens the chain for profiling)."""
     from synth import make_problem
-    return make_problem(2, seed=seed)
+    return make_problem(2, seed=seed, **({"L": sites} if sites > 0 else {}))
 
 
 def oracle_time(prob, reps: int = 1):
@@ -159,9 +160,12 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--concurrency", type=int, default=1,
+    ap.add_argument("--concurrency", type=int, default=32,
                     help="independent applications per step (seeds rank*B .. rank*B+B-1), "
-                         "run concurrently by cbc_apply_batched, one stream each")
+                         "run by cbc_apply_batched: same-shape instances go in lockstep "
+                         "groups of up to 32 (one launch per step per group)")
+    ap.add_argument("--sites", type=int, default=0,
+                    help="shorter chains for profiling captures (default: the workload's 64)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -188,7 +192,7 @@ def main():
 
     # precision of the headline number: mixed when built, else fp64
     prec_name = args.precision
-    probs = [make_workload(seed=rank * B + j) for j in range(B)]
+    probs = [make_workload(seed=rank * B + j, sites=args.sites) for j in range(B)]
     prob = probs[0]
     st, op = prob.state, prob.op
     hs_list, ho_list = [], []
@@ -279,22 +283,35 @@ def main():
     ms_per_step = t_max / args.steps
 
     # per-kernel-class roofline of the dominant class
+    issued = stats.pop("tc_issued", {"flops": 0.0})["flops"]  # tensor-pipe flops, no time
     classes = {k: v for k, v in stats.items() if v["ms"] > 0}
     dom = max(classes, key=lambda k: classes[k]["ms"]) if classes else None
     flops_per_app = sum(v["flops"] for v in stats.values()) / args.steps
+    bf16_peak, bf16_note = 1700.0, "of fallback"
+    try:
+        mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        bf16_peak = float(mp.get("bf16_tflops_sustained") or mp.get("bf16_tflops"))
+        bf16_note = "of measured sustained bf16"
+    except (OSError, ValueError, TypeError):
+        pass
+    roofline_tc = None
+    if "gemm_tc" in classes:
+        d = classes["gemm_tc"]
+        sec = d["ms"] / 1e3
+        roofline_tc = {"bound": "tensor", "kernel_class": "gemm_tc",
+                       "achieved": issued / sec / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                       "frac": issued / sec / 1e12 / bf16_peak,
+                       "algorithmic_tflops": d["flops"] / sec / 1e12,
+                       "note": "bf16 slice products issued on the tensor pipe (padded, "
+                               f"real-embedded shapes) over the class's event time, {bf16_note}"}
     roofline = None
     if dom is not None:
         d = classes[dom]
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
         if dom == "gemm_tc":
-            peak, bound, note = None, "tensor", "split-precision bf16 tensor flops"
-            try:
-                mp = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-                peak = float(mp.get("bf16_tflops_sustained") or mp.get("bf16_tflops"))
-                note += " (of measured sustained bf16)"
-            except (OSError, ValueError, TypeError):
-                peak = 1700.0
-                note += " (of fallback)"
+            peak, bound = bf16_peak, "tensor"
+            achieved = issued / (d["ms"] / 1e3) / 1e12
+            note = f"bf16 slice products issued on the tensor pipe, {bf16_note}"
         else:
             peak, bound = FP64_PEAK_TFLOPS, "alu"
             note = "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x ~2.06 GHz)"
@@ -310,6 +327,8 @@ def main():
             "dtype": "f64" if prec_name == "fp64" else "bf16-slices+f64",
             "data": "synthetic",
             "config": dict(WORKLOAD, precision=prec_name, concurrent_applications=B,
+                           batching="cbc_apply_batched: lockstep groups of <= 32 same-shape "
+                                    "instances" if B > 1 else "single cbc_apply",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                            l2="flushed between steps (256 MB write, untimed)"),
             "tflops": flops_per_app / B * value / 1e12,
@@ -318,9 +337,13 @@ def main():
                                    "launches_per_step": v["launches"] / args.steps}
                                for k, v in stats.items() if v["launches"]},
             "roofline": roofline,
+            "roofline_tensor": roofline_tc,
             "gpu_launches": int(sum(v["launches"] for v in stats.values())),
             "clocks": clock_info}
 
+    if args.sites > 0:  # a shortened chain: not the headline workload
+        line["config"]["L"] = args.sites
+        line["config"]["workload"] = line["config"]["workload"].replace("L=64", f"L={args.sites}")
     # parity of this run's output with the oracle, and the oracle's own time
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import metrics

@@ -951,10 +951,13 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   const int wpb = 8;
   bisect32_kernel<<<dim3((m + wpb - 1) / wpb, nb), 32 * wpb, 2 * sizeof(float) * m, s>>>(
       d, e, m, lam32, wb);
-  // 3. eigenvectors of T for the candidates, FP64
-  // one candidate per CTA: the LU and the solves are long dependent FP64 chains, best
-  // run with a whole SM (and its FP64 unit) per chain
-  const int tpb = 1;
+  // 3. eigenvectors of T for the candidates, FP64.  The LU and the solves are long
+  // dependent FP64 chains: alone, one candidate per CTA runs fastest (a whole SM and its
+  // FP64 unit per chain); in a batch with many candidates per SM, up to 16 candidates
+  // share a warp (one per lane), which issues 16x fewer FP64 warp instructions.
+  int tpb = 1;
+  if ((size_t)nb * kmax >= 4 * (size_t)num_sms)
+    tpb = (int)std::max<size_t>(1, std::min<size_t>(16, (200 * 1024 - 64) / ((size_t)m * 41)));
   size_t shi = (size_t)tpb * m * 41 + 64;
   err = allow_max_smem((const void*)invit_kernel);
   if (err != cudaSuccess) return err;

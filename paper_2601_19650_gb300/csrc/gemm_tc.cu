@@ -165,9 +165,11 @@ struct TcArgs {
   char* C;               // FP64 output (double or zdbl) through the view
   View vc;               // vc.bs: elements between the outputs of consecutive problems
   int* status;
-  int splits;            // K splits per problem; blockIdx.z = problem * splits + split
+  int splits;            // K splits per problem
   int Mp, N2p;           // packed rows of one problem in the A and B planes
   int ebsB;              // entries of expB per problem
+  int tiles_m, tiles_n;  // output tiles of one (problem, split)
+  int total_tiles;       // tiles_m * tiles_n * splits * problems
 };
 
 // ldexp((double)a, e) formed with integer operations: the int64 is rounded to 53 bits
@@ -220,13 +222,25 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM;
-  const int n0 = blockIdx.y * BN;
-  const int prob = blockIdx.z / a.splits;
-  const int a_begin = (blockIdx.z % a.splits) * a.atoms_per_split;
-  const int a_end = min(a.atoms_total, a_begin + a.atoms_per_split);
-  const int n_atoms = max(0, a_end - a_begin);
-  const int n_chunks = (n_atoms + a.atoms_per_chunk - 1) / a.atoms_per_chunk;
+  // Persistent: CTA b takes tiles b, b + gridDim.x, ...  A tile index runs over the
+  // 128-row blocks fastest (neighbouring CTAs share the B tile), then the column
+  // blocks, then (problem, K split).  The smem ring and the two TMEM buffers carry on
+  // across tiles, so one tile's epilogue overlaps the next tile's loads and MMAs.
+  struct Tile {
+    int m0, n0, prob, a_begin, n_atoms, n_chunks;
+  };
+  auto tile_of = [&](int t) {
+    Tile q;
+    const int mt = t % a.tiles_m, r = t / a.tiles_m;
+    const int nt = r % a.tiles_n, z = r / a.tiles_n;
+    q.m0 = mt * BM;
+    q.n0 = nt * BN;
+    q.prob = z / a.splits;
+    q.a_begin = (z % a.splits) * a.atoms_per_split;
+    q.n_atoms = max(0, min(a.atoms_total, q.a_begin + a.atoms_per_split) - q.a_begin);
+    q.n_chunks = (q.n_atoms + a.atoms_per_chunk - 1) / a.atoms_per_chunk;
+    return q;
+  };
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < NSTAGE; ++i) {
@@ -256,17 +270,25 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
     if (lane == 0) {
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmA) : "memory");
       asm volatile("prefetch.tensormap [%0];" ::"l"(&tmB) : "memory");
-      for (int j = 0; j < n_atoms; ++j) {
-        const int stage = j % NSTAGE, use = j / NSTAGE;
-        if (!mbar_wait(empty + stage, (use & 1) ^ 1, abort_flag, a.status)) break;
-        uint8_t* sA = smem + stage * STAGE_BYTES;
-        uint8_t* sB = sA + S * A_BYTES;
-        mbar_expect_tx(full + stage, STAGE_BYTES);
-        const int k = (a_begin + j) * KA;
+      int jg = 0;  // atoms loaded by this CTA so far (position in the smem ring)
+      bool run = true;
+      for (int t = blockIdx.x; t < a.total_tiles && run; t += gridDim.x) {
+        const Tile q = tile_of(t);
+        for (int j = 0; j < q.n_atoms; ++j, ++jg) {
+          const int stage = jg % NSTAGE, use = jg / NSTAGE;
+          if (!mbar_wait(empty + stage, (use & 1) ^ 1, abort_flag, a.status)) {
+            run = false;
+            break;
+          }
+          uint8_t* sA = smem + stage * STAGE_BYTES;
+          uint8_t* sB = sA + S * A_BYTES;
+          mbar_expect_tx(full + stage, STAGE_BYTES);
+          const int k = (q.a_begin + j) * KA;
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-          tma_load_3d(&tmA, full + stage, sA + s * A_BYTES, k, prob * a.Mp + m0, s);
-          tma_load_3d(&tmB, full + stage, sB + s * B_BYTES, k, prob * a.N2p + n0, s);
+          for (int s = 0; s < S; ++s) {
+            tma_load_3d(&tmA, full + stage, sA + s * A_BYTES, k, q.prob * a.Mp + q.m0, s);
+            tma_load_3d(&tmB, full + stage, sB + s * B_BYTES, k, q.prob * a.N2p + q.n0, s);
+          }
         }
       }
     }
@@ -274,37 +296,49 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      int j = 0;
-      for (int c = 0; c < n_chunks && !*abort_flag; ++c) {
-        const int buf = c & 1, use = c >> 1;
-        if (!mbar_wait(tempty + buf, (use & 1) ^ 1, abort_flag, a.status)) break;
-        tc_fence_after();
-        const int j_end = min(n_atoms, j + a.atoms_per_chunk);
-        bool first = true;
-        for (; j < j_end; ++j) {
-          const int stage = j % NSTAGE, su = j / NSTAGE;
-          if (!mbar_wait(full + stage, su & 1, abort_flag, a.status)) break;
+      int jg = 0, cg = 0;  // atoms consumed, chunks issued (TMEM buffer cg & 1)
+      bool run = true;
+      for (int t = blockIdx.x; t < a.total_tiles && run; t += gridDim.x) {
+        const Tile q = tile_of(t);
+        int j = 0;
+        for (int c = 0; c < q.n_chunks; ++c, ++cg) {
+          const int buf = cg & 1, use = cg >> 1;
+          if (!mbar_wait(tempty + buf, (use & 1) ^ 1, abort_flag, a.status)) {
+            run = false;
+            break;
+          }
           tc_fence_after();
-          const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
-          const uint32_t sB = sA + S * A_BYTES;
+          const int j_end = min(q.n_atoms, j + a.atoms_per_chunk);
+          bool first = true;
+          for (; j < j_end; ++j, ++jg) {
+            const int stage = jg % NSTAGE, su = jg / NSTAGE;
+            if (!mbar_wait(full + stage, su & 1, abort_flag, a.status)) {
+              run = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t sA = smem_u32(smem + stage * STAGE_BYTES);
+            const uint32_t sB = sA + S * A_BYTES;
 #pragma unroll
-          for (int g = 0; g < S; ++g) {
-            const uint32_t d = tmem_base + (uint32_t)((buf * S + g) * BN);
+            for (int g = 0; g < S; ++g) {
+              const uint32_t d = tmem_base + (uint32_t)((buf * S + g) * BN);
 #pragma unroll
-            for (int s = 0; s <= g; ++s) {
-              const int t = g - s;
+              for (int s = 0; s <= g; ++s) {
+                const int tt = g - s;
 #pragma unroll
-              for (int kk = 0; kk < KA / 16; ++kk) {
-                uint64_t ad = sdesc_sw128(sA + s * A_BYTES + kk * 32);
-                uint64_t bd = sdesc_sw128(sB + t * B_BYTES + kk * 32);
-                umma_bf16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
+                for (int kk = 0; kk < KA / 16; ++kk) {
+                  uint64_t ad = sdesc_sw128(sA + s * A_BYTES + kk * 32);
+                  uint64_t bd = sdesc_sw128(sB + tt * B_BYTES + kk * 32);
+                  umma_bf16(d, ad, bd, idesc, (first && s == 0 && kk == 0) ? 0u : 1u);
+                }
               }
             }
+            first = false;
+            umma_commit(empty + stage);  // smem stage free once these MMAs complete
           }
-          first = false;
-          umma_commit(empty + stage);  // smem stage free once these MMAs complete
+          if (!run) break;
+          umma_commit(tfull + buf);      // chunk sums ready in TMEM
         }
-        umma_commit(tfull + buf);      // chunk sums ready in TMEM
       }
     }
   } else {
@@ -313,57 +347,61 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
     // 0-31, warps 6-9 columns 32-63 (BN = 64)
     const int ew = warp - 2;
     const int quarter = warp & 3;
-    const int cg = ew >> 2;
-    const int row = m0 + quarter * 32 + lane;
-    long long acc[32];
+    const int colg = ew >> 2;
+    int cg = 0;  // chunks drained (TMEM buffer cg & 1)
+    bool run = true;
+    for (int t = blockIdx.x; t < a.total_tiles && run; t += gridDim.x) {
+      const Tile q = tile_of(t);
+      const int row = q.m0 + quarter * 32 + lane;
+      long long acc[32];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0;
-    bool ok = true;
-    for (int c = 0; c < n_chunks; ++c) {
-      const int buf = c & 1, use = c >> 1;
-      if (!mbar_wait(tfull + buf, use & 1, abort_flag, a.status)) {
-        ok = false;
-        break;
+      for (int i = 0; i < 32; ++i) acc[i] = 0;
+      for (int c = 0; c < q.n_chunks; ++c, ++cg) {
+        const int buf = cg & 1, use = cg >> 1;
+        if (!mbar_wait(tfull + buf, use & 1, abort_flag, a.status)) {
+          run = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int g = 0; g < S; ++g) {
+          const int shift = 8 * (S - 1 - g);
+          uint32_t r[32];
+          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                        (uint32_t)((buf * S + g) * BN + colg * 32),
+                    r);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            long long qv = (long long)__float2int_rn(__uint_as_float(r[i]));
+            acc[i] += qv << shift;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty + buf);
       }
-      tc_fence_after();
-#pragma unroll
-      for (int g = 0; g < S; ++g) {
-        const int shift = 8 * (S - 1 - g);
-        uint32_t r[32];
-        tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
-                      (uint32_t)((buf * S + g) * BN + cg * 32),
-                  r);
+      if (run && q.n_chunks > 0 && row < a.M) {
+        const int ea = a.expA[q.prob * a.Mp + row];
+        const int* expB = a.expB + (int64_t)q.prob * a.ebsB;
+        char* Cp = a.C + (int64_t)q.prob * a.vc.bs * (a.cplx ? 16 : 8);
+        const int bias = -14 - 8 * (S - 1);
+        const int64_t ro = a.vc.roff(row);
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          long long q = (long long)__float2int_rn(__uint_as_float(r[i]));
-          acc[i] += q << shift;
-        }
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty + buf);
-    }
-    if (ok && n_chunks > 0 && row < a.M) {
-      const int ea = a.expA[prob * a.Mp + row];
-      const int* expB = a.expB + (int64_t)prob * a.ebsB;
-      char* Cp = a.C + (int64_t)prob * a.vc.bs * (a.cplx ? 16 : 8);
-      const int bias = -14 - 8 * (S - 1);
-      const int64_t ro = a.vc.roff(row);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) {
-        const int col = n0 + cg * 32 + i;
-        if (col < a.N2) {
-          const int ncol = a.cplx ? (col >> 1) : col;
-          const double v = i64_ldexp(acc[i], ea + expB[ncol] + bias);
-          double* dst;
-          if (a.cplx)
-            dst = reinterpret_cast<double*>(Cp + 16 * (ro + a.vc.coff(ncol))) + (col & 1);
-          else
-            dst = reinterpret_cast<double*>(Cp + 8 * (ro + a.vc.coff(ncol)));
-          if (a.atomic)
-            atomicAdd(dst, v);
-          else
-            *dst = v;
+          const int col = q.n0 + colg * 32 + i;
+          if (col < a.N2) {
+            const int ncol = a.cplx ? (col >> 1) : col;
+            const double v = i64_ldexp(acc[i], ea + expB[ncol] + bias);
+            double* dst;
+            if (a.cplx)
+              dst = reinterpret_cast<double*>(Cp + 16 * (ro + a.vc.coff(ncol))) + (col & 1);
+            else
+              dst = reinterpret_cast<double*>(Cp + 8 * (ro + a.vc.coff(ncol)));
+            if (a.atomic)
+              atomicAdd(dst, v);
+            else
+              *dst = v;
+          }
         }
       }
     }
@@ -720,7 +758,10 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
     cudaError_t e = gemm_f64<T>(M, N, 0, nb, A, va, false, B, vb, false, C, vc, s);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid(g.Mp / BM, g.N2p / g.BN, splits * nb);
+  args.tiles_m = g.Mp / BM;
+  args.tiles_n = g.N2p / g.BN;
+  args.total_tiles = args.tiles_m * args.tiles_n * splits * nb;
+  dim3 grid(std::min(args.total_tiles, g_sms));
   note_launches(CBC_K_GEMM_TC, 1);
   note_flops(CBC_K_TC_ISSUED, 2.0 * g.Mp * g.N2p * g.K2p * (S * (S + 1) / 2) * nb);
   switch (S) {
