@@ -2,9 +2,12 @@
 """Benchmark of the CBC application (arXiv 2601.19650, Sec. III A) on one GB300.
 
 Workload: MPO applied to an MPS and compressed by CBC, L=64 sites, d=2, MPS bond 128,
-MPO bond 16, cap 128, complex64 Gaussian entries with unit Frobenius norm per tensor,
-seed 0 (per rank: seed = rank).  A step is one full application (forward sweep with
-compressions, backward sweep with CholeskyQR2) on inputs resident in HBM.
+MPO bond 16, cap 128, complex64 Gaussian entries with unit Frobenius norm per tensor.
+A step applies B independent instances (default 32; rank r uses seeds r*B .. r*B+B-1)
+through cbc_apply_batched, which runs same-shape instances as one lockstep group; every
+application is a full forward sweep with compressions and backward sweep with
+CholeskyQR2, on inputs resident in HBM.  Several GPUs run independent replicas (no
+collective on the data path); the step time is the maximum over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
     python bench.py --impl reference ...   # the FP64 CPU oracle, timed on the host
@@ -30,6 +33,34 @@ WORKLOAD = dict(workload="MPO on MPS, L=64, d=2, chi=128, D=16, max_bond=128, co
                          "Gaussian entries (unit Frobenius norm per tensor)",
                 L=64, d=2, chi=128, D=16, max_bond=128, input_dtype="complex64")
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure in MEASURED_PEAKS)
+# DRAM bytes per launch of a class's dominant kernel, read from an ncu capture of this
+# workload; each entry names the summary under profiles/ it comes from.  A class whose
+# kernel changed after its capture has no entry (traffic null).
+PROFILED_TRAFFIC = {}
+KERNEL_OF_CLASS = {"tridiag": "tridiag_smem_kernel", "eig": "bisect32/invit/rank/backtransform",
+                   "gemm_tc": "gemm_tc_kernel (+ operand slicing)", "cholqr": "chol_kernel + trsm",
+                   "gemm_f64": "gemm_f64_kernel"}
+
+
+def instance_seeds(rank: int, B: int):
+    """Seeds of the B instances a rank applies: disjoint across ranks."""
+    return [rank * B + j for j in range(B)]
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the job's step time); x itself on one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, B: int, steps: int, t_max_ms: float) -> float:
+    """Applications per second of the whole job: every rank's instances over the
+    slowest rank's time."""
+    return world * B * steps / (t_max_ms / 1e3)
 
 
 def env_int(name, default):
@@ -192,7 +223,7 @@ def main():
 
     # precision of the headline number: mixed when built, else fp64
     prec_name = args.precision
-    probs = [make_workload(seed=rank * B + j, sites=args.sites) for j in range(B)]
+    probs = [make_workload(seed=sd, sites=args.sites) for sd in instance_seeds(rank, B)]
     prob = probs[0]
     st, op = prob.state, prob.op
     hs_list, ho_list = [], []
@@ -274,12 +305,8 @@ def main():
     stats = _cbc.cbc_stats_read()
     _cbc.cbc_stats_enable(False)
 
-    t_max = total_ms
-    if dist:
-        tt = torch.tensor([total_ms], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * B * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, dist, f"cuda:{local}")
+    value = whole_job_value(world, B, args.steps, t_max)
     ms_per_step = t_max / args.steps
 
     # per-kernel-class roofline of the dominant class
@@ -315,9 +342,13 @@ def main():
         else:
             peak, bound = FP64_PEAK_TFLOPS, "alu"
             note = "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x ~2.06 GHz)"
-        roofline = {"bound": bound, "kernel_class": dom, "achieved": achieved, "peak": peak,
+        prof = PROFILED_TRAFFIC.get(dom, {})
+        roofline = {"bound": bound, "kernel_class": dom, "kernel": KERNEL_OF_CLASS.get(dom, dom),
+                    "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
-                    "traffic": None, "note": note,
+                    "traffic": prof.get("bytes_per_launch"),
+                    "traffic_source": prof.get("source") if prof.get("bytes_per_launch") else None,
+                    "note": note,
                     "launch_groups": d["groups"], "ms_total": d["ms"],
                     "share_of_step": d["ms"] / total_ms}
 

@@ -180,9 +180,14 @@ int cbc_gemm(int precision, int slices, int dtype, int M, int N, int K, const vo
 enum cbc_kclass {
   CBC_K_GEMM_F64 = 0, /* FP64 SIMT contractions and Gram products                     */
   CBC_K_GEMM_TC = 1,  /* tcgen05 split-precision contractions and Gram products        */
-  CBC_K_EIG = 2,      /* Hermitian eigensolver of the truncation                      */
+  CBC_K_EIG = 2,      /* truncation eigensolver after the tridiagonal reduction        */
   CBC_K_CHOLQR = 3,   /* Cholesky and triangular solves of CholeskyQR2                */
   CBC_K_AUX = 4,      /* normalisation, identity, operand slicing, conversions        */
+  CBC_K_TC_ISSUED = 5, /* flops only: bf16 products issued on the tensor pipe by the
+                          split-precision GEMMs (S(S+1)/2 slice products on the padded,
+                          real-embedded shape); no launches or time of its own          */
+  CBC_K_TRIDIAG = 6,   /* Householder reduction to tridiagonal form (first stage of the
+                          truncation eigensolver; CBC_K_EIG holds the other stages)     */
   CBC_K_COUNT = 8
 };
 typedef struct cbc_stats {

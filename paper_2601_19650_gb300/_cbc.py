@@ -44,7 +44,8 @@ class cbc_stats(ctypes.Structure):
                 ("ms", ctypes.c_double * 8), ("flops", ctypes.c_double * 8)]
 
 
-KCLASS = {0: "gemm_f64", 1: "gemm_tc", 2: "eig", 3: "cholqr", 4: "aux"}
+KCLASS = {0: "gemm_f64", 1: "gemm_tc", 2: "eig", 3: "cholqr", 4: "aux", 5: "tc_issued",
+          6: "tridiag"}
 
 _lib = None
 

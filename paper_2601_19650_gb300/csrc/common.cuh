@@ -162,6 +162,12 @@ __device__ __forceinline__ int tri_row(int64_t t) {
 }
 
 // warp / block reductions -----------------------------------------------------------
+__device__ __forceinline__ double shfl_xor(double v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ zdbl shfl_xor(zdbl v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.re, o), __shfl_xor_sync(0xffffffffu, v.im, o)};
+}
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -213,9 +213,9 @@ __global__ void __launch_bounds__(TPB) tridiag_kernel(TriArgs<T> a) {
 // from the owner of each row.  Both travel as plain data: the receiving buffers are
 // filled with the all-ones bit pattern before the launch, each entry is written once
 // with a relaxed store, and readers poll every entry until it differs from that
-// pattern, so no fence, counter or atomic sits on the dependency chain.  Every CTA
-// forms v^H p from the gathered p itself, in one fixed order, so all CTAs apply the
-// same rank-2 update.  Every wait is bounded.
+// pattern, so no fence, counter or atomic sits on the dependency chain.  Each CTA also
+// publishes its share of v^H p (its own rows); every CTA adds the P shares in one fixed
+// order, so all CTAs apply the same rank-2 update.  Every wait is bounded.
 template <typename T>
 struct Tri2Args {
   const T* A;
@@ -225,6 +225,7 @@ struct Tri2Args {
   T* tau;
   T* V;    // m x m; row j: [j] = tau_j, [j+1, m) = v_j; sentinel-filled before the launch
   T* Pg;   // m x m; row j: [j+1, m) = tau_j A v_j;     sentinel-filled before the launch
+  T* Dg;   // (m-1) x P; [j][q] = CTA q's share of v_j^H p_j; sentinel-filled too
   int* status;
   int P;            // CTAs per matrix; CTA b handles matrix b / P of a batch
   int64_t a_bs;     // elements between consecutive matrices A
@@ -284,6 +285,35 @@ __device__ bool gather_pub(const T* src, T* dst, int lo, int hi, int* status) {
   return __syncthreads_and(ok) != 0;
 }
 
+// Two ranges in one polling pass (one barrier).
+template <typename T>
+__device__ bool gather_pub2(const T* s1, T* d1, int lo1, int hi1, const T* s2, T* d2, int lo2,
+                            int hi2, int* status) {
+  bool ok = true;
+  const int n1 = hi1 - lo1, n = n1 + (hi2 - lo2);
+  for (int q = threadIdx.x; q < n && ok; q += blockDim.x) {
+    const T* src = (q < n1) ? s1 + lo1 + q : s2 + lo2 + (q - n1);
+    T* dst = (q < n1) ? d1 + lo1 + q : d2 + lo2 + (q - n1);
+    T v;
+    if (!ld_pub(src, &v)) {
+      const long long t0 = clock64();
+      while (!ld_pub(src, &v)) {
+        if (*((volatile int*)status) != 0) {
+          ok = false;
+          break;
+        }
+        if (clock64() - t0 > kWaitCycles) {
+          set_status(status, CBC_ERR_TIMEOUT);
+          ok = false;
+          break;
+        }
+      }
+    }
+    *dst = v;
+  }
+  return __syncthreads_and(ok) != 0;
+}
+
 // (sum x, sum y) over the CTA; sh holds at least 66 doubles
 __device__ __forceinline__ double2 block_sum2(double x, double y, double* sh) {
   x = warp_sum(x);
@@ -328,9 +358,11 @@ __device__ void householder_pub(const Tri2Args<T>& a, const T* row, int j, T* vs
     beta = ar;
     scale = O::zero();
   } else {
-    const double nrm = sqrt(ar * ar + ai * ai + xn2);
+    const double n2 = ar * ar + ai * ai + xn2;
+    const double rn = rsqrt64(n2);  // 1 / ||x||
+    const double nrm = n2 * rn;
     beta = (ar >= 0.0) ? -nrm : nrm;
-    const double ib = rcp64(beta);
+    const double ib = (ar >= 0.0) ? -rn : rn;  // 1 / beta
     tau = O::make((beta - ar) * ib, -ai * ib);
     const double zr = ar - beta, zi = ai;
     const double iden = rcp64(zr * zr + zi * zi);
@@ -352,7 +384,60 @@ __device__ void householder_pub(const Tri2Args<T>& a, const T* row, int j, T* vs
   __syncthreads();
 }
 
+// ---- double-float arithmetic (value = h + l, two FP32 numbers, ~2^-46 relative) -----
+// On this part FP32 issues ~64x faster than FP64, so the mixed path keeps the rows of
+// the tridiagonal reduction as double-float pairs and runs its two O(m^2)-per-column
+// loops (p = A v and the rank-2 update) in FP32 with error-free transformations
+// (TwoProduct by fma, TwoSum; Dekker and Knuth).  The rounded intrinsics keep the
+// compiler from contracting them.
+struct df1 {
+  float h, l;
+};
+struct dfz {
+  df1 re, im;
+};
 template <typename T>
+struct dfof;
+template <>
+struct dfof<double> {
+  using type = df1;
+};
+template <>
+struct dfof<zdbl> {
+  using type = dfz;
+};
+__device__ __forceinline__ df1 df_make(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ df1 df_neg(df1 a) { return {-a.h, -a.l}; }
+// c + a b
+__device__ __forceinline__ df1 df_fma(df1 a, df1 b, df1 c) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float s = __fadd_rn(c.h, p);
+  const float bb = __fsub_rn(s, c.h);
+  float t = __fadd_rn(__fsub_rn(c.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  t = __fadd_rn(t, __fadd_rn(c.l, e));
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df1 to_df(double x) { return df_make(x); }
+__device__ __forceinline__ dfz to_df(zdbl x) { return {df_make(x.re), df_make(x.im)}; }
+__device__ __forceinline__ double from_df(df1 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ zdbl from_df(dfz a) { return {from_df(a.re), from_df(a.im)}; }
+__device__ __forceinline__ df1 dff(df1 a, df1 b, df1 c) { return df_fma(a, b, c); }
+__device__ __forceinline__ dfz dff(dfz a, dfz b, dfz c) {  // c + a b, complex
+  return {df_fma(df_neg(a.im), b.im, df_fma(a.re, b.re, c.re)),
+          df_fma(a.im, b.re, df_fma(a.re, b.im, c.im))};
+}
+__device__ __forceinline__ df1 dfconj(df1 a) { return a; }
+__device__ __forceinline__ dfz dfconj(dfz a) { return {a.re, df_neg(a.im)}; }
+
+// DF: rows as double-float pairs (mixed path); else FP64 throughout.
+template <typename T, bool DF>
 __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
   using O = ops<T>;
   extern __shared__ unsigned char sm_raw[];
@@ -368,6 +453,7 @@ __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
     a.tau = byte_shift(a0.tau, off);
     a.V = byte_shift(a0.V, off);
     a.Pg = byte_shift(a0.Pg, off);
+    a.Dg = byte_shift(a0.Dg, off);
   }
   const int m = a.m;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -375,80 +461,179 @@ __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
   T* rows = reinterpret_cast<T*>(sm_raw);
   T* vbuf = rows + (size_t)nr * m;  // v of two consecutive columns
   T* psm = vbuf + 2 * (size_t)m;    // p, then w
+  T* pown = psm + m;                // p of the own rows (by local row index)
+  T* dsm = pown + m;                // the P shares of v^H p
+  // DF only: v and w as double-float, and the owner's row j+1 back in FP64
+  using D = typename dfof<T>::type;
+  D* rdf = reinterpret_cast<D*>(rows);
+  D* vdf = reinterpret_cast<D*>(dsm + P);
+  D* wdf = vdf + m;
+  T* hrow = reinterpret_cast<T*>(wdf + m);
   for (int t = 0; t < nr; ++t)
-    for (int c = threadIdx.x; c < m; c += blockDim.x)
-      rows[(size_t)t * m + c] = a.A[(int64_t)(cta + P * t) * m + c];
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+      const T x = a.A[(int64_t)(cta + P * t) * m + c];
+      if constexpr (DF)
+        rdf[(size_t)t * m + c] = to_df(x);
+      else
+        rows[(size_t)t * m + c] = x;
+    }
   __syncthreads();
+  // own row t as FP64 (DF: converted into hrow from column `from` on)
+  auto row64 = [&](int t, int from) -> const T* {
+    if constexpr (DF) {
+      for (int c = from + threadIdx.x; c < m; c += blockDim.x) hrow[c] = from_df(rdf[(size_t)t * m + c]);
+      __syncthreads();
+      return hrow;
+    } else {
+      return rows + (size_t)t * m;
+    }
+  };
   if (m == 1) {
-    if (cta == 0 && threadIdx.x == 0) a.d[0] = O::real(rows[0]);
+    if (cta == 0) {
+      const T* r0 = row64(0, 0);
+      if (threadIdx.x == 0) a.d[0] = O::real(r0[0]);
+    }
     return;
   }
-  if (cta == 0) householder_pub(a, rows, 0, vbuf, sh);
+  if (cta == 0) householder_pub(a, row64(0, 0), 0, vbuf, sh);
   for (int j = 0; j < m - 1; ++j) {
     T* vsm = vbuf + (size_t)(j & 1) * m;
     // v_j and tau_j (the owner of row j computed them into vsm itself)
     if (j % P != cta && !gather_pub(a.V + (int64_t)j * m, vsm, j, m, a.status)) return;
     const T tau = vsm[j];
-    // phase B: p_r = tau sum_{c>j} A[r][c] v_c for own rows r > j, S warps per row
+    if constexpr (DF) {
+      for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) vdf[c] = to_df(vsm[c]);
+      __syncthreads();
+    }
+    // phase B: p_r = tau sum_{c>j} A[r][c] v_c for own rows r > j
     const int t0 = (j + 1 - cta + P - 1) / P;  // first own row beyond j
     const int live = nr - t0;
     T* pg = a.Pg + (int64_t)j * m;
     if (live > 0) {
       int S = 1;
       while (S * 2 * live <= nw) S *= 2;
-      for (int item = warp; item < live * S; item += nw) {
-        const int t = t0 + item / S, sg = item % S;
-        const T* row = rows + (size_t)t * m;
-        T acc = O::zero();
-        for (int c = j + 1 + sg * 32 + lane; c < m; c += S * 32) acc = O::fma(row[c], vsm[c], acc);
-        acc = warp_sum(acc);
-        if (S == 1) {
-          if (lane == 0) st_pub(pg + cta + P * t, tau * acc);
-        } else if (lane == 0) {
-          part[item] = acc;
+      if (S == 1) {
+        // rows ta and ta + nw per warp pass; a reduce-scatter butterfly leaves row ta's
+        // sum in lanes 0-15 and row tb's in lanes 16-31 (5 add levels for both rows)
+        for (int item = warp; item < live; item += 2 * nw) {
+          const int ta = t0 + item;
+          const bool two = item + nw < live;
+          const int tb = two ? ta + nw : ta;
+          T xa = O::zero(), xb = O::zero();
+          if constexpr (DF) {
+            const D* ra = rdf + (size_t)ta * m;
+            const D* rb = rdf + (size_t)tb * m;
+            D ya = to_df(O::zero()), yb = ya;
+            for (int c = j + 1 + lane; c < m; c += 32) {
+              const D vc = vdf[c];
+              ya = dff(ra[c], vc, ya);
+              if (two) yb = dff(rb[c], vc, yb);
+            }
+            xa = from_df(ya);
+            xb = from_df(yb);
+          } else {
+            const T* ra = rows + (size_t)ta * m;
+            const T* rb = rows + (size_t)tb * m;
+            for (int c = j + 1 + lane; c < m; c += 32) {
+              const T vc = vsm[c];
+              xa = O::fma(ra[c], vc, xa);
+              if (two) xb = O::fma(rb[c], vc, xb);
+            }
+          }
+          if (two) {
+            T keep = (lane < 16) ? xa : xb;
+            keep = keep + shfl_xor((lane < 16) ? xb : xa, 16);
+#pragma unroll
+            for (int o = 8; o > 0; o >>= 1) keep = keep + shfl_xor(keep, o);
+            if ((lane & 15) == 0) {
+              const int t = (lane == 0) ? ta : tb;
+              const T pr = tau * keep;
+              pown[t] = pr;
+              st_pub(pg + cta + P * t, pr);
+            }
+          } else {
+            xa = warp_sum(xa);
+            if (lane == 0) {
+              const T pr = tau * xa;
+              pown[ta] = pr;
+              st_pub(pg + cta + P * ta, pr);
+            }
+          }
         }
-      }
-      if (S > 1) {
+      } else {
+        for (int item = warp; item < live * S; item += nw) {
+          const int t = t0 + item / S, sg = item % S;
+          T acc = O::zero();
+          if constexpr (DF) {
+            const D* row = rdf + (size_t)t * m;
+            D y = to_df(O::zero());
+            for (int c = j + 1 + sg * 32 + lane; c < m; c += S * 32) y = dff(row[c], vdf[c], y);
+            acc = from_df(y);
+          } else {
+            const T* row = rows + (size_t)t * m;
+            for (int c = j + 1 + sg * 32 + lane; c < m; c += S * 32) acc = O::fma(row[c], vsm[c], acc);
+          }
+          acc = warp_sum(acc);
+          if (lane == 0) part[item] = acc;
+        }
         __syncthreads();
         if (threadIdx.x < live) {
-          T s = part[threadIdx.x * S];
-          for (int q = 1; q < S; ++q) s = s + part[threadIdx.x * S + q];
-          st_pub(pg + cta + P * (t0 + threadIdx.x), tau * s);
+          T sp = part[threadIdx.x * S];
+          for (int q = 1; q < S; ++q) sp = sp + part[threadIdx.x * S + q];
+          const T pr = tau * sp;
+          pown[t0 + threadIdx.x] = pr;
+          st_pub(pg + cta + P * (t0 + threadIdx.x), pr);
         }
       }
     }
-    // all of p, then w = p - (conj(tau)/2)(v^H p) v in place
-    if (!gather_pub(pg, psm, j + 1, m, a.status)) return;
-    double dre = 0.0, dim = 0.0;
-    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) {
-      const T vd = O::conj(vsm[c]) * psm[c];
-      dre += O::real(vd);
-      dim += O::imag(vd);
+    __syncthreads();
+    // this CTA's share of v^H p, published next to p
+    if (warp == 0) {
+      T dv = O::zero();
+      for (int t = t0 + lane; t < nr; t += 32) dv = O::fma(O::conj(vsm[cta + P * t]), pown[t], dv);
+      dv = warp_sum(dv);
+      if (lane == 0) st_pub(a.Dg + (int64_t)j * P + cta, dv);
     }
-    const double2 dd = block_sum2(dre, dim, sh);
-    const T coef = O::scale(-0.5, O::conj(tau) * O::make(dd.x, dd.y));
-    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) psm[c] = O::fma(coef, vsm[c], psm[c]);
+    // all of p and all shares; v^H p summed in one fixed order (the same in every CTA);
+    // then w = p - (conj(tau)/2)(v^H p) v in place
+    if (!gather_pub2(pg, psm, j + 1, m, a.Dg + (int64_t)j * P, dsm, 0, P, a.status)) return;
+    T dot = O::zero();
+    for (int q = lane; q < P; q += 32) dot = dot + dsm[q];
+    dot = warp_sum(dot);
+    const T coef = O::scale(-0.5, O::conj(tau) * dot);
+    for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) {
+      psm[c] = O::fma(coef, vsm[c], psm[c]);
+      if constexpr (DF) wdf[c] = to_df(psm[c]);
+    }
     __syncthreads();
     // phase C: own rows r > j: A[r][c] -= v_r conj(w_c) + w_r conj(v_c), c > j
     auto update_row = [&](int t, int c0, int cstep) {
       const int r = cta + P * t;
-      T* row = rows + (size_t)t * m;
-      const T vr = vsm[r], wr = psm[r];
-      for (int c = j + 1 + c0; c < m; c += cstep)
-        row[c] = row[c] - O::fma(vr, O::conj(psm[c]), wr * O::conj(vsm[c]));
+      const T nvr = O::scale(-1.0, vsm[r]), nwr = O::scale(-1.0, psm[r]);
+      if constexpr (DF) {
+        D* row = rdf + (size_t)t * m;
+        const D dvr = to_df(nvr), dwr = to_df(nwr);
+        for (int c = j + 1 + c0; c < m; c += cstep)
+          row[c] = dff(dwr, dfconj(vdf[c]), dff(dvr, dfconj(wdf[c]), row[c]));
+      } else {
+        T* row = rows + (size_t)t * m;
+        for (int c = j + 1 + c0; c < m; c += cstep)
+          row[c] = O::fma(nwr, O::conj(vsm[c]), O::fma(nvr, O::conj(psm[c]), row[c]));
+      }
     };
     int tstart = t0;
     if (j + 1 < m - 1 && (j + 1) % P == cta) {
       // the next column's owner: update that row with the whole CTA, publish v_{j+1}
       update_row(t0, threadIdx.x, blockDim.x);
       __syncthreads();
-      householder_pub(a, rows + (size_t)t0 * m, j + 1, vbuf + (size_t)((j + 1) & 1) * m, sh);
+      householder_pub(a, row64(t0, j + 1), j + 1, vbuf + (size_t)((j + 1) & 1) * m, sh);
       tstart = t0 + 1;
     }
     for (int t = tstart + warp; t < nr; t += nw) update_row(t, lane, 32);
     if (j + 1 == m - 1 && (m - 1) % P == cta) {
       __syncthreads();
-      if (threadIdx.x == 0) a.d[m - 1] = O::real(rows[(size_t)((m - 1 - cta) / P) * m + (m - 1)]);
+      const T* rl = row64((m - 1 - cta) / P, m - 1);
+      if (threadIdx.x == 0) a.d[m - 1] = O::real(rl[m - 1]);
     }
     __syncthreads();
   }
@@ -857,13 +1042,14 @@ size_t eig_workspace_bytes(int m, int kmax, bool cplx) {
   b += align256(sizeof(GridBarrier));                // barrier
   b += align256(sizeof(double) * (size_t)m * kmax);  // X
   b += align256(ts * (size_t)m * m);                 // p of every column (exchange)
+  b += align256(ts * (size_t)m * m);                 // shares of v^H p (exchange)
   return b;
 }
 
 template <typename T>
 cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double floor_rel,
                      double* lam, T* U, int* k_dev, void* work, int* status, int num_sms,
-                     cudaStream_t s, int nb, bool prefer_cluster) {
+                     cudaStream_t s, int nb, bool prefer_cluster, bool df) {
   char* w = static_cast<char*>(work);
   auto take = [&](size_t bytes) {
     char* p = w;
@@ -884,6 +1070,7 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   GridBarrier* bar = (GridBarrier*)take(sizeof(GridBarrier));
   double* X = (double*)take(sizeof(double) * (size_t)m * kmax);
   T* Pg = (T*)take(ts * (size_t)m * m);
+  T* Dg = (T*)take(ts * (size_t)m * m);
 
   cudaError_t err = cudaSuccess;
   for (int b = 0; b < nb && err == cudaSuccess; ++b) {
@@ -893,7 +1080,11 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
     if (err == cudaSuccess && m == 1) err = cudaMemsetAsync(byte_shift(e, off), 0, sizeof(double), s);
   }
   if (err != cudaSuccess) return err;
-  note_launches(CBC_K_EIG, 5);
+  // algorithmic FP64 flops: Householder tridiagonalisation (16/3) m^3 complex,
+  // (4/3) m^3 real; back transformation of kmax vectors 8 m^2 kmax complex, 2 m^2 kmax real
+  const double cm = ops<T>::cplx ? 4.0 : 1.0;
+  const double fl_tri = cm * (4.0 / 3.0) * m * (double)m * m * nb;
+  const double fl_rest = cm * 2.0 * m * (double)m * kmax * nb;
   // 1. tridiagonalisation.  Rows in shared memory when they fit: one thread-block
   // cluster of up to 16 CTAs per matrix for a batch or when `prefer_cluster`
   // (co-scheduled and, unlike cooperative launches, concurrent with other streams'
@@ -902,14 +1093,21 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   // count (1..16 selects a cluster).
   int Pw = 0;
   if (const char* env = getenv("CBC_TRIDIAG_CTAS")) Pw = std::max(0, std::min(num_sms, atoi(env)));
-  auto shm_for = [&](int P) { return ((size_t)((m + P - 1) / P) + 3) * m * ts; };
+  auto shm_for = [&](int P) {
+    return (((size_t)((m + P - 1) / P) + (df ? 7 : 4)) * m + P) * ts;
+  };
+  // double-float rows pay off when the batch makes the reduction throughput bound; a
+  // lone reduction is latency bound and runs faster in FP64
+  df = df && nb > 1;
+  const void* ksm = df ? (const void*)tridiag_smem_kernel<T, true>
+                       : (const void*)tridiag_smem_kernel<T, false>;
   const size_t shm_cap = 160 * 1024;
   int P = Pw > 0 ? Pw : std::max(1, std::min(16, m / 2));
   bool cluster = false;
   if ((Pw > 0 || prefer_cluster || nb > 1) && P <= 16 && shm_for(P) <= shm_cap) {
-    err = allow_max_smem((const void*)tridiag_smem_kernel<T>);
+    err = allow_max_smem(ksm);
     if (err != cudaSuccess) return err;
-    cluster = cluster_ctas((const void*)tridiag_smem_kernel<T>, P, TPB, shm_for(P)) == P;
+    cluster = cluster_ctas(ksm, P, TPB, shm_for(P)) == P;
   }
   if (!cluster && Pw <= 0) P = std::max(1, std::min(num_sms, m / 4));
   const bool in_smem = cluster || shm_for(P) <= shm_cap;
@@ -918,23 +1116,26 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
     for (int b = 0; b < nb && err == cudaSuccess; ++b) {
       err = cudaMemsetAsync(byte_shift(V, b * wb), 0xff, ts * (size_t)m * m, s);
       if (err == cudaSuccess) err = cudaMemsetAsync(byte_shift(Pg, b * wb), 0xff, ts * (size_t)m * m, s);
+      if (err == cudaSuccess) err = cudaMemsetAsync(byte_shift(Dg, b * wb), 0xff, ts * (size_t)m * m, s);
     }
-    if (err == cudaSuccess) err = allow_max_smem((const void*)tridiag_smem_kernel<T>);
+    if (err == cudaSuccess) err = allow_max_smem(ksm);
     if (err != cudaSuccess) return err;
   }
+  {
+  KTimer tt(CBC_K_TRIDIAG, s, cluster ? 1 : nb, fl_tri);
   if (cluster) {
-    Tri2Args<T> ta{A, m, d, e, tau, V, Pg, status, P, (int64_t)m * m, wb};
+    Tri2Args<T> ta{A, m, d, e, tau, V, Pg, Dg, status, P, (int64_t)m * m, wb};
     void* args[] = {&ta};
-    err = launch_cluster((const void*)tridiag_smem_kernel<T>, P, nb * P, TPB, shm_for(P), args, s);
+    err = launch_cluster(ksm, P, nb * P, TPB, shm_for(P), args, s);
   } else {
     for (int b = 0; b < nb && err == cudaSuccess; ++b) {
       const size_t off = (size_t)b * wb;
       T* Ab = A + (int64_t)b * m * m;
       if (in_smem) {
         Tri2Args<T> ta{Ab, m, byte_shift(d, off), byte_shift(e, off), byte_shift(tau, off),
-                       byte_shift(V, off), byte_shift(Pg, off), status, P, 0, 0};
+                       byte_shift(V, off), byte_shift(Pg, off), byte_shift(Dg, off), status, P, 0, 0};
         void* args[] = {&ta};
-        err = cudaLaunchCooperativeKernel((const void*)tridiag_smem_kernel<T>, dim3(P), dim3(TPB),
+        err = cudaLaunchCooperativeKernel(ksm, dim3(P), dim3(TPB),
                                           args, shm_for(P), s);
       } else {
         TriArgs<T> ta{Ab, m, byte_shift(d, off), byte_shift(e, off), byte_shift(tau, off),
@@ -946,7 +1147,9 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
       }
     }
   }
+  }
   if (err != cudaSuccess) return err;
+  KTimer te(CBC_K_EIG, s, 4, fl_rest);
   // 2. eigenvalue estimates
   const int wpb = 8;
   bisect32_kernel<<<dim3((m + wpb - 1) / wpb, nb), 32 * wpb, 2 * sizeof(float) * m, s>>>(
@@ -987,8 +1190,9 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
 }
 
 template cudaError_t heev_top<double>(double*, int, int, int64_t, double, double, double*,
-                                      double*, int*, void*, int*, int, cudaStream_t, int, bool);
+                                      double*, int*, void*, int*, int, cudaStream_t, int, bool,
+                                      bool);
 template cudaError_t heev_top<zdbl>(zdbl*, int, int, int64_t, double, double, double*, zdbl*,
-                                    int*, void*, int*, int, cudaStream_t, int, bool);
+                                    int*, void*, int*, int, cudaStream_t, int, bool, bool);
 
 }  // namespace cbc

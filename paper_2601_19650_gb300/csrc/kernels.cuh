@@ -82,7 +82,8 @@ size_t eig_workspace_bytes(int m, int kmax, bool cplx);
 template <typename T>
 cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double floor_rel,
                      double* lam, T* U, int* k_dev, void* work, int* status, int num_sms,
-                     cudaStream_t s, int nb = 1, bool prefer_cluster = false);
+                     cudaStream_t s, int nb = 1, bool prefer_cluster = false,
+                     bool df = false);
 
 // ---- Cholesky QR (FP64) ------------------------------------------------------------
 // Q = C^{-1} S with G = S S^H = C C^H, S: m x n (m <= n), row-major, in place on S.

@@ -136,11 +136,6 @@ cudaError_t tgemm(const Prec& pr, bool fwd, bool gram, int M, int N, int K, cons
   return gemm_f64<T>(M, N, K, pr.nb, A, va, ca, B, vb, cb, C, vc, s);
 }
 
-template <typename T>
-double eig_flops(int m, int k) {
-  return ops<T>::cplx ? (16.0 / 3.0) * m * (double)m * m + 8.0 * m * (double)m * k
-                      : (4.0 / 3.0) * m * (double)m * m + 2.0 * m * (double)m * k;
-}
 
 // read status and k after a compression (k of every instance of a group: they must
 // agree, else kGroupSplit)
@@ -182,11 +177,9 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
     CK(tgemm<T>(pr, true, true, n, n, m, M, View::transposed(n, mbs), true, M,
                 View::rowmajor(n, mbs), false, K, View::rowmajor(n, (int64_t)g * g), s));
   }
-  {
-    KTimer t(CBC_K_EIG, s, 0, eig_flops<T>(g, kmax) * nb);
-    CK(heev_top<T>(K, g, kmax, max_bond, tol, floor_rel, lam, U, sc.k, work, sc.status, num_sms(),
-                   s, nb));
-  }
+  // the mixed path reduces to tridiagonal form in double-float arithmetic
+  CK(heev_top<T>(K, g, kmax, max_bond, tol, floor_rel, lam, U, sc.k, work, sc.status, num_sms(),
+                 s, nb, false, pr.mixed));
   int k = 0;
   int rc = read_k(sc, s, nb, &k);
   if (rc != CBC_OK) return rc;
