@@ -22,6 +22,7 @@
 #include <float.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cstdlib>
 
 #include "kernels.cuh"
@@ -955,14 +956,18 @@ __global__ void __launch_bounds__(128) backtransform_kernel(const T* V, const T*
 // one-vector-per-CTA form.  u needs m * 32 elements of shared memory.
 constexpr int BT_WARPS = 8;
 
-template <typename T>
+// DF (mixed path, batches): u and the staged v as double-float pairs, the two O(m) loops
+// per reflector in FP32 (the partial sums and tau * sum stay FP64).
+template <typename T, bool DF>
 __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
     const T* V, const T* tau, const double* X, int m, int kmax, const int* k_dev, T* U,
     size_t wb) {
   using O = ops<T>;
+  using D = typename dfof<T>::type;
+  using E = typename std::conditional<DF, D, T>::type;  // element type of u and v in smem
   extern __shared__ unsigned char smem_raw[];
-  T* u = reinterpret_cast<T*>(smem_raw);  // [m][32]
-  T* vs = u + (size_t)m * 32;             // [3][m]: v_j in slot j % 3 (staged one ahead)
+  E* u = reinterpret_cast<E*>(smem_raw);  // [m][32]
+  E* vs = u + (size_t)m * 32;             // [3][m]: v_j in slot j % 3 (staged one ahead)
   __shared__ T part[2][BT_WARPS][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // matrix blockIdx.y of a batch
@@ -978,34 +983,57 @@ __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
   const bool live = col < k;
   const int rb = (m + BT_WARPS - 1) / BT_WARPS;
   const int r0 = warp * rb, r1 = min(m, r0 + rb);
-  for (int r = r0; r < r1; ++r) u[(size_t)r * 32 + lane] = O::make(live ? X[(int64_t)r * kmax + col] : 0.0, 0.0);
+  auto to_e = [](const T& x) -> E {
+    if constexpr (DF)
+      return to_df(x);
+    else
+      return x;
+  };
+  for (int r = r0; r < r1; ++r)
+    u[(size_t)r * 32 + lane] = to_e(O::make(live ? X[(int64_t)r * kmax + col] : 0.0, 0.0));
   if (m >= 2) {  // v_{m-2}: rows > m - 2
     const T* vg = V + (int64_t)(m - 2) * m;
-    T* v0 = vs + (size_t)((m - 2) % 3) * m;
-    for (int q = m - 1 + (int)threadIdx.x; q < m; q += blockDim.x) v0[q] = vg[q];
+    E* v0 = vs + (size_t)((m - 2) % 3) * m;
+    for (int q = m - 1 + (int)threadIdx.x; q < m; q += blockDim.x) v0[q] = to_e(vg[q]);
   }
   __syncthreads();
   int par = 0;
   for (int j = m - 2; j >= 0; --j) {
-    const T* v = vs + (size_t)(j % 3) * m;
+    const E* v = vs + (size_t)(j % 3) * m;
     // partial dot over this warp's rows r > j, four independent accumulators
     const int rs = max(r0, j + 1);
-    T a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
-    int r = rs;
-    for (; r + 3 < r1; r += 4) {
-      a0 = O::fma(O::conj(v[r]), u[(size_t)r * 32 + lane], a0);
-      a1 = O::fma(O::conj(v[r + 1]), u[(size_t)(r + 1) * 32 + lane], a1);
-      a2 = O::fma(O::conj(v[r + 2]), u[(size_t)(r + 2) * 32 + lane], a2);
-      a3 = O::fma(O::conj(v[r + 3]), u[(size_t)(r + 3) * 32 + lane], a3);
+    T psum;
+    if constexpr (DF) {
+      const D z = to_df(O::zero());
+      D a0 = z, a1 = z, a2 = z, a3 = z;
+      int r = rs;
+      for (; r + 3 < r1; r += 4) {
+        a0 = dff(dfconj(v[r]), u[(size_t)r * 32 + lane], a0);
+        a1 = dff(dfconj(v[r + 1]), u[(size_t)(r + 1) * 32 + lane], a1);
+        a2 = dff(dfconj(v[r + 2]), u[(size_t)(r + 2) * 32 + lane], a2);
+        a3 = dff(dfconj(v[r + 3]), u[(size_t)(r + 3) * 32 + lane], a3);
+      }
+      for (; r < r1; ++r) a0 = dff(dfconj(v[r]), u[(size_t)r * 32 + lane], a0);
+      psum = (from_df(a0) + from_df(a1)) + (from_df(a2) + from_df(a3));
+    } else {
+      T a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
+      int r = rs;
+      for (; r + 3 < r1; r += 4) {
+        a0 = O::fma(O::conj(v[r]), u[(size_t)r * 32 + lane], a0);
+        a1 = O::fma(O::conj(v[r + 1]), u[(size_t)(r + 1) * 32 + lane], a1);
+        a2 = O::fma(O::conj(v[r + 2]), u[(size_t)(r + 2) * 32 + lane], a2);
+        a3 = O::fma(O::conj(v[r + 3]), u[(size_t)(r + 3) * 32 + lane], a3);
+      }
+      for (; r < r1; ++r) a0 = O::fma(O::conj(v[r]), u[(size_t)r * 32 + lane], a0);
+      psum = (a0 + a1) + (a2 + a3);
     }
-    for (; r < r1; ++r) a0 = O::fma(O::conj(v[r]), u[(size_t)r * 32 + lane], a0);
-    part[par][warp][lane] = (a0 + a1) + (a2 + a3);
+    part[par][warp][lane] = psum;
     // stage the next reflector's vector (rows > j - 1).  Its slot last held v_{j+2},
     // whose readers all finished before the barrier this warp passed last.
     if (j >= 1) {
       const T* vg = V + (int64_t)(j - 1) * m;
-      T* vn = vs + (size_t)((j - 1) % 3) * m;
-      for (int q = j + threadIdx.x; q < m; q += blockDim.x) vn[q] = vg[q];
+      E* vn = vs + (size_t)((j - 1) % 3) * m;
+      for (int q = j + threadIdx.x; q < m; q += blockDim.x) vn[q] = to_e(vg[q]);
     }
     __syncthreads();
     if (rs < r1) {
@@ -1013,13 +1041,23 @@ __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
 #pragma unroll
       for (int w = 1; w < BT_WARPS; ++w) tot = tot + part[par][w][lane];
       const T cf = tau[j] * tot;
-      for (int q = rs; q < r1; ++q) u[(size_t)q * 32 + lane] = u[(size_t)q * 32 + lane] - v[q] * cf;
+      if constexpr (DF) {
+        const D ncf = to_df(O::scale(-1.0, cf));
+        for (int q = rs; q < r1; ++q) u[(size_t)q * 32 + lane] = dff(v[q], ncf, u[(size_t)q * 32 + lane]);
+      } else {
+        for (int q = rs; q < r1; ++q) u[(size_t)q * 32 + lane] = u[(size_t)q * 32 + lane] - v[q] * cf;
+      }
     }
     par ^= 1;
   }
   __syncthreads();
   if (live)
-    for (int r = r0; r < r1; ++r) U[(int64_t)r * kmax + col] = u[(size_t)r * 32 + lane];
+    for (int r = r0; r < r1; ++r) {
+      if constexpr (DF)
+        U[(int64_t)r * kmax + col] = from_df(u[(size_t)r * 32 + lane]);
+      else
+        U[(int64_t)r * kmax + col] = u[(size_t)r * 32 + lane];
+    }
 }
 
 }  // namespace
@@ -1174,10 +1212,16 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   // else one vector per CTA
   const size_t shm32 = ((size_t)m * 32 + 3 * (size_t)m) * ts;
   if (shm32 <= 200 * 1024 && (size_t)nb * ((kmax + 31) / 32) * 2 >= (size_t)num_sms) {
-    err = allow_max_smem((const void*)backtransform32_kernel<T>);
+    const void* kbt = df ? (const void*)backtransform32_kernel<T, true>
+                         : (const void*)backtransform32_kernel<T, false>;
+    err = allow_max_smem(kbt);
     if (err != cudaSuccess) return err;
-    backtransform32_kernel<T><<<dim3((kmax + 31) / 32, nb), 32 * BT_WARPS, shm32, s>>>(
-        V, tau, X, m, kmax, k_dev, U, wb);
+    if (df)
+      backtransform32_kernel<T, true><<<dim3((kmax + 31) / 32, nb), 32 * BT_WARPS, shm32, s>>>(
+          V, tau, X, m, kmax, k_dev, U, wb);
+    else
+      backtransform32_kernel<T, false><<<dim3((kmax + 31) / 32, nb), 32 * BT_WARPS, shm32, s>>>(
+          V, tau, X, m, kmax, k_dev, U, wb);
     return cudaGetLastError();
   }
   size_t shm = (size_t)m * ts;

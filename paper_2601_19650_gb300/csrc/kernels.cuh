@@ -126,6 +126,11 @@ cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const
 // dst (n_elem) = identity rows r < n of an n x n matrix
 template <typename T>
 cudaError_t fill_identity(T* dst, int n, cudaStream_t s, int nb = 1);
+// nb tensors (device array ptrs of nb pointers, n elements each) <-> one buffer with them
+// `stride` elements apart: to_group gathers into buf, else scatters out of it
+template <typename T>
+cudaError_t group_copy(T* const* ptrs, T* buf, int64_t stride, int64_t n, int nb, bool to_group,
+                       cudaStream_t s);
 // widen an input tensor to FP64 storage
 cudaError_t widen_to_f64(const void* src, int src_dtype, void* dst, int64_t n_elem,
                          cudaStream_t s);

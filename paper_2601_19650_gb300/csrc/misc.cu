@@ -67,6 +67,21 @@ __global__ void scaled_adjoint_kernel(const T* V, int ldv, const double* lam, co
   }
 }
 
+// between nb separate tensors (ptrs[b], n elements each) and one buffer holding them
+// `stride` elements apart; instance blockIdx.y
+template <typename T>
+__global__ void group_copy_kernel(T* const* ptrs, T* buf, int64_t stride, int64_t n, int to_group) {
+  T* p = ptrs[blockIdx.y];
+  T* g = buf + (int64_t)blockIdx.y * stride;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (to_group)
+      g[i] = p[i];
+    else
+      p[i] = g[i];
+  }
+}
+
 template <typename T>
 __global__ void identity_kernel(T* dst, int n) {
   dst += (int64_t)blockIdx.y * n * n;
@@ -217,6 +232,15 @@ cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_
 }
 
 template <typename T>
+cudaError_t group_copy(T* const* ptrs, T* buf, int64_t stride, int64_t n, int nb, bool to_group,
+                       cudaStream_t s) {
+  note_launches(CBC_K_AUX, 1);
+  group_copy_kernel<T><<<dim3(std::min(grid_for(n), std::max(1, 2048 / nb)), nb), 256, 0, s>>>(
+      ptrs, buf, stride, n, to_group ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t fill_identity(T* dst, int n, cudaStream_t s, int nb) {
   note_launches(CBC_K_AUX, 1);
   identity_kernel<T><<<dim3(grid_for((int64_t)n * n), nb), 256, 0, s>>>(dst, n);
@@ -272,6 +296,10 @@ template cudaError_t permute<double>(const double*, double*, int, const int64_t*
                                      cudaStream_t);
 template cudaError_t permute<zdbl>(const zdbl*, zdbl*, int, const int64_t*, const int*,
                                    cudaStream_t);
+template cudaError_t group_copy<double>(double* const*, double*, int64_t, int64_t, int, bool,
+                                        cudaStream_t);
+template cudaError_t group_copy<zdbl>(zdbl* const*, zdbl*, int64_t, int64_t, int, bool,
+                                      cudaStream_t);
 template cudaError_t fill_identity<double>(double*, int, cudaStream_t, int);
 template cudaError_t fill_identity<zdbl>(zdbl*, int, cudaStream_t, int);
 

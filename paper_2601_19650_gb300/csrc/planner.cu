@@ -264,7 +264,20 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
   auto sb = [&](int i) { return i < L ? (int)st.bond[i] : 1; };  // alpha_{i-1} (site i's parent leg)
   auto ob = [&](int i) { return i < L ? (int)op.bond[i] : 1; };
   const std::vector<T> ones(nb, host_one<T>());
-  // node tensor i of every instance, consecutive (a gather into `tmp` when nb > 1)
+  // pointer table of the inputs, [site][state, op][instance], for the gathers
+  T** in_ptrs = nullptr;
+  if (nb > 1) {
+    std::vector<void*> h((size_t)2 * L * nb);
+    for (int i = 0; i < L; ++i)
+      for (int b = 0; b < nb; ++b) {
+        h[((size_t)i * 2 + 0) * nb + b] = sts[b]->data[i];
+        h[((size_t)i * 2 + 1) * nb + b] = opv[b]->data[i];
+      }
+    in_ptrs = ar.get<T*>(h.size());
+    CKA(in_ptrs);
+    CK(cudaMemcpyAsync(in_ptrs, h.data(), sizeof(void*) * h.size(), cudaMemcpyHostToDevice, s));
+  }
+  // node tensor i of every instance, consecutive (one gather launch into `tmp` when nb > 1)
   auto site_in = [&](int i, bool opside, const T** p) -> int {
     const Net& ref = opside ? op : st;
     if (nb == 1) {
@@ -274,9 +287,7 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     const int64_t ne = ref.numel[i];
     T* g = tmp.get<T>((size_t)nb * ne);
     if (!g) return cuda_fail(tmp.err, "workspace allocation (gathered inputs)");
-    for (int b = 0; b < nb; ++b)
-      CK(cudaMemcpyAsync(g + b * ne, (opside ? opv[b] : sts[b])->data[i], sizeof(T) * ne,
-                         cudaMemcpyDeviceToDevice, s));
+    CK(group_copy<T>(in_ptrs + ((size_t)i * 2 + (opside ? 1 : 0)) * nb, g, ne, ne, nb, true, s));
     *p = g;
     return CBC_OK;
   };
@@ -396,12 +407,15 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     // publishes the group's node tensors into the per-instance outputs
     auto emit = [&]() -> int {
       if (nb == 1) return CBC_OK;
+      std::vector<void*> h(nb);
       for (int b = 0; b < nb; ++b) {
-        void* dst = nullptr;
-        CK(cudaMallocAsync(&dst, sizeof(T) * (size_t)cn * n, s));
-        outs[b]->data[i] = dst;
-        CK(cudaMemcpyAsync(dst, node + b * nbs, sizeof(T) * (size_t)cn * n, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMallocAsync(&h[b], sizeof(T) * (size_t)cn * n, s));
+        outs[b]->data[i] = h[b];
       }
+      T** tab = tmp.get<T*>(nb);
+      if (!tab) return cuda_fail(tmp.err, "workspace allocation (output table)");
+      CK(cudaMemcpyAsync(tab, h.data(), sizeof(void*) * nb, cudaMemcpyHostToDevice, s));
+      CK(group_copy<T>(tab, node, nbs, (int64_t)cn * n, nb, false, s));
       return CBC_OK;
     };
     if (i == 0) {  // T'^[1] = S^[1]
