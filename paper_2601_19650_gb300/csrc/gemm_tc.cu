@@ -484,13 +484,31 @@ __global__ void __launch_bounds__(256) expo_kernel(const T* src, View v, int R, 
   }
 }
 
-// Balanced base-256 digits of t = x 2^(7-e) (|t| < 128): N = rint(t 256^(S-1)) is formed
-// by one FP64 scaling and rounding; the digits q_{S-1} .. q_1 are the balanced
-// remainders of N by 256 (in [-128, 127]) and q_0 the remaining quotient (|q_0| <= 128),
-// so t = sum_s q_s 256^-s up to 0.5 256^-(S-1).  Integer operations only after the
-// rounding.
+// Balanced base-256 digits of t = x 2^(7-e) (|t| < 128): N = rint(t 256^(S-1)) (round to
+// nearest, ties to even), then the digits q_{S-1} .. q_1 are the balanced remainders of N
+// by 256 (in [-128, 127]) and q_0 the remaining quotient (|q_0| <= 128), so
+// t = sum_s q_s 256^-s up to 0.5 256^-(S-1).  N is taken straight from the bit pattern of
+// x (mantissa shifted with the rounding done on the bits that fall off): integer
+// operations only, since a scaling and an FP64-to-integer conversion per value would run
+// on the narrow FP64 pipe of this part.
 __device__ __forceinline__ void digits(double x, int e, int S, int (&q)[5]) {
-  long long N = __double2ll_rn(ldexp(x, 7 + 8 * (S - 1) - e));
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long mant = (b & 0xfffffffffffffull) | (ex ? (1ull << 52) : 0ull);
+  const int k = (ex ? ex : 1) - 1075 + 7 + 8 * (S - 1) - e;  // N = rint(mant 2^k)
+  long long N;
+  if (k >= 0) {
+    N = (long long)(mant << min(k, 63));
+  } else if (k <= -64) {
+    N = 0;
+  } else {
+    const int sh = -k;
+    unsigned long long qq = mant >> sh;
+    const unsigned long long rem = mant & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (qq & 1ull))) ++qq;
+    N = (long long)qq;
+  }
+  if (b >> 63) N = -N;
   for (int sl = S - 1; sl >= 1; --sl) {
     const long long hi = (N + 128) >> 8;  // floor((N + 128) / 256)
     q[sl] = (int)(N - (hi << 8));
