@@ -158,6 +158,65 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
   }
 }
 
+// One CTA per matrix of a batch (blockIdx.x), the lower triangle packed in shared memory
+// ((i, l) at i (i + 1) / 2 + l): right-looking, one column per step, no grid barriers.
+// For batches, where the matrices themselves fill the SMs.
+template <typename T>
+__global__ void __launch_bounds__(TPB) chol1_kernel(T* G, int m, int* status) {
+  using O = ops<T>;
+  extern __shared__ unsigned char sm_raw[];
+  T* L = reinterpret_cast<T*>(sm_raw);
+  __shared__ double s_rc;
+  __shared__ int s_bad;
+  G += (int64_t)blockIdx.x * m * m;
+  const int64_t tri = (int64_t)m * (m + 1) / 2;
+  for (int64_t t = threadIdx.x; t < tri; t += blockDim.x) {
+    const int i = tri_row(t);
+    L[t] = G[(int64_t)i * m + (t - (int64_t)i * (i + 1) / 2)];
+  }
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int j = 0; j < m; ++j) {
+    const int64_t dj = (int64_t)j * (j + 1) / 2 + j;
+    if (threadIdx.x == 0) {
+      const double piv = O::real(L[dj]);
+      if (!(piv > 0.0) || !isfinite(piv)) {
+        s_bad = 1;
+      } else {
+        const double rc = rsqrt64(piv);  // 1 / sqrt(piv)
+        L[dj] = O::make(piv * rc, 0.0);
+        s_rc = rc;
+      }
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const double rc = s_rc;
+    for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) {
+      T* x = L + (int64_t)i * (i + 1) / 2 + j;
+      *x = O::scale(rc, *x);
+    }
+    __syncthreads();
+    // trailing lower triangle (i, l), j < l <= i: L[i][l] -= L[i][j] conj(L[l][j])
+    const int r = m - j - 1;
+    const int64_t nt = (int64_t)r * (r + 1) / 2;
+    for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) {
+      const int ii = tri_row(t);
+      const int i = j + 1 + ii, l = j + 1 + (int)(t - (int64_t)ii * (ii + 1) / 2);
+      const int64_t bi = (int64_t)i * (i + 1) / 2, bl = (int64_t)l * (l + 1) / 2;
+      L[bi + l] = O::fma(O::scale(-1.0, L[bi + j]), O::conj(L[bl + j]), L[bi + l]);
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (threadIdx.x == 0) set_status(status, CBC_ERR_NOT_POSITIVE_DEFINITE);
+    return;
+  }
+  for (int64_t t = threadIdx.x; t < tri; t += blockDim.x) {
+    const int i = tri_row(t);
+    G[(int64_t)i * m + (t - (int64_t)i * (i + 1) / 2)] = L[t];
+  }
+}
+
 // S (m x n) <- C^{-1} S, C lower triangular (row-major m x m).  One warp per column.
 template <typename T, bool CSMEM>
 __global__ void trsm_cols_kernel(const T* C, T* S, int m, int n) {
@@ -217,6 +276,15 @@ cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cud
     if (err != cudaSuccess) return err;
   }
   note_launches(CBC_K_CHOLQR, 1);
+  // a batch of 8 or more: one CTA per matrix (its FP64 work spread over the batch
+  // instead of over a cluster per matrix)
+  const size_t tri_bytes = (size_t)m * (m + 1) / 2 * sizeof(T);
+  if (nb >= 8 && tri_bytes <= 200 * 1024) {
+    err = allow_max_smem((const void*)chol1_kernel<T>);
+    if (err != cudaSuccess) return err;
+    chol1_kernel<T><<<nb, TPB, tri_bytes, s>>>(G, m, status);
+    return cudaGetLastError();
+  }
   int P = std::max(1, std::min(16, (m * m) / 256));
   if (cluster_ctas((const void*)chol_kernel<T>, P, TPB, shm) == P) {
     CholArgs<T> a{G, m, status, (GridBarrier*)bar, P};

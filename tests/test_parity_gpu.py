@@ -200,10 +200,12 @@ def _check_against_oracle(probs, res, bar):
     return refs
 
 
-@pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
-def test_group_lockstep(precision, bar):
+@pytest.mark.parametrize("precision,bar,count", [(0, FP64_BAR, 4), (1, MIXED_BAR, 4),
+                                                 (0, FP64_BAR, 9), (1, MIXED_BAR, 9)])
+def test_group_lockstep(precision, bar, count):
+    # 4 instances: one cluster per matrix; 9: one CTA per matrix for the Cholesky
     L = 9
-    probs = [make_problem(2, seed=20 + j, L=L, chi=16, D=4, max_bond=12) for j in range(4)]
+    probs = [make_problem(2, seed=20 + j, L=L, chi=16, D=4, max_bond=12) for j in range(count)]
     res, stats = _apply_batched(probs, precision)
     _check_against_oracle(probs, res, bar)
     # one eigensolver launch group per cut for the whole group, not one per instance
