@@ -307,7 +307,9 @@ cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* b
   (void)status;
   (void)bar;
   (void)num_sms;
-  const int nw = 4;  // warps (columns) per CTA: one per SM sub-partition
+  // warps (columns) per CTA sharing one staged triangle: two per SM sub-partition when a
+  // batch provides the CTAs, else one (more CTAs for a lone solve)
+  const int nw = nb >= 8 ? 8 : 4;
   const size_t tri = (size_t)m * (m + 1) / 2 * sizeof(T);
   const size_t rest = (size_t)m * sizeof(double) + (size_t)nw * m * sizeof(T);
   note_launches(CBC_K_CHOLQR, 1);

@@ -1060,6 +1060,26 @@ __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
     }
 }
 
+// Initial contents of a batch of eigensolver workspaces in one launch: up to 6 segments
+// of 64-bit words per instance (instance blockIdx.y, workspaces wb bytes apart).
+struct WsInit {
+  unsigned long long* seg[6];
+  int64_t words[6];
+  unsigned long long val[6];
+  int nseg;
+  size_t wb;
+};
+
+__global__ void ws_init_kernel(WsInit a) {
+  const size_t off = blockIdx.y * a.wb;
+  for (int g = 0; g < a.nseg; ++g) {
+    unsigned long long* p = byte_shift(a.seg[g], off);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.words[g];
+         i += (int64_t)gridDim.x * blockDim.x)
+      p[i] = a.val[g];
+  }
+}
+
 }  // namespace
 
 // workspace layout (all 256-byte aligned)
@@ -1111,13 +1131,6 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   T* Dg = (T*)take(ts * (size_t)m * m);
 
   cudaError_t err = cudaSuccess;
-  for (int b = 0; b < nb && err == cudaSuccess; ++b) {
-    const size_t off = (size_t)b * wb;
-    err = cudaMemsetAsync(byte_shift(bar, off), 0, sizeof(GridBarrier), s);
-    if (err == cudaSuccess) err = cudaMemsetAsync(byte_shift(tau, off), 0, ts * m, s);
-    if (err == cudaSuccess && m == 1) err = cudaMemsetAsync(byte_shift(e, off), 0, sizeof(double), s);
-  }
-  if (err != cudaSuccess) return err;
   // algorithmic FP64 flops: Householder tridiagonalisation (16/3) m^3 complex,
   // (4/3) m^3 real; back transformation of kmax vectors 8 m^2 kmax complex, 2 m^2 kmax real
   const double cm = ops<T>::cplx ? 4.0 : 1.0;
@@ -1149,14 +1162,29 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   }
   if (!cluster && Pw <= 0) P = std::max(1, std::min(num_sms, m / 4));
   const bool in_smem = cluster || shm_for(P) <= shm_cap;
-  if (in_smem) {
-    // the exchange buffers start as all-ones bit patterns (the "not yet written" mark)
-    for (int b = 0; b < nb && err == cudaSuccess; ++b) {
-      err = cudaMemsetAsync(byte_shift(V, b * wb), 0xff, ts * (size_t)m * m, s);
-      if (err == cudaSuccess) err = cudaMemsetAsync(byte_shift(Pg, b * wb), 0xff, ts * (size_t)m * m, s);
-      if (err == cudaSuccess) err = cudaMemsetAsync(byte_shift(Dg, b * wb), 0xff, ts * (size_t)m * m, s);
+  {
+    // barrier, tau and e[0] start at zero; with the rows in shared memory the exchange
+    // buffers start as all-ones bit patterns (the "not yet written" mark)
+    WsInit wi{};
+    auto add = [&](void* p, size_t bytes, unsigned long long v) {
+      wi.seg[wi.nseg] = static_cast<unsigned long long*>(p);
+      wi.words[wi.nseg] = (int64_t)(bytes / 8);
+      wi.val[wi.nseg] = v;
+      ++wi.nseg;
+    };
+    add(bar, sizeof(GridBarrier), 0ull);
+    add(tau, ts * m, 0ull);
+    add(e, sizeof(double), 0ull);
+    if (in_smem) {
+      add(V, ts * (size_t)m * m, ~0ull);
+      add(Pg, ts * (size_t)m * m, ~0ull);
+      add(Dg, ts * (size_t)m * m, ~0ull);
     }
-    if (err == cudaSuccess) err = allow_max_smem(ksm);
+    wi.wb = wb;
+    note_launches(CBC_K_AUX, 1);
+    ws_init_kernel<<<dim3((unsigned)std::min<int64_t>(64, ((int64_t)m * m * (ts / 8) + 255) / 256), nb), 256, 0, s>>>(wi);
+    err = cudaGetLastError();
+    if (err == cudaSuccess && in_smem) err = allow_max_smem(ksm);
     if (err != cudaSuccess) return err;
   }
   {
