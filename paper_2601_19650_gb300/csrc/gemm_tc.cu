@@ -175,8 +175,10 @@ struct TcArgs {
 // ldexp((double)a, e) formed with integer operations: the int64 is rounded to 53 bits
 // (round to nearest, ties to even, as the conversion instruction does) and the exponent
 // field written directly, so the epilogue keeps off the narrow FP64 pipe of this part.
-// Results outside the normal range take the FP64 route.
-__device__ __forceinline__ double i64_ldexp(long long a, int e) {
+// Results outside the normal range take the FP64 route.  Not inlined: the epilogue calls
+// it once per accumulator, and 32 inlined copies per instantiation overflow the
+// instruction cache.
+__device__ __noinline__ double i64_ldexp(long long a, int e) {
   if (a == 0) return 0.0;
   const unsigned long long neg = a < 0 ? 1ull : 0ull;
   const unsigned long long m = neg ? 0ull - (unsigned long long)a : (unsigned long long)a;
@@ -380,23 +382,33 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty + buf);
       }
-      if (run && q.n_chunks > 0 && row < a.M) {
-        const int ea = a.expA[q.prob * a.Mp + row];
+      if (!run) break;
+      if (q.n_chunks > 0) {
+        // the 32 columns of this warp are shared by its lanes (the lanes are rows): lane i
+        // finds column i's offset and exponent once, the loop takes them by shuffle
         const int* expB = a.expB + (int64_t)q.prob * a.ebsB;
         char* Cp = a.C + (int64_t)q.prob * a.vc.bs * (a.cplx ? 16 : 8);
+        const int mycol = q.n0 + colg * 32 + lane;
+        const int myn = a.cplx ? (mycol >> 1) : mycol;
+        const bool myok = mycol < a.N2;
+        const long long mycoff = myok ? (long long)a.vc.coff(myn) : 0;
+        const int myexp = myok ? expB[myn] : 0;
+        const bool rowok = row < a.M;
+        const int ea = rowok ? a.expA[q.prob * a.Mp + row] : 0;
         const int bias = -14 - 8 * (S - 1);
-        const int64_t ro = a.vc.roff(row);
+        const int64_t ro = rowok ? a.vc.roff(row) : 0;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
+          const long long co = __shfl_sync(0xffffffffu, mycoff, i);
+          const int eb = __shfl_sync(0xffffffffu, myexp, i);
           const int col = q.n0 + colg * 32 + i;
-          if (col < a.N2) {
-            const int ncol = a.cplx ? (col >> 1) : col;
-            const double v = i64_ldexp(acc[i], ea + expB[ncol] + bias);
+          if (rowok && col < a.N2) {
+            const double v = i64_ldexp(acc[i], ea + eb + bias);
             double* dst;
             if (a.cplx)
-              dst = reinterpret_cast<double*>(Cp + 16 * (ro + a.vc.coff(ncol))) + (col & 1);
+              dst = reinterpret_cast<double*>(Cp + 16 * (ro + co)) + (col & 1);
             else
-              dst = reinterpret_cast<double*>(Cp + 8 * (ro + a.vc.coff(ncol)));
+              dst = reinterpret_cast<double*>(Cp + 8 * (ro + co));
             if (a.atomic)
               atomicAdd(dst, v);
             else
