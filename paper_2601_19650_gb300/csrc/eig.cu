@@ -437,6 +437,52 @@ __device__ __forceinline__ dfz dff(dfz a, dfz b, dfz c) {  // c + a b, complex
 __device__ __forceinline__ df1 dfconj(df1 a) { return a; }
 __device__ __forceinline__ dfz dfconj(dfz a) { return {a.re, df_neg(a.im)}; }
 
+// householder_pub by one warp (lane = this thread's lane): no CTA barrier, so the other
+// warps of the owner CTA keep updating their rows meanwhile.
+template <typename T>
+__device__ void householder_pub_warp(const Tri2Args<T>& a, const T* row, int j, T* vs,
+                                     int lane) {
+  using O = ops<T>;
+  const int m = a.m;
+  double xn2 = 0.0;
+  for (int c = j + 2 + lane; c < m; c += 32) xn2 += O::abs2(row[c]);
+  xn2 = warp_sum(xn2);
+  const T alpha = O::conj(row[j + 1]);
+  const double ar = O::real(alpha), ai = O::imag(alpha);
+  T tau, scale;
+  double beta;
+  const bool trivial = (xn2 == 0.0 && ai == 0.0);
+  if (trivial) {
+    tau = O::zero();
+    beta = ar;
+    scale = O::zero();
+  } else {
+    const double n2 = ar * ar + ai * ai + xn2;
+    const double rn = rsqrt64(n2);  // 1 / ||x||
+    const double nrm = n2 * rn;
+    beta = (ar >= 0.0) ? -nrm : nrm;
+    const double ib = (ar >= 0.0) ? -rn : rn;  // 1 / beta
+    tau = O::make((beta - ar) * ib, -ai * ib);
+    const double zr = ar - beta, zi = ai;
+    const double iden = rcp64(zr * zr + zi * zi);
+    scale = O::make(zr * iden, -zi * iden);
+  }
+  T* vg = a.V + (int64_t)j * m;
+  for (int c = j + 1 + lane; c < m; c += 32) {
+    const T v = (c == j + 1) ? O::one() : (trivial ? O::zero() : O::conj(row[c]) * scale);
+    vs[c] = v;
+    st_pub(vg + c, v);
+  }
+  if (lane == 0) {
+    vs[j] = tau;
+    st_pub(vg + j, tau);
+    a.tau[j] = tau;
+    a.e[j] = beta;
+    a.d[j] = O::real(row[j]);
+  }
+  __syncwarp();
+}
+
 // DF: rows as double-float pairs (mixed path); else FP64 throughout.
 template <typename T, bool DF>
 __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
@@ -622,15 +668,27 @@ __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
           row[c] = O::fma(nwr, O::conj(vsm[c]), O::fma(nvr, O::conj(psm[c]), row[c]));
       }
     };
-    int tstart = t0;
     if (j + 1 < m - 1 && (j + 1) % P == cta) {
-      // the next column's owner: update that row with the whole CTA, publish v_{j+1}
-      update_row(t0, threadIdx.x, blockDim.x);
-      __syncthreads();
-      householder_pub(a, row64(t0, j + 1), j + 1, vbuf + (size_t)((j + 1) & 1) * m, sh);
-      tstart = t0 + 1;
+      // the next column's owner: warp 0 updates that row and publishes v_{j+1} while
+      // the other warps update the remaining rows
+      if (warp == 0) {
+        update_row(t0, lane, 32);
+        __syncwarp();
+        const T* hr;
+        if constexpr (DF) {
+          for (int c = j + 1 + lane; c < m; c += 32) hrow[c] = from_df(rdf[(size_t)t0 * m + c]);
+          __syncwarp();
+          hr = hrow;
+        } else {
+          hr = rows + (size_t)t0 * m;
+        }
+        householder_pub_warp(a, hr, j + 1, vbuf + (size_t)((j + 1) & 1) * m, lane);
+      } else {
+        for (int t = t0 + 1 + (warp - 1); t < nr; t += nw - 1) update_row(t, lane, 32);
+      }
+    } else {
+      for (int t = t0 + warp; t < nr; t += nw) update_row(t, lane, 32);
     }
-    for (int t = tstart + warp; t < nr; t += nw) update_row(t, lane, 32);
     if (j + 1 == m - 1 && (m - 1) % P == cta) {
       __syncthreads();
       const T* rl = row64((m - 1 - cta) / P, m - 1);
