@@ -260,10 +260,64 @@ __device__ __forceinline__ bool ld_pub(const zdbl* p, zdbl* v) {
   return __double_as_longlong(x) != kSentinel && __double_as_longlong(y) != kSentinel;
 }
 
-// dst[lo, hi) <- src[lo, hi) as the entries get published.  False (for the whole CTA)
-// when a wait ran out or another CTA has reported an error.
+// ---- double-float arithmetic (value = h + l, two FP32 numbers, ~2^-46 relative) -----
+// On this part FP32 issues ~64x faster than FP64, so the mixed path keeps the rows of
+// the tridiagonal reduction as double-float pairs and runs its two O(m^2)-per-column
+// loops (p = A v and the rank-2 update) in FP32 with error-free transformations
+// (TwoProduct by fma, TwoSum; Dekker and Knuth).  The rounded intrinsics keep the
+// compiler from contracting them.
+struct df1 {
+  float h, l;
+};
+struct dfz {
+  df1 re, im;
+};
 template <typename T>
-__device__ bool gather_pub(const T* src, T* dst, int lo, int hi, int* status) {
+struct dfof;
+template <>
+struct dfof<double> {
+  using type = df1;
+};
+template <>
+struct dfof<zdbl> {
+  using type = dfz;
+};
+__device__ __forceinline__ df1 df_make(double x) {
+  const float h = __double2float_rn(x);
+  return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ df1 df_neg(df1 a) { return {-a.h, -a.l}; }
+// c + a b
+__device__ __forceinline__ df1 df_fma(df1 a, df1 b, df1 c) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, e);
+  e = __fmaf_rn(a.l, b.h, e);
+  const float s = __fadd_rn(c.h, p);
+  const float bb = __fsub_rn(s, c.h);
+  float t = __fadd_rn(__fsub_rn(c.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  t = __fadd_rn(t, __fadd_rn(c.l, e));
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df1 to_df(double x) { return df_make(x); }
+__device__ __forceinline__ dfz to_df(zdbl x) { return {df_make(x.re), df_make(x.im)}; }
+__device__ __forceinline__ double from_df(df1 a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ zdbl from_df(dfz a) { return {from_df(a.re), from_df(a.im)}; }
+__device__ __forceinline__ df1 dff(df1 a, df1 b, df1 c) { return df_fma(a, b, c); }
+__device__ __forceinline__ dfz dff(dfz a, dfz b, dfz c) {  // c + a b, complex
+  return {df_fma(df_neg(a.im), b.im, df_fma(a.re, b.re, c.re)),
+          df_fma(a.im, b.re, df_fma(a.re, b.im, c.im))};
+}
+__device__ __forceinline__ df1 dfconj(df1 a) { return a; }
+__device__ __forceinline__ dfz dfconj(dfz a) { return {a.re, df_neg(a.im)}; }
+
+// dst[lo, hi) <- src[lo, hi) as the entries get published (and their double-float forms
+// into ddst when given).  False (for the whole CTA) when a wait ran out or another CTA
+// has reported an error.
+template <typename T>
+__device__ bool gather_pub(const T* src, T* dst, int lo, int hi, int* status,
+                           typename dfof<T>::type* ddst = nullptr) {
   bool ok = true;
   for (int c = lo + threadIdx.x; c < hi && ok; c += blockDim.x) {
     T v;
@@ -282,6 +336,7 @@ __device__ bool gather_pub(const T* src, T* dst, int lo, int hi, int* status) {
       }
     }
     dst[c] = v;
+    if (ddst) ddst[c] = to_df(v);
   }
   return __syncthreads_and(ok) != 0;
 }
@@ -385,58 +440,6 @@ __device__ void householder_pub(const Tri2Args<T>& a, const T* row, int j, T* vs
   __syncthreads();
 }
 
-// ---- double-float arithmetic (value = h + l, two FP32 numbers, ~2^-46 relative) -----
-// On this part FP32 issues ~64x faster than FP64, so the mixed path keeps the rows of
-// the tridiagonal reduction as double-float pairs and runs its two O(m^2)-per-column
-// loops (p = A v and the rank-2 update) in FP32 with error-free transformations
-// (TwoProduct by fma, TwoSum; Dekker and Knuth).  The rounded intrinsics keep the
-// compiler from contracting them.
-struct df1 {
-  float h, l;
-};
-struct dfz {
-  df1 re, im;
-};
-template <typename T>
-struct dfof;
-template <>
-struct dfof<double> {
-  using type = df1;
-};
-template <>
-struct dfof<zdbl> {
-  using type = dfz;
-};
-__device__ __forceinline__ df1 df_make(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ df1 df_neg(df1 a) { return {-a.h, -a.l}; }
-// c + a b
-__device__ __forceinline__ df1 df_fma(df1 a, df1 b, df1 c) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  const float s = __fadd_rn(c.h, p);
-  const float bb = __fsub_rn(s, c.h);
-  float t = __fadd_rn(__fsub_rn(c.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  t = __fadd_rn(t, __fadd_rn(c.l, e));
-  const float h = __fadd_rn(s, t);
-  return {h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-__device__ __forceinline__ df1 to_df(double x) { return df_make(x); }
-__device__ __forceinline__ dfz to_df(zdbl x) { return {df_make(x.re), df_make(x.im)}; }
-__device__ __forceinline__ double from_df(df1 a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ zdbl from_df(dfz a) { return {from_df(a.re), from_df(a.im)}; }
-__device__ __forceinline__ df1 dff(df1 a, df1 b, df1 c) { return df_fma(a, b, c); }
-__device__ __forceinline__ dfz dff(dfz a, dfz b, dfz c) {  // c + a b, complex
-  return {df_fma(df_neg(a.im), b.im, df_fma(a.re, b.re, c.re)),
-          df_fma(a.im, b.re, df_fma(a.re, b.im, c.im))};
-}
-__device__ __forceinline__ df1 dfconj(df1 a) { return a; }
-__device__ __forceinline__ dfz dfconj(dfz a) { return {a.re, df_neg(a.im)}; }
-
 // householder_pub by one warp (lane = this thread's lane): no CTA barrier, so the other
 // warps of the owner CTA keep updating their rows meanwhile.
 template <typename T>
@@ -470,9 +473,10 @@ __device__ void householder_pub_warp(const Tri2Args<T>& a, const T* row, int j, 
   T* vg = a.V + (int64_t)j * m;
   for (int c = j + 1 + lane; c < m; c += 32) {
     const T v = (c == j + 1) ? O::one() : (trivial ? O::zero() : O::conj(row[c]) * scale);
-    vs[c] = v;
     st_pub(vg + c, v);
+    vs[c] = v;
   }
+
   if (lane == 0) {
     vs[j] = tau;
     st_pub(vg + j, tau);
@@ -513,8 +517,8 @@ __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
   // DF only: v and w as double-float, and the owner's row j+1 back in FP64
   using D = typename dfof<T>::type;
   D* rdf = reinterpret_cast<D*>(rows);
-  D* vdf = reinterpret_cast<D*>(dsm + P);
-  D* wdf = vdf + m;
+  D* vdfb = reinterpret_cast<D*>(dsm + P);  // two buffers, like vbuf
+  D* wdf = vdfb + 2 * (size_t)m;
   T* hrow = reinterpret_cast<T*>(wdf + m);
   for (int t = 0; t < nr; ++t)
     for (int c = threadIdx.x; c < m; c += blockDim.x) {
@@ -542,16 +546,25 @@ __global__ void __launch_bounds__(TPB) tridiag_smem_kernel(Tri2Args<T> a0) {
     }
     return;
   }
-  if (cta == 0) householder_pub(a, row64(0, 0), 0, vbuf, sh);
+  if (cta == 0) {
+    householder_pub(a, row64(0, 0), 0, vbuf, sh);
+    if constexpr (DF) {
+      for (int c = 1 + threadIdx.x; c < m; c += blockDim.x) vdfb[c] = to_df(vbuf[c]);
+      __syncthreads();
+    }
+  }
   for (int j = 0; j < m - 1; ++j) {
     T* vsm = vbuf + (size_t)(j & 1) * m;
+    D* vdf = vdfb + (size_t)(j & 1) * m;
     // v_j and tau_j (the owner of row j computed them into vsm itself)
-    if (j % P != cta && !gather_pub(a.V + (int64_t)j * m, vsm, j, m, a.status)) return;
-    const T tau = vsm[j];
-    if constexpr (DF) {
+    // (the double-float copy of v goes with the gather; the owner converts its own v)
+    if (j % P != cta) {
+      if (!gather_pub(a.V + (int64_t)j * m, vsm, j, m, a.status, DF ? vdf : nullptr)) return;
+    } else if (DF && j > 0) {
       for (int c = j + 1 + threadIdx.x; c < m; c += blockDim.x) vdf[c] = to_df(vsm[c]);
       __syncthreads();
     }
+    const T tau = vsm[j];
     // phase B: p_r = tau sum_{c>j} A[r][c] v_c for own rows r > j
     const int t0 = (j + 1 - cta + P - 1) / P;  // first own row beyond j
     const int live = nr - t0;
@@ -1203,7 +1216,7 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   int Pw = 0;
   if (const char* env = getenv("CBC_TRIDIAG_CTAS")) Pw = std::max(0, std::min(num_sms, atoi(env)));
   auto shm_for = [&](int P) {
-    return (((size_t)((m + P - 1) / P) + (df ? 7 : 4)) * m + P) * ts;
+    return (((size_t)((m + P - 1) / P) + (df ? 8 : 4)) * m + P) * ts;
   };
   // double-float rows pay off when the batch makes the reduction throughput bound; a
   // lone reduction is latency bound and runs faster in FP64
