@@ -55,7 +55,9 @@ struct CholArgs {
 };
 
 // G (row-major m x m, Hermitian, lower triangle read) -> C (lower triangle), G = C C^H
-template <typename T>
+// PSMEM: the panel of the trailing update is copied to shared memory (m up to ~440
+// complex); else the update reads it from global memory (L2).
+template <typename T, bool PSMEM>
 __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
   using O = ops<T>;
   extern __shared__ unsigned char sm_raw[];
@@ -137,19 +139,27 @@ __global__ void __launch_bounds__(TPB) chol_kernel(CholArgs<T> a) {
     const int r0 = b0 + nb;
     if (r0 < m) {
       const int rows = m - r0;
-      for (int t = threadIdx.x; t < rows * NB; t += blockDim.x) {
-        int i = t / NB, l = t % NB;
-        pan[t] = (l < nb) ? ldg_cg(a.G + (int64_t)(r0 + i) * m + b0 + l) : O::zero();
+      if (PSMEM) {
+        for (int t = threadIdx.x; t < rows * NB; t += blockDim.x) {
+          int i = t / NB, l = t % NB;
+          pan[t] = (l < nb) ? ldg_cg(a.G + (int64_t)(r0 + i) * m + b0 + l) : O::zero();
+        }
+        __syncthreads();
       }
-      __syncthreads();
       const int64_t nt = (int64_t)rows * (rows + 1) / 2;
       for (int64_t t = (int64_t)cta * blockDim.x + threadIdx.x; t < nt; t += (int64_t)P * blockDim.x) {
         // t -> (i, c) with c <= i in the packed lower triangle
         const int i = tri_row(t);
         const int c = (int)(t - (int64_t)i * (i + 1) / 2);
         T sacc = O::zero();
+        if (PSMEM) {
 #pragma unroll 8
-        for (int l = 0; l < NB; ++l) sacc = O::fma(pan[i * NB + l], O::conj(pan[c * NB + l]), sacc);
+          for (int l = 0; l < NB; ++l) sacc = O::fma(pan[i * NB + l], O::conj(pan[c * NB + l]), sacc);
+        } else {
+          const T* pi = a.G + (int64_t)(r0 + i) * m + b0;
+          const T* pc = a.G + (int64_t)(r0 + c) * m + b0;
+          for (int l = 0; l < nb; ++l) sacc = O::fma(ldg_cg(pi + l), O::conj(ldg_cg(pc + l)), sacc);
+        }
         T* g = a.G + (int64_t)(r0 + i) * m + r0 + c;
         *g = ldg_cg(g) - sacc;
       }
@@ -270,9 +280,12 @@ cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cud
   // streams' work), else a cooperative launch over more SMs per matrix
   cudaError_t err = cudaMemsetAsync(bar, 0, sizeof(GridBarrier) * nb, s);
   if (err != cudaSuccess) return err;
-  size_t shm = (size_t)std::max(m, NB) * NB * sizeof(T);
+  // the panel in shared memory when it fits, else read from global memory
+  const bool psmem = (size_t)std::max(m, NB) * NB * sizeof(T) <= 200 * 1024;
+  const size_t shm = (size_t)(psmem ? std::max(m, NB) : NB) * NB * sizeof(T);
+  const void* kch = psmem ? (const void*)chol_kernel<T, true> : (const void*)chol_kernel<T, false>;
   if (shm > 48 * 1024) {
-    err = allow_max_smem((const void*)chol_kernel<T>);
+    err = allow_max_smem(kch);
     if (err != cudaSuccess) return err;
   }
   note_launches(CBC_K_CHOLQR, 1);
@@ -286,16 +299,16 @@ cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cud
     return cudaGetLastError();
   }
   int P = std::max(1, std::min(16, (m * m) / 256));
-  if (cluster_ctas((const void*)chol_kernel<T>, P, TPB, shm) == P) {
+  if (cluster_ctas(kch, P, TPB, shm) == P) {
     CholArgs<T> a{G, m, status, (GridBarrier*)bar, P};
     void* args[] = {&a};
-    return launch_cluster((const void*)chol_kernel<T>, P, nb * P, TPB, shm, args, s);
+    return launch_cluster(kch, P, nb * P, TPB, shm, args, s);
   }
   P = std::max(1, std::min(num_sms, (m * m) / 256));
   for (int b = 0; b < nb; ++b) {
     CholArgs<T> a{G + (int64_t)b * m * m, m, status, (GridBarrier*)bar + b, P};
     void* args[] = {&a};
-    err = cudaLaunchCooperativeKernel((const void*)chol_kernel<T>, dim3(P), dim3(TPB), args, shm, s);
+    err = cudaLaunchCooperativeKernel(kch, dim3(P), dim3(TPB), args, shm, s);
     if (err != cudaSuccess) return err;
   }
   return cudaSuccess;

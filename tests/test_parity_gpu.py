@@ -151,6 +151,22 @@ def test_batched_heterogeneous(precision, bar):
 
 
 # ---------------------------------------------------------------------------------------
+# large bonds: the paths for matrices too large for shared memory
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+def test_large_bonds(precision):
+    # bond 480 in the middle of a d = 4 chain: the CholeskyQR Gram is 480 x 480 (blocked
+    # Cholesky with its panel read from global memory, triangular solve with the factor in
+    # global memory) and a truncation Gram is 960 x 960 (tridiagonal reduction with the
+    # rows in global memory, one-vector-per-CTA back transformation)
+    p = make_problem(2, seed=3, L=10, d=4, chi=480, D=2, max_bond=480)
+    if precision == 0:
+        _compare(p)
+    else:
+        _compare_mixed(p)
+
+
+# ---------------------------------------------------------------------------------------
 # lockstep groups: cbc_apply_batched runs instances of one shape as one launch per step
 # ---------------------------------------------------------------------------------------
 def _apply_batched(probs, precision, workers=1):
