@@ -29,9 +29,26 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "CBC applications/sec & TFLOP/s, mixed vs FP64 plain on 1 GB300 at rel err ≤1e-6"
-WORKLOAD = dict(workload="MPO on MPS, L=64, d=2, chi=128, D=16, max_bond=128, complex64 "
-                         "Gaussian entries (unit Frobenius norm per tensor)",
-                L=64, d=2, chi=128, D=16, max_bond=128, input_dtype="complex64")
+WORKLOADS = {
+    # the headline: MPO on MPS (config 2); a step is B instances in one lockstep group
+    "mpo_mps": dict(workload="MPO on MPS, L=64, d=2, chi=128, D=16, max_bond=128, complex64 "
+                             "Gaussian entries (unit Frobenius norm per tensor)",
+                    L=64, d=2, chi=128, D=16, max_bond=128, input_dtype="complex64"),
+    # TTNO on TTNS (config 3)
+    "tree": dict(workload="TTNO on TTNS, perfect binary tree with 64 physical leaves (d=2) and "
+                          "63 virtual nodes, state bond 64, operator bond 8, max_bond 64, "
+                          "float32 Gaussian entries", L=6, d=2, chi=64, D=8, max_bond=64,
+                 input_dtype="float32"),
+    # the serving set (config 4): heterogeneous chains, instance j with seed j
+    "serving": dict(workload="independent MPO.MPS instances, L ~ U{16..64}, chi in "
+                             "{32,64,128,256}, D in {4,8,16,32}, d=2, max_bond = chi, float32",
+                    input_dtype="float32"),
+    # the large tensor train (config 5)
+    "large": dict(workload="MPO on MPS, L=100, d=4, chi=1024, D=32, max_bond=1024, complex64 "
+                           "Gaussian entries", L=100, d=4, chi=1024, D=32, max_bond=1024,
+                  input_dtype="complex64"),
+}
+DEFAULT_B = {"mpo_mps": 32, "tree": 8, "serving": 256, "large": 1}
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure in MEASURED_PEAKS)
 # DRAM bytes per launch of a class's dominant kernel, read from an ncu capture of this
 # workload; each entry names the summary under profiles/ it comes from.  A class whose
@@ -133,10 +150,20 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------------------
-def make_workload(seed: int, sites: int = 0):
-    """The MPO-on-MPS workload (L=64 unless `sites` shortens the chain for profiling)."""
+def make_workload(seed: int, sites: int = 0, workload: str = "mpo_mps"):
+    """One instance of a tensor-train or tree workload (`sites` shortens a chain)."""
     from synth import make_problem
-    return make_problem(2, seed=seed, **({"L": sites} if sites > 0 else {}))
+    cfg = {"mpo_mps": 2, "tree": 3, "large": 5}[workload]
+    over = {"L": sites} if (sites > 0 and workload != "tree") else {}
+    return make_problem(cfg, seed=seed, **over)
+
+
+def make_workloads(workload: str, rank: int, B: int, sites: int = 0):
+    """The B instances a rank applies per step."""
+    if workload == "serving":
+        from synth.networks import make_batch
+        return make_batch(n=B, seed0=rank * B)
+    return [make_workload(sd, sites, workload) for sd in instance_seeds(rank, B)]
 
 
 def oracle_time(prob, reps: int = 1):
@@ -164,7 +191,7 @@ def blas_threads() -> int:
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    prob = make_workload(0)
+    prob = make_workloads(args.workload, 0, 1)[0]
     for _ in range(args.warmup):
         oracle_time(prob)
     t = 0.0
@@ -176,7 +203,8 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": dict(WORKLOAD, precision="fp64 (numpy, host)", l2="n/a (host)"),
+            "config": dict(WORKLOADS[args.workload], precision="fp64 (numpy, host)",
+                           l2="n/a (host)"),
             "cpu_baseline": {"value": value, "unit": "applications/s", "cores": blas_threads(),
                              "kind": "oracle",
                              "sample": "one full application of the workload per step (seed 0)"},
@@ -195,10 +223,13 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--concurrency", type=int, default=32,
+    ap.add_argument("--concurrency", type=int, default=0,
                     help="independent applications per step (seeds rank*B .. rank*B+B-1), "
                          "run by cbc_apply_batched: same-shape instances go in lockstep "
-                         "groups of up to 32 (one launch per step per group)")
+                         "groups of up to 32 (one launch per step per group); default per "
+                         "workload: mpo_mps 32, tree 8, serving 256, large 1")
+    ap.add_argument("--workload", default="mpo_mps", choices=sorted(WORKLOADS),
+                    help="mpo_mps (the headline), tree, serving, large")
     ap.add_argument("--sites", type=int, default=0,
                     help="shorter chains for profiling captures (default: the workload's 64)")
     args = ap.parse_args()
@@ -220,14 +251,14 @@ def main():
         import torch.distributed as dist_mod
         dist_mod.init_process_group("nccl")
         dist = dist_mod
-    B = max(1, args.concurrency)
+    B = args.concurrency if args.concurrency > 0 else DEFAULT_B[args.workload]
     streams = [torch.cuda.Stream() for _ in range(B)]
     stream = streams[0]
     sptr = stream.cuda_stream
 
     # precision of the headline number: mixed when built, else fp64
     prec_name = args.precision
-    probs = [make_workload(seed=sd, sites=args.sites) for sd in instance_seeds(rank, B)]
+    probs = make_workloads(args.workload, rank, B, args.sites)
     prob = probs[0]
     st, op = prob.state, prob.op
     hs_list, ho_list = [], []
@@ -346,7 +377,9 @@ def main():
         else:
             peak, bound = FP64_PEAK_TFLOPS, "alu"
             note = "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x ~2.06 GHz)"
-        prof = PROFILED_TRAFFIC.get(dom, {})
+        # the captured traffic belongs to the default step (32 instances, 64 sites)
+        default_step = args.workload == "mpo_mps" and B == 32 and args.sites == 0
+        prof = PROFILED_TRAFFIC.get(dom, {}) if default_step else {}
         roofline = {"bound": bound, "kernel_class": dom, "kernel": KERNEL_OF_CLASS.get(dom, dom),
                     "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak if peak else None,
@@ -361,7 +394,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_name == "fp64" else "bf16-slices+f64",
             "data": "synthetic",
-            "config": dict(WORKLOAD, precision=prec_name, concurrent_applications=B,
+            "config": dict(WORKLOADS[args.workload], precision=prec_name, concurrent_applications=B,
                            batching="cbc_apply_batched: lockstep groups of <= 32 same-shape "
                                     "instances" if B > 1 else "single cbc_apply",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU",
@@ -380,15 +413,26 @@ def main():
         line["config"]["L"] = args.sites
         line["config"]["workload"] = line["config"]["workload"].replace("L=64", f"L={args.sites}")
     # parity of this run's output with the oracle, and the oracle's own time
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "large":
+        line["cpu_baseline"] = None
+        line["cpu_baseline_note"] = "not timed: the FP64 oracle needs hours per application here"
+    elif rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import metrics
+        # instance 0 against the oracle; the oracle timed on instances 0, 1, ... until about
+        # 20 s of host time (a bounded sample of the step's instances)
         t_or, ref = oracle_time(prob)
         shape = _cbc.output_shape_fn(st.parent, st.phys)
-        tens, bonds, log_norm = _cbc.fetch_network(last[0], shape, True)
+        tens, bonds, log_norm = _cbc.fetch_network(last[0], shape,
+                                                   bool(np.iscomplexobj(st.tensors[0])))
         line["rel_err_vs_oracle"] = metrics.rel_err(st.parent, tens, ref.tensors, log_norm, 0.0)
-        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "applications/s",
+        n_or, t_sum = 1, t_or
+        while t_sum < 20.0 and n_or < len(probs):
+            t_sum += oracle_time(probs[n_or])[0]
+            n_or += 1
+        line["cpu_baseline"] = {"value": n_or / t_sum, "unit": "applications/s",
                                 "cores": blas_threads(), "kind": "oracle",
-                                "sample": "one full application of the workload (seed 0)"}
+                                "sample": f"full applications of instances 0..{n_or - 1} of the "
+                                          f"step (seeds {rank * B}..{rank * B + n_or - 1})"}
     if last is not None:
         destroy(last)
 
@@ -398,7 +442,8 @@ def main():
         pins = [([torch.from_numpy(t).pin_memory().numpy() for t in p.state.tensors],
                  [torch.from_numpy(t).pin_memory().numpy() for t in p.op.tensors]) for p in probs]
         h2d = sum(sum(t.nbytes for t in a) + sum(t.nbytes for t in b) for a, b in pins)
-        shape = _cbc.output_shape_fn(st.parent, st.phys)
+        shapes = [_cbc.output_shape_fn(p.state.parent, p.state.phys) for p in probs]
+        cplxs = [bool(np.iscomplexobj(p.state.tensors[0])) for p in probs]
         d2h = 0
         e2e_t = 0.0
         n_e2e = max(2, args.steps)
@@ -415,8 +460,8 @@ def main():
             else:
                 outs = _cbc.cbc_apply_batched(ha, hb, [p.max_bond for p in probs], [0.0] * B, opt)
             d2h = 0
-            for o in outs:
-                tens, bonds, _ = _cbc.fetch_network(o, shape, True)
+            for o, shp, cx in zip(outs, shapes, cplxs):
+                tens, bonds, _ = _cbc.fetch_network(o, shp, cx)
                 d2h += sum(t.nbytes for t in tens)
             e2e_t += time.perf_counter() - t0
             destroy(outs + ha)

@@ -200,7 +200,7 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
 }
 
 // S (m x n, row-major) -> Q with orthonormal rows spanning the row space of S, in place
-// (CholeskyQR2; Eq. (tt_cbc_qr_decomp) is the LQ on chi_{i-1}).  Requires m <= n.
+// (CholeskyQR2; Eq. (tt_cbc_qr_decomp) is the LQ on chi_{i-1}).  Used for m < n.
 // (nb instances: S m*n elements apart.)
 template <typename T>
 int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars& sc,
@@ -388,8 +388,10 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     // B3: S[chi, (sigma' chi')] = sum_{(b a)} L^[i-1][chi, (b a)] Z[(b a), (sigma' chi')]
     const int n = d * cp;
     const int m = c;
-    const int cn = (m <= n) ? m : n;
-    const bool formed = (i == 0 || m <= n);            // else Q is the identity
+    // at least as many rows as columns: every unitary Q spans the whole row space, so the
+    // identity is exact (and skips an ill-conditioned square CholeskyQR)
+    const int cn = (m < n) ? m : n;
+    const bool formed = (i == 0 || m < n);             // else Q is the identity
     const int64_t nbs = formed ? (int64_t)m * n : (int64_t)n * n;  // node stride in the group
     T* node = nullptr;
     if (nb == 1) {  // built in the output tensor itself
@@ -427,7 +429,7 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
       break;
     }
     // B4: S = R Q on chi_{i-1}; Q^[i] is the new tensor
-    if (m <= n) {
+    if (m < n) {
       rc = lq_rows_inplace<T>(tmp, pr, node, m, n, sc, s);
       if (rc != CBC_OK) return rc;
     } else {  // more rows than columns: any unitary basis of the columns; take the identity
@@ -729,14 +731,14 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
     const int nba = (int)(op.bond[i] * st.bond[i]);
     const int m = (int)chi_down[i];
     const int nzi = (int)nz;
-    const int cn = (m <= nzi) ? m : nzi;
+    const int cn = (m < nzi) ? m : nzi;  // square or tall: Q = I (exact, as on chains)
     T* node = nullptr;
     CK(cudaMallocAsync(reinterpret_cast<void**>(&node),
                        sizeof(T) * std::max<size_t>((size_t)cn * nzi, (size_t)m * nzi), s));
     out->data[i] = node;
     out->numel[i] = (int64_t)cn * nzi;
     // S^[i] = L^[(p_i, i)] contracted with Z over (b_p, a_p)
-    if (i == st.root || m <= nzi)
+    if (i == st.root || m < nzi)
       CK(tgemm<T>(pr, false, false, m, nzi, nba, Ldown[i], View::rowmajor(nba), false, Z.p,
                   View::transposed(nba), false, node, View::rowmajor(nzi), s));
     if (i == st.root) {
@@ -744,7 +746,7 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
       out->bond[i] = 1;
       continue;
     }
-    if (m <= nzi) {
+    if (m < nzi) {
       rc = lq_rows_inplace<T>(ar, pr, node, m, nzi, sc, s);
       if (rc != CBC_OK) return rc;
     } else {
