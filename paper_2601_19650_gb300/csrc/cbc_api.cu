@@ -255,8 +255,16 @@ static int parse_options(const cbc_options* opt, Options* o) {
   return CBC_OK;
 }
 
+static int apply_one(ttn_t state, ttno_t op, int64_t max_bond, double tol,
+                     const cbc_options* opt, bool concurrent, ttn_t* out);
+
 int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_options* opt,
               ttn_t* out) {
+  return apply_one(state, op, max_bond, tol, opt, false, out);
+}
+
+static int apply_one(ttn_t state, ttno_t op, int64_t max_bond, double tol,
+                     const cbc_options* opt, bool concurrent, ttn_t* out) {
   if (!out) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: out is NULL");
   *out = nullptr;
   if (!state || !op) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: NULL network");
@@ -267,6 +275,7 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_op
   Options o;
   int prc = parse_options(opt, &o);
   if (prc != CBC_OK) return prc;
+  o.concurrent = concurrent;
   auto* res = new cbc_ttn_s();
   int rc = run_cbc(*state, *op, max_bond, tol, o, res);
   if (rc != CBC_OK) {
@@ -326,9 +335,10 @@ int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64
   cudaGetDevice(&dev);
   std::vector<int> rc(n, CBC_OK);
   std::vector<std::string> msg(n);
+  const bool concurrent = workers > 1;
   auto one = [&](int j) {
-    rc[j] = cbc_apply(states[j], ops[j], max_bond ? max_bond[j] : 0, tol ? tol[j] : 0.0, opt,
-                      &outs[j]);
+    rc[j] = apply_one(states[j], ops[j], max_bond ? max_bond[j] : 0, tol ? tol[j] : 0.0, opt,
+                      concurrent, &outs[j]);
     if (rc[j] != CBC_OK) msg[j] = g_last_error;
   };
   auto group = [&](const std::vector<int>& t) {

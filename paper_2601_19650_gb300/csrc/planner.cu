@@ -179,7 +179,7 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
   }
   // the mixed path reduces to tridiagonal form in double-float arithmetic
   CK(heev_top<T>(K, g, kmax, max_bond, tol, floor_rel, lam, U, sc.k, work, sc.status, num_sms(),
-                 s, nb, false, pr.mixed));
+                 s, nb, o.concurrent, pr.mixed));
   int k = 0;
   int rc = read_k(sc, s, nb, &k);
   if (rc != CBC_OK) return rc;

@@ -32,6 +32,10 @@ struct Options {
   double eps_rank = 1e-6;
   int slices_fwd = 5;
   int slices_bwd = 4;
+  // set for instances that run next to others on their own streams (cbc_apply_batched):
+  // kernels whose CTAs wait on each other then use cluster launches, which run
+  // concurrently with other streams' work, instead of cooperative ones, which do not
+  bool concurrent = false;
 };
 
 int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
