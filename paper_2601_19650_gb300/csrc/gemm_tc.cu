@@ -23,13 +23,15 @@
 // [Re C, Im C] interleaved along N: the 4 real products of a complex product in one
 // real GEMM.
 //
-// Kernel: one 128 x BN output tile per CTA (cta_group::1), 6 warps: warp 0 issues TMA
-// loads of 64-wide K atoms (S slices of A and of B per atom, 128B swizzle, two smem
-// stages), warp 1 issues tcgen05.mma (one elected thread) into S TMEM accumulators per
-// chunk, double buffered so the epilogue of chunk c overlaps the MMAs of chunk c+1,
-// warps 2-5 drain TMEM (tcgen05.ld) into int64 registers and finally write FP64.
-// Every wait is bounded (clock64); a timeout raises CBC_ERR_TIMEOUT in the status
-// word, all roles leave their loops, and TMEM is freed before the CTA exits.
+// Kernel: persistent, one CTA per SM (cta_group::1) looping over 128 x BN output tiles of
+// all the problems of a call (a lockstep group of CBC instances is one call).  Warp 0
+// issues TMA loads of 64-wide K atoms (S slices of A and of B per atom, 128B swizzle,
+// two smem stages), warp 1 issues tcgen05.mma (one elected thread) into S TMEM
+// accumulators per K chunk, double buffered across chunks and tiles so the epilogue of
+// one chunk overlaps the MMAs of the next, and 4 (BN = 32) or 8 (BN = 64) epilogue warps
+// drain TMEM (tcgen05.ld) into int64 registers and write FP64, assembled with integer
+// operations.  Every wait is bounded (clock64); a timeout raises CBC_ERR_TIMEOUT in the
+// status word, all roles leave their loops, and TMEM is freed before the CTA exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
