@@ -140,6 +140,15 @@ int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(409
 }  // namespace
 
 cudaError_t allow_max_smem(const void* func) {
+  // once per kernel: the attribute call takes a driver lock and costs microseconds, and
+  // the planners ask before many launches
+  static std::mutex mu;
+  static std::vector<const void*> done;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (const void* f : done)
+      if (f == func) return cudaSuccess;
+  }
   static int optin = 0;
   if (optin == 0) {
     int dev = 0, v = 0;
@@ -150,8 +159,13 @@ cudaError_t allow_max_smem(const void* func) {
   cudaFuncAttributes fa;
   cudaError_t e = cudaFuncGetAttributes(&fa, func);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              optin - (int)fa.sharedSizeBytes);
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    done.push_back(func);
+  }
+  return e;
 }
 
 // Largest cluster size <= want (at most 16) for which one cluster of `func` with this
