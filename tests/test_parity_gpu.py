@@ -228,6 +228,17 @@ def test_group_lockstep(precision, bar, count):
     assert stats["eig"]["groups"] == L - 1, stats["eig"]
 
 
+@pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
+def test_group_wide_batch(precision, bar):
+    # 20 instances keeping 128 eigenvectors at the middle cuts: enough CTAs for the
+    # 32-vectors-per-CTA back transformation (double-float in the mixed path), one CTA
+    # per matrix for the Cholesky, clusters for the tridiagonal reduction
+    probs = [make_problem(2, seed=60 + j, L=16, chi=64, D=4, max_bond=128) for j in range(20)]
+    res, stats = _apply_batched(probs, precision)
+    _check_against_oracle(probs, res, bar)
+    assert stats["eig"]["groups"] == 16 - 1, stats["eig"]
+
+
 def test_group_mixed_shapes_and_real():
     # two shapes interleaved (two groups) plus a real-valued group
     probs = [make_problem(2, seed=30 + j, L=7 + (j % 2), chi=12, D=3, max_bond=10)
