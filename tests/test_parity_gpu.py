@@ -151,6 +151,20 @@ def test_batched_heterogeneous(precision, bar):
 
 
 # ---------------------------------------------------------------------------------------
+# the paper's own benchmark shape (Sec. IV A): MPS L=50, d=3, D_S=D_O=40, complex entries
+# with Re, Im ~ U[-0.5, 1], swept over the target bond
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("max_bond", [4, 16, 40])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_paper_benchmark_shape(max_bond, precision):
+    p = make_problem("P", max_bond=max_bond)
+    if precision == 0:
+        _compare(p)
+    else:
+        _compare_mixed(p)
+
+
+# ---------------------------------------------------------------------------------------
 # large bonds: the paths for matrices too large for shared memory
 # ---------------------------------------------------------------------------------------
 @pytest.mark.parametrize("precision", [0, 1])
