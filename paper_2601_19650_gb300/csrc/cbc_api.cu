@@ -9,6 +9,7 @@
 #include <cstring>
 #include <atomic>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -63,11 +64,34 @@ static size_t dtype_bytes(int dt) {
   }
 }
 
+// Stream-ordered allocations come from the device's default memory pool.  With its
+// default release threshold (0) every stream synchronisation returns the pool's free
+// memory to the driver, and the next allocation maps it again; the sweeps synchronise
+// once per compressed bond and allocate per site, so the library keeps freed memory
+// in the pool instead (a property of this process's pool only).
+static void keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  for (int d : done)
+    if (d == dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
 static int build_network(Net* net, int kind, int n_nodes, const int32_t* parent,
                          const int64_t* phys_dim, const int64_t* bond_dim, int dtype,
                          const void* const* node_data, int data_on_device, void* stream) {
   if (n_nodes < 1 || !parent || !phys_dim || !bond_dim || !node_data)
     return fail(CBC_ERR_INVALID_ARG, "create: null argument or n_nodes < 1");
+  keep_pool_memory();
   if (!valid_dtype(dtype)) return fail(CBC_ERR_INVALID_ARG, "create: bad dtype %d", dtype);
   net->kind = kind;
   net->n = n_nodes;
@@ -104,29 +128,43 @@ static int build_network(Net* net, int kind, int n_nodes, const int32_t* parent,
   net->data.assign(n_nodes, nullptr);
   net->numel.assign(n_nodes, 0);
   cudaStream_t s = net->stream;
-  const size_t es = net->elem_bytes();
+  const size_t es = net->elem_bytes(), hs = dtype_bytes(dtype);
+  // one allocation for all node tensors (and one staging buffer for host input), node i
+  // at element offset off[i] (multiples of 32 elements, so every node starts 256-byte
+  // aligned in FP64 storage): a few runtime calls per network instead of five per node
+  std::vector<int64_t> off(n_nodes + 1, 0);
   for (int i = 0; i < n_nodes; ++i) {
     int64_t ne = net->bond[i] * net->phys[i] * (kind == 1 ? net->phys[i] : 1);
     for (int c : net->children[i]) ne *= net->bond[c];
     net->numel[i] = ne;
-    cudaError_t e = cudaMallocAsync(&net->data[i], ne * es, s);
-    if (e != cudaSuccess) return cuda_fail(e, "create: device allocation");
-    const void* src = node_data[i];
-    void* staging = nullptr;
-    if (!data_on_device) {
-      e = cudaMallocAsync(&staging, ne * dtype_bytes(dtype), s);
-      if (e != cudaSuccess) return cuda_fail(e, "create: staging alloc");
-      e = cudaMemcpyAsync(staging, src, ne * dtype_bytes(dtype), cudaMemcpyHostToDevice, s);
-      if (e != cudaSuccess) return cuda_fail(e, "create: H2D copy");
-      src = staging;
-    }
-    e = widen_to_f64(src, dtype, net->data[i], ne, s);
-    if (e != cudaSuccess) return cuda_fail(e, "create: widen");
-    if (staging) cudaFreeAsync(staging, s);
+    off[i + 1] = off[i] + (ne + 31) / 32 * 32;
   }
+  const int64_t total = off[n_nodes];
+  cudaError_t e = cudaMallocAsync(&net->block, total * es, s);
+  if (e != cudaSuccess) {
+    net->block = nullptr;
+    return cuda_fail(e, "create: device allocation");
+  }
+  for (int i = 0; i < n_nodes; ++i) net->data[i] = static_cast<char*>(net->block) + off[i] * es;
   if (!data_on_device) {
-    cudaError_t e = cudaStreamSynchronize(s);
+    void* staging = nullptr;
+    e = cudaMallocAsync(&staging, total * hs, s);
+    if (e != cudaSuccess) return cuda_fail(e, "create: staging alloc");
+    for (int i = 0; i < n_nodes && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(static_cast<char*>(staging) + off[i] * hs, node_data[i],
+                          net->numel[i] * hs, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "create: H2D copy");
+    // one widening pass over all nodes (the padding between them is never read)
+    e = widen_to_f64(staging, dtype, net->block, total, s);
+    if (e != cudaSuccess) return cuda_fail(e, "create: widen");
+    cudaFreeAsync(staging, s);
+    e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "create: synchronize");
+  } else {
+    for (int i = 0; i < n_nodes; ++i) {
+      e = widen_to_f64(node_data[i], dtype, net->data[i], net->numel[i], s);
+      if (e != cudaSuccess) return cuda_fail(e, "create: widen");
+    }
   }
   return CBC_OK;
 }
@@ -134,11 +172,16 @@ static int build_network(Net* net, int kind, int n_nodes, const int32_t* parent,
 // node tensors are stream-ordered allocations on the network's stream
 Net::~Net() {
   bool any = false;
-  for (void* p : data)
-    if (p) {
-      cudaFreeAsync(p, stream);
-      any = true;
-    }
+  if (block) {
+    cudaFreeAsync(block, stream);
+    any = true;
+  } else {
+    for (void* p : data)
+      if (p) {
+        cudaFreeAsync(p, stream);
+        any = true;
+      }
+  }
   if (any) cudaStreamSynchronize(stream);
 }
 
@@ -266,6 +309,7 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_op
 static int apply_one(ttn_t state, ttno_t op, int64_t max_bond, double tol,
                      const cbc_options* opt, bool concurrent, ttn_t* out) {
   if (!out) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: out is NULL");
+  keep_pool_memory();
   *out = nullptr;
   if (!state || !op) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: NULL network");
   if (state->kind != 0 || op->kind != 1) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: wrong handle kinds");
@@ -292,6 +336,7 @@ int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply_batched: bad arguments");
   for (int j = 0; j < n; ++j) outs[j] = nullptr;
   if (n == 0) return CBC_OK;
+  keep_pool_memory();
   // groups: chains with identical shapes, max_bond and tol (at most kMaxGroup each) run
   // in lockstep, one launch per step for the whole group; the rest one by one
   constexpr int kMaxGroup = 32;

@@ -21,6 +21,7 @@ struct Net {
   bool cplx = false;
   std::vector<void*> data;
   std::vector<int64_t> numel;
+  void* block = nullptr;  // when set, data[i] point into this one allocation
   double log_norm = 0.0;
   cudaStream_t stream = nullptr;
   size_t elem_bytes() const { return cplx ? 16 : 8; }
