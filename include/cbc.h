@@ -153,6 +153,14 @@ int ttn_get_info(ttn_t t, int32_t* n_nodes_out, int64_t* bond_dims_out,
  *         complex network; CBC_F64 for a real one; lower precisions are rounded).   */
 int ttn_get_node(ttn_t t, int node, void* dst, int dst_on_device, int dtype);
 
+/* Copy every node tensor out at once (one synchronisation of the stream): node 0, then
+ * node 1, ..., each in the leg order above, back to back without padding.
+ *   dst   host (dst_on_device == 0) or device pointer with room for the sum over nodes
+ *         of the node sizes (ttn_get_info gives the bonds), element type `dtype` as for
+ *         ttn_get_node.
+ * Errors: CBC_ERR_INVALID_ARG (NULL handle or pointer, dtype), CBC_ERR_CUDA.        */
+int ttn_get_network(ttn_t t, void* dst, int dst_on_device, int dtype);
+
 int ttn_destroy(ttn_t t);   /* NULL is a no-op */
 int ttno_destroy(ttno_t t); /* NULL is a no-op */
 

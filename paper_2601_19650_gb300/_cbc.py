@@ -67,6 +67,7 @@ def lib():
         L.cbc_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
         L.ttn_get_info.argtypes = [vp, P(i32), P(i64), P(dbl)]
         L.ttn_get_node.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
+        L.ttn_get_network.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
         L.ttn_destroy.argtypes = [vp]
         L.ttno_destroy.argtypes = [vp]
         L.cbc_apply_tt_noalloc.argtypes = [ctypes.c_int, P(i64), P(i64), P(i64), ctypes.c_int,
@@ -88,7 +89,7 @@ def lib():
         L.cbc_last_error.restype = ctypes.c_char_p
         L.cbc_last_error.argtypes = []
         for f in ("ttn_create", "ttno_create", "cbc_apply", "ttn_get_info", "ttn_get_node",
-                  "ttn_destroy", "ttno_destroy"):
+                  "ttn_get_network", "ttn_destroy", "ttno_destroy"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -253,14 +254,19 @@ def create_from_device(parent, phys, bond, tensors, kind: str = "state", stream=
 
 
 def fetch_network(t, shapes_of_node, cplx: bool):
-    """Copy every node of a TTNS handle to host (FP64 / complex128) -> (tensors, bonds, log_norm)."""
+    """Copy every node of a TTNS handle to host (FP64 / complex128) -> (tensors, bonds, log_norm).
+
+    One ttn_get_network call into one host buffer; the tensors are views of it."""
     n, bonds, log_norm = ttn_get_info(t)
-    out = []
-    for i in range(n):
-        shape = shapes_of_node(i, bonds)
-        a = np.empty(shape, dtype=np.complex128 if cplx else np.float64)
-        ttn_get_node(t, i, a.ctypes.data, False, CBC_C128 if cplx else CBC_F64)
-        out.append(a)
+    shapes = [shapes_of_node(i, bonds) for i in range(n)]
+    sizes = [int(np.prod(sh)) for sh in shapes]
+    buf = np.empty(sum(sizes), dtype=np.complex128 if cplx else np.float64)
+    _check(lib().ttn_get_network(t, ctypes.c_void_p(buf.ctypes.data), 0,
+                                 CBC_C128 if cplx else CBC_F64))
+    out, off = [], 0
+    for sh, sz in zip(shapes, sizes):
+        out.append(buf[off:off + sz].reshape(sh))
+        off += sz
     return out, bonds, log_norm
 
 

@@ -286,6 +286,43 @@ int ttn_get_node(ttn_t t, int node, void* dst, int dst_on_device, int dtype) {
   return CBC_OK;
 }
 
+int ttn_get_network(ttn_t t, void* dst, int dst_on_device, int dtype) {
+  if (!t || !dst) return fail(CBC_ERR_INVALID_ARG, "ttn_get_network: NULL argument");
+  if (!valid_dtype(dtype)) return fail(CBC_ERR_INVALID_ARG, "ttn_get_network: bad dtype");
+  bool want_c = (dtype == CBC_C64 || dtype == CBC_C128);
+  if (want_c != t->cplx)
+    return fail(CBC_ERR_INVALID_ARG, "ttn_get_network: dtype must be %s for this network",
+                t->cplx ? "complex" : "real");
+  cudaStream_t s = t->stream;
+  const size_t hs = dtype_bytes(dtype);
+  int64_t total = 0;
+  for (int i = 0; i < t->n; ++i) total += t->numel[i];
+  // every node into one device buffer (the destination itself when it is on the device),
+  // then one copy to the host and one synchronisation
+  char* gather = static_cast<char*>(dst);
+  cudaError_t e = cudaSuccess;
+  if (!dst_on_device) {
+    e = cudaMallocAsync(reinterpret_cast<void**>(&gather), total * hs, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ttn_get_network: alloc");
+  }
+  int64_t off = 0;
+  for (int i = 0; i < t->n && e == cudaSuccess; ++i) {
+    if (dtype == CBC_F64 || dtype == CBC_C128)
+      e = cudaMemcpyAsync(gather + off * hs, t->data[i], t->numel[i] * hs,
+                          cudaMemcpyDeviceToDevice, s);
+    else
+      e = narrow_from_f64(t->data[i], t->cplx, gather + off * hs, dtype, t->numel[i], s);
+    off += t->numel[i];
+  }
+  if (e == cudaSuccess && !dst_on_device)
+    e = cudaMemcpyAsync(dst, gather, total * hs, cudaMemcpyDeviceToHost, s);
+  if (!dst_on_device) cudaFreeAsync(gather, s);
+  if (e != cudaSuccess) return cuda_fail(e, "ttn_get_network: copy");
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "ttn_get_network: synchronize");
+  return CBC_OK;
+}
+
 static int parse_options(const cbc_options* opt, Options* o) {
   if (opt) {
     o->precision = opt->precision;
