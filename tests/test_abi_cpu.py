@@ -66,6 +66,14 @@ def test_library_loads_and_rejects_bad_arguments(libpath):
     rc = L.ttn_create(1, par, d1, d1, 9, p1, 1, None, ctypes.byref(out))
     assert rc == 1 and "dtype" in _cbc.cbc_last_error()
     assert L.ttn_destroy(None) == 0 and L.ttno_destroy(None) == 0
+    # fetching from a NULL handle, into a NULL buffer
+    buf = (ctypes.c_double * 4)()
+    assert L.ttn_get_network(None, buf, 0, 1) == 1
+    assert "NULL" in _cbc.cbc_last_error()
+    assert L.ttn_get_node(None, 0, buf, 0, 1) == 1
+    # an empty batch is a no-op; a batch with NULL arrays is rejected
+    assert L.cbc_apply_batched(0, None, None, None, None, None, 0, None) == 0
+    assert L.cbc_apply_batched(2, None, None, None, None, None, 0, None) == 1
 
 
 def test_build_targets_sm103a_only():
