@@ -148,3 +148,43 @@ def chain_left_block(state, op, i: int) -> np.ndarray:
         O = O.transpose(0, 2, 1, 3, 4).reshape(nout * w.shape[1], nin * w.shape[2], w.shape[3])
     B = np.einsum("Psb,sa->Pab", O, psi)
     return B.reshape(B.shape[0], -1)
+
+
+def edge_block(parent, state, op, k: int, side: str) -> np.ndarray:
+    """Dense block of ``O |psi>`` on one side of the edge between node ``k`` and its parent.
+
+    ``side="sub"`` takes the nodes of the subtree of ``k``, ``side="rest"`` all the other
+    nodes.  The result is the matrix ``B[(sigma'_j, j in the block, ascending), (alpha, beta)]``
+    with ``(alpha, beta)`` the state and operator bonds of that edge left open, i.e. the
+    block of the exact network (Eqs. (ttns), (ttno)) that a compression of that edge sees:
+    ``B^H B`` is the exact Gram on the edge from that side (Sec. III B, steps 1 and 2)."""
+    parent = [int(p) for p in parent]
+    n = len(parent)
+    ch = _children(parent)
+    sub = set(_subtree(parent, k))
+    nodes = sorted(sub) if side == "sub" else [j for j in range(n) if j not in sub]
+    if side not in ("sub", "rest") or parent[k] < 0:
+        raise ValueError("edge_block: need a non-root node and side 'sub' or 'rest'")
+    inset = set(nodes)
+    nxt = [0]
+
+    def lab():
+        nxt[0] += 1
+        return nxt[0] - 1
+
+    ls = {j: lab() for j in nodes}            # sigma_j
+    lso = {j: lab() for j in nodes}           # sigma'_j
+    la = {j: lab() for j in range(n) if parent[j] >= 0}   # alpha on edge (j, parent j)
+    lb = {j: lab() for j in range(n) if parent[j] >= 0}   # beta on edge (j, parent j)
+    st_ops, op_ops = [], []
+    for j in nodes:
+        pa = la[j] if parent[j] >= 0 else lab()   # the root's parent leg has dimension 1
+        pb = lb[j] if parent[j] >= 0 else lab()
+        st_ops += [np.asarray(state[j]), [pa, ls[j]] + [la[c] for c in ch[j]]]
+        op_ops += [np.asarray(op[j]), [pb, lso[j], ls[j]] + [lb[c] for c in ch[j]]]
+        for c in ch[j]:
+            assert (c in inset) or c == k
+    psi = np.einsum(*st_ops, [ls[j] for j in nodes] + [la[k]], optimize=True)
+    B = np.einsum(*op_ops, psi, [ls[j] for j in nodes] + [la[k]],
+                  [lso[j] for j in nodes] + [la[k], lb[k]], optimize=True)
+    return B.reshape(-1, B.shape[-2] * B.shape[-1])

@@ -105,7 +105,8 @@ class CBCResult:
     forward_cuts: List[CutInfo]        # compressions of the first sweep(s)
     env_ranks: List[int]               # chi_i of the environments
     out_bonds: List[int]               # bond of each node to its parent in the output
-    envs: Optional[list] = None        # environments kept for checking (TT: L^[i])
+    envs: Optional[object] = None      # environments kept for checking (TT: list of L^[i];
+                                       # trees: {"sub": L^[i], "down": L^[(p_k, k)]} by node)
 
 
 def _as_tt(state, op):
@@ -326,7 +327,7 @@ def cbc_tree(parent, state: List[np.ndarray], op: List[np.ndarray], max_bond: in
         R[i] = _contract(ops, [_X_NEW, _A_P, _B_P])
     bonds = [int(out[i].shape[0]) for i in range(n)]
     ranks = [int(Lsub[i].shape[0]) for i in sorted(Lsub)]
-    return CBCResult(out, cuts, ranks, bonds)
+    return CBCResult(out, cuts, ranks, bonds, {"sub": Lsub, "down": Ldown})
 
 
 def cbc(parent, state, op, max_bond: int = 0, tol: float = 0.0,

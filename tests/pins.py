@@ -212,8 +212,66 @@ def check_first_cut_keeps_dominant_gram(cbc_mod):
         assert done, p.name
 
 
+def _best_rank_k_gram(B, max_bond):
+    """Numerical rank of B, the rank k = min(max_bond, rank), and the best rank-k part
+    of B^H B from the SVD of B (Eckart-Young), scaled by the largest singular value."""
+    _, s, Vh = np.linalg.svd(B, full_matrices=False)
+    rank = int(np.count_nonzero(s > 1e-10 * s[0]))
+    k = min(int(max_bond), rank) if max_bond > 0 else rank
+    Gk = (Vh[:k].conj().T * s[:k] ** 2) @ Vh[:k]
+    return rank, k, Gk, s[0] ** 2
+
+
+def check_tree_cuts_keep_dominant_gram(cbc_mod):
+    """On a branching tree, every compression whose inputs are all exact (nothing was
+    truncated in the environments it contracts) keeps the best rank-k part of the exact
+    Gram of its block of O|psi>, built by brute force: step 1 (Eq.
+    (cbc_tree_first_contraction)) sees the subtree of the edge, step 2 (Eq.
+    (cbc_tree_second_contraction)) everything else (Sec. III B).  At least one truncated
+    step-1 cut and one truncated step-2 cut must be checked."""
+    cases = [make_problem(3, L=2, chi=6, D=3, max_bond=1, dtype=np.complex128, seed=5),
+             make_problem(3, L=2, chi=6, D=3, max_bond=4, dtype=np.complex128, seed=6),
+             make_problem(3, topo="ttree", L=2, d=2, chi=4, D=2, max_bond=3,
+                          dtype=np.complex128, seed=4)]
+    trunc = {"sub": 0, "rest": 0}
+    for p in cases:
+        par = [int(x) for x in p.state.parent]
+        ch = p.state.children
+        r = cbc_mod.cbc_tree(par, p.state.tensors, p.op.tensors, p.max_bond)
+        envs = r.envs
+
+        def check(env, k_node, side):
+            B = brute.edge_block(par, p.state.tensors, p.op.tensors, k_node, side)
+            rank, k, Gk, s0 = _best_rank_k_gram(B, p.max_bond)
+            e = np.asarray(env).reshape(np.asarray(env).shape[0], -1)
+            assert e.shape[0] == k, (p.name, side, k_node, e.shape, k, rank)
+            err = np.abs(e.conj().T @ e - Gk).max() / s0
+            assert err < 1e-11, (p.name, side, k_node, err)
+            if k < rank:
+                trunc[side] += 1
+            return k == rank
+
+        exact_sub = {}
+        post = [v for v in cbc_mod._postorder(par)]
+        root = post[-1]
+        for i in post:
+            if i == root:
+                continue
+            if all(exact_sub[c] for c in ch[i]):
+                exact_sub[i] = check(envs["sub"][i], i, "sub")
+            else:
+                exact_sub[i] = False
+        exact_down = {root: True}
+        for i in reversed(post):
+            for k in ch[i]:
+                ok_in = exact_down[i] and all(exact_sub[c] for c in ch[i] if c != k)
+                exact_down[k] = check(envs["down"][k], k, "rest") if ok_in else False
+    assert trunc["sub"] > 0 and trunc["rest"] > 0, trunc
+
+
 ALL_CHECKS = [
     check_first_cut_keeps_dominant_gram,
+    check_tree_cuts_keep_dominant_gram,
     check_exact_without_truncation,
     check_eckart_young,
     check_projection,

@@ -30,6 +30,14 @@ MUTATIONS = {
                                   'env_ops = [Lsub.get(i, Ldown[i]), [_X_P, _A_P, _B_P]]'),
     "lq-uses-transpose-not-adjoint": ('np.linalg.qr(S.conj().T, mode="reduced")',
                                       'np.linalg.qr(S.T, mode="reduced")'),
+    # caught only by the dense-Gram pin on branching trees (isometries, projection and
+    # exactness still hold: the truncation just keeps a worse subspace)
+    "tree-step1-child-env-conjugated": (
+        '            ops += [Lsub[c], [_x(j), _a(j), _b(j)]]\n        out_legs = [_S_OUT]',
+        '            ops += [Lsub[c].conj(), [_x(j), _a(j), _b(j)]]\n        out_legs = [_S_OUT]'),
+    "tree-step2-sibling-env-conjugated": (
+        'if c != k:\n                    ops += [Lsub[c], ',
+        'if c != k:\n                    ops += [Lsub[c].conj(), '),
 }
 
 
