@@ -33,6 +33,10 @@
  * in a status word and reported by the next call that synchronises (cbc_apply,
  * ttn_get_node, ttn_get_info).
  *
+ * Device memory: stream-ordered allocations (networks, per-call workspaces) come from a
+ * memory pool the library creates for itself on each device, which keeps freed memory
+ * for reuse; the device's default memory pool is neither used nor reconfigured.
+ *
  * Status: every function returns 0 (CBC_OK) or a positive cbc_status code; a message
  * for the calling thread is available from cbc_last_error().  No entry point aborts,
  * traps or leaves the process in an undefined state on bad input.
@@ -78,7 +82,9 @@ typedef struct cbc_options {
   int slices_fwd;    /* mixed: bf16 slices per operand in the first sweep(s) (0 = 5) */
   int slices_bwd;    /* mixed: bf16 slices per operand in the last sweep (0 = 4)     */
   int reserved_i;
-  double eps_rank;   /* singular values s_j <= eps_rank * s_0 are dropped (<=0: 1e-6) */
+  double eps_rank;   /* singular values s_j <= eps_rank * s_0 are dropped (<= 0: the
+                        default, 1e-12 for CBC_PREC_FP64 as in the FP64 reference, 1e-9
+                        for CBC_PREC_MIXED, whose products resolve s only to ~3e-11 s_0) */
   double reserved_d[3];
 } cbc_options;
 
@@ -114,8 +120,13 @@ int ttno_create(int n_nodes, const int32_t* parent, const int64_t* phys_dim,
  *             isometries toward the root (the Q^[i] of Eqs. (tt_cbc_qr_decomp),
  *             (cbc_tree_qr)); the root holds S^[root] divided by exp(log_norm)
  *             (ttn_get_info), so |psi'> = exp(log_norm) * network.
+ * Truncation: the candidate directions of each compression come from the Gram matrix
+ * and an eigensolver; the rank rule runs on weights measured on the factor itself
+ * (||u_j^H M||^2 and, with tol > 0, the exact weight outside the candidates), and
+ * directions the rule keeps below the Gram's resolution (weight < 1e-10 of the largest
+ * in FP64, 1e-8 in the mixed path) are recomputed from the Gram of the residual.
  * The call is stream ordered; it synchronises the stream once per compressed bond to
- * read the rank chosen on the device.  State and op are not modified.
+ * read the weights back.  State and op are not modified.
  * Errors: CBC_ERR_INVALID_ARG, CBC_ERR_TOPOLOGY_MISMATCH, CBC_ERR_OOM,
  * CBC_ERR_NOT_POSITIVE_DEFINITE, CBC_ERR_NUMERICAL, CBC_ERR_TIMEOUT, CBC_ERR_CUDA,
  * CBC_ERR_UNSUPPORTED.  On error *out is left NULL and nothing leaks.               */
@@ -143,9 +154,15 @@ int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64
 /* Information about a TTNS (synchronises its stream).
  *   n_nodes_out     may be NULL
  *   bond_dims_out   NULL or [n_nodes]: bond of each node to its parent (1 at the root)
- *   log_norm_out    NULL or scalar: the network is scaled by exp(*log_norm_out)      */
+ *   log_norm_out    NULL or scalar: the network is scaled by exp(*log_norm_out)
+ *   discarded_weight_out  NULL or [n_nodes]: for a result of cbc_apply, the relative
+ *                   weight sum_{j>=k} s_j^2 / sum_j s_j^2 that the compression of the
+ *                   edge from node i to its parent dropped (Sec. III A truncation; on a
+ *                   chain the forward sweep's cut, on a tree the sum of the step-1 and
+ *                   step-2 compressions of that edge); 0 at the root and for networks
+ *                   made by ttn_create                                               */
 int ttn_get_info(ttn_t t, int32_t* n_nodes_out, int64_t* bond_dims_out,
-                 double* log_norm_out);
+                 double* log_norm_out, double* discarded_weight_out);
 
 /* Copy one node tensor out (synchronises the stream).
  *   dst   host (dst_on_device == 0) or device pointer with room for the node tensor
@@ -172,11 +189,51 @@ int ttno_destroy(ttno_t t); /* NULL is a no-op */
  *              result (see cbc_apply)
  *   M, N, K    op(A) is M x K, op(B) is K x N, C is M x N (ldc >= N), K >= 1
  *   lda, ldb   leading dimensions of A and B as stored
- * Stream ordered on `stream`; allocates its workspace with cudaMallocAsync on it.
+ * Stream ordered on `stream`; allocates its workspace stream-ordered on it.
  * Errors: CBC_ERR_INVALID_ARG, CBC_ERR_OOM, CBC_ERR_CUDA.                           */
 int cbc_gemm(int precision, int slices, int dtype, int M, int N, int K, const void* A,
              int64_t lda, int transA, int conjA, const void* B, int64_t ldb, int transB,
              int conjB, void* C, int64_t ldc, void* stream);
+
+/* Truncation eigensolver, exposed as a building block (and for kernel-level tests).
+ * The compression of Sec. III A keeps the dominant singular subspace of M; the sweeps
+ * reach it through the Hermitian Gram matrix K = M M^H and this solver (Householder
+ * reduction to tridiagonal form, Sturm multisection, inverse iteration, back
+ * transformation).
+ *   dtype    CBC_F64 or CBC_C128
+ *   m, kmax  A is m x m Hermitian; the eigenvectors of the kmax largest eigenvalues
+ *   nb       matrices in the batch, back to back (A: m*m apart, lam_out: m, U_out: m*kmax)
+ *   A        DEVICE, row-major, overwritten
+ *   lam_out  DEVICE, m doubles per matrix, descending: the first kmax are FP64 Rayleigh
+ *            quotients of the computed vectors, the rest single-precision estimates
+ *   U_out    DEVICE, m x kmax row-major per matrix, column j = eigenvector j
+ *   mixed    nonzero: the mixed path's double-float reduction (used for batches, nb > 1)
+ * Allocates its workspace stream-ordered on `stream` and synchronises it.
+ * Errors: CBC_ERR_INVALID_ARG, CBC_ERR_OOM, CBC_ERR_TIMEOUT, CBC_ERR_CUDA.            */
+int cbc_heev(int dtype, int m, int kmax, int nb, void* A, double* lam_out, void* U_out,
+             int mixed, void* stream);
+
+/* CholeskyQR2 of the backward sweep, exposed as a building block: the LQ of S on its row
+ * leg (Eq. (tt_cbc_qr_decomp); Eq. (cbc_tree_qr) on trees) by G = S S^H, G = C C^H,
+ * S <- C^{-1} S, twice, in FP64.
+ *   S      DEVICE, m x n row-major with 1 <= m <= n, nb matrices m*n apart; replaced by Q
+ *          with orthonormal rows spanning the row space of S
+ * Synchronises the stream.  Errors: CBC_ERR_INVALID_ARG, CBC_ERR_OOM,
+ * CBC_ERR_NOT_POSITIVE_DEFINITE (S rank deficient), CBC_ERR_TIMEOUT, CBC_ERR_CUDA.   */
+int cbc_cholqr2(int dtype, int m, int n, int nb, void* S, void* stream);
+
+/* Self-tests of device primitives the kernels rely on (no counterpart in the paper).
+ * cbc_selftest_math: for n DEVICE doubles x, writes to the DEVICE array out[4 n]
+ *   out[4i] = the library's Newton reciprocal of x_i (used where long chains of FP64
+ *   divisions would dominate), out[4i+1] = 1.0 / x_i computed by CUDA, out[4i+2] = the
+ *   library's Newton reciprocal square root (0 for x_i <= 0), out[4i+3] = CUDA's rsqrt.
+ * cbc_selftest_wait: runs the library's bounded device-side wait on a word that nothing
+ *   writes, with a limit of limit_cycles SM clock cycles; *returned_out = 1 when the
+ *   kernel gave up and returned.  Returns CBC_ERR_TIMEOUT in that (expected) case: every
+ *   wait of the library ends this way instead of hanging, and the context stays usable.
+ * Both synchronise the stream.                                                       */
+int cbc_selftest_math(const double* x_dev, double* out_dev, int64_t n, void* stream);
+int cbc_selftest_wait(long long limit_cycles, int* returned_out, void* stream);
 
 /* Launch statistics per kernel class, process wide, for benchmarks and profiling.
  * Launch counts are always kept.  With timing enabled, every group of launches of one
@@ -214,8 +271,9 @@ int cbc_stats_read(cbc_stats* out); /* synchronises the recorded events         
  * cudaMalloc (or any allocator) at the point where they need the application, e.g.
  * code running under a framework that owns every byte of device memory through its
  * own pool, or a real-time host loop in which allocation is forbidden after start-up.
- * It runs the same kernels as cbc_apply for a chain (Sec. III A, precision FP64), but
- * every intermediate lives in one library-owned scratch array of
+ * It runs the same sweeps and kernels as cbc_apply on a chain in precision FP64 (the
+ * same rank rule, and the identity as the new tensor wherever S has at least as many
+ * rows as columns), but every intermediate lives in one library-owned scratch array of
  * CBC_NOALLOC_SCRATCH_BYTES, a file-scope __device__ array that each GPU which loads
  * the library holds until the process exits.
  *
@@ -231,15 +289,20 @@ int cbc_stats_read(cbc_stats* out); /* synchronises the recorded events         
  *                (canonical layout, bonds out_bonds) starts at element out_offsets[i]
  *   out_offsets  [L] host, filled;  out_bonds [L] host, filled (1 at site 0)
  *   log_norm     host, filled: the result is exp(*log_norm) times the network
- *   cuda_stream  stream for all work (may be NULL); the call returns after it drained
+ *   cuda_stream  stream for all work (may be NULL)
+ * The call synchronises the stream once per compressed bond (it reads the chosen rank
+ * back to the host) and returns after the stream has drained, on success and on error.
  * The first call on a device looks up the device address of the scratch array on that
  * device (cudaGetSymbolAddress); make that first call before any stream capture.
  * Every call shares the one array and keeps nothing in it that a later call relies on
  * (it clears what must start at zero), so calls that overlap on the GPU, from several
- * threads or streams, race: serialise them.  A problem whose intermediates do not fit,
- * or a result larger than out_capacity, is rejected with CBC_ERR_INVALID_ARG and a
- * message naming the size it would need; nothing is launched for a problem rejected by
- * the up-front size check.                                                          */
+ * threads or streams, race: serialise them.
+ * Errors: CBC_ERR_INVALID_ARG for a NULL argument, a dimension < 1, a dimension product
+ * beyond 2^31 - 1, intermediates that do not fit the scratch array (checked before
+ * anything is launched; the message names the size needed) or a result larger than
+ * out_capacity (checked once the forward sweep has fixed the ranks, before the
+ * backward sweep writes anything; the message names the size needed); otherwise the
+ * statuses of cbc_apply.                                                            */
 #define CBC_NOALLOC_SCRATCH_BYTES (32u << 20)
 int cbc_apply_tt_noalloc(int L, const int64_t* phys_dim, const int64_t* state_bond,
                          const int64_t* op_bond, int dtype, const void* const* state_nodes,

@@ -65,7 +65,7 @@ def lib():
         L.ttn_create.argtypes = create_args
         L.ttno_create.argtypes = create_args
         L.cbc_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
-        L.ttn_get_info.argtypes = [vp, P(i32), P(i64), P(dbl)]
+        L.ttn_get_info.argtypes = [vp, P(i32), P(i64), P(dbl), P(dbl)]
         L.ttn_get_node.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
         L.ttn_get_network.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
         L.ttn_destroy.argtypes = [vp]
@@ -78,6 +78,15 @@ def lib():
                                ctypes.c_int, ctypes.c_int, vp, i64, ctypes.c_int, ctypes.c_int,
                                vp, i64, ctypes.c_int, ctypes.c_int, vp, i64, vp]
         L.cbc_gemm.restype = ctypes.c_int
+        L.cbc_heev.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp,
+                               vp, ctypes.c_int, vp]
+        L.cbc_heev.restype = ctypes.c_int
+        L.cbc_cholqr2.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.cbc_cholqr2.restype = ctypes.c_int
+        L.cbc_selftest_math.argtypes = [vp, vp, i64, vp]
+        L.cbc_selftest_math.restype = ctypes.c_int
+        L.cbc_selftest_wait.argtypes = [ctypes.c_longlong, P(ctypes.c_int), vp]
+        L.cbc_selftest_wait.restype = ctypes.c_int
         L.cbc_apply_batched.argtypes = [ctypes.c_int, P(vp), P(vp), P(i64), P(dbl),
                                         P(cbc_options), ctypes.c_int, P(vp)]
         L.cbc_apply_batched.restype = ctypes.c_int
@@ -188,6 +197,30 @@ def cbc_gemm(precision: int, slices: int, dtype: int, M: int, N: int, K: int, A_
                           int(ldc), ctypes.c_void_p(stream or 0)))
 
 
+def cbc_heev(dtype: int, m: int, kmax: int, nb: int, A_ptr: int, lam_ptr: int, U_ptr: int,
+             mixed: bool = False, stream=None):
+    _check(lib().cbc_heev(int(dtype), int(m), int(kmax), int(nb), ctypes.c_void_p(int(A_ptr)),
+                          ctypes.c_void_p(int(lam_ptr)), ctypes.c_void_p(int(U_ptr)),
+                          1 if mixed else 0, ctypes.c_void_p(stream or 0)))
+
+
+def cbc_cholqr2(dtype: int, m: int, n: int, nb: int, S_ptr: int, stream=None):
+    _check(lib().cbc_cholqr2(int(dtype), int(m), int(n), int(nb), ctypes.c_void_p(int(S_ptr)),
+                             ctypes.c_void_p(stream or 0)))
+
+
+def cbc_selftest_math(x_ptr: int, out_ptr: int, n: int, stream=None):
+    _check(lib().cbc_selftest_math(ctypes.c_void_p(int(x_ptr)), ctypes.c_void_p(int(out_ptr)),
+                                   int(n), ctypes.c_void_p(stream or 0)))
+
+
+def cbc_selftest_wait(limit_cycles: int, stream=None):
+    """Returns (status code, returned flag) of the bounded-wait self-test."""
+    ret = ctypes.c_int(0)
+    rc = lib().cbc_selftest_wait(int(limit_cycles), ctypes.byref(ret), ctypes.c_void_p(stream or 0))
+    return rc, ret.value
+
+
 def cbc_apply_batched(states, ops, max_bond, tol, opt: Optional[cbc_options] = None,
                       workers: int = 0):
     """Run len(states) independent applications concurrently; returns the output handles."""
@@ -205,11 +238,20 @@ def cbc_apply_batched(states, ops, max_bond, tol, opt: Optional[cbc_options] = N
 
 def ttn_get_info(t):
     n = ctypes.c_int32()
-    _check(lib().ttn_get_info(t, ctypes.byref(n), None, None))
+    _check(lib().ttn_get_info(t, ctypes.byref(n), None, None, None))
     bonds = (ctypes.c_int64 * n.value)()
     ln = ctypes.c_double()
-    _check(lib().ttn_get_info(t, None, bonds, ctypes.byref(ln)))
+    _check(lib().ttn_get_info(t, None, bonds, ctypes.byref(ln), None))
     return n.value, np.array(bonds[:], dtype=np.int64), ln.value
+
+
+def ttn_get_discarded(t):
+    """Relative discarded weight of the compression(s) of each node's parent edge."""
+    n = ctypes.c_int32()
+    _check(lib().ttn_get_info(t, ctypes.byref(n), None, None, None))
+    d = (ctypes.c_double * n.value)()
+    _check(lib().ttn_get_info(t, None, None, None, d))
+    return np.array(d[:], dtype=np.float64)
 
 
 def ttn_get_node(t, node: int, dst_ptr: int, dst_on_device: bool, dtype: int):

@@ -64,26 +64,43 @@ static size_t dtype_bytes(int dt) {
   }
 }
 
-// Stream-ordered allocations come from the device's default memory pool.  With its
-// default release threshold (0) every stream synchronisation returns the pool's free
-// memory to the driver, and the next allocation maps it again; the sweeps synchronise
-// once per compressed bond and allocate per site, so the library keeps freed memory
-// in the pool instead (a property of this process's pool only).
-static void keep_pool_memory() {
+// Stream-ordered allocations come from a memory pool the library creates for itself on
+// each device (never from the device's default pool, which other code in the process may
+// use with its own settings).  The sweeps synchronise once per compressed bond and
+// allocate per site; with a release threshold of 0 every synchronisation would hand the
+// pool's free memory back to the driver and the next allocation would map it again, so
+// the library's pool keeps freed memory (release threshold UINT64_MAX).
+cudaError_t cbc::pool_malloc(void** p, size_t bytes, cudaStream_t s) {
+  constexpr int kMaxDev = 64;
   static std::mutex mu;
-  static std::vector<int> done;
+  static cudaMemPool_t pools[kMaxDev] = {};
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return;
-  std::lock_guard<std::mutex> lk(mu);
-  for (int d : done)
-    if (d == dev) return;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
   cudaMemPool_t pool;
-  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t keep = UINT64_MAX;
-    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!pools[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.handleTypes = cudaMemHandleTypeNone;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t np;
+      e = cudaMemPoolCreate(&np, &props);
+      if (e != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) {
+        cudaMemPoolDestroy(np);
+        return e;
+      }
+      pools[dev] = np;
+    }
+    pool = pools[dev];
   }
-  cudaGetLastError();
-  done.push_back(dev);
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
 }
 
 static int build_network(Net* net, int kind, int n_nodes, const int32_t* parent,
@@ -91,7 +108,6 @@ static int build_network(Net* net, int kind, int n_nodes, const int32_t* parent,
                          const void* const* node_data, int data_on_device, void* stream) {
   if (n_nodes < 1 || !parent || !phys_dim || !bond_dim || !node_data)
     return fail(CBC_ERR_INVALID_ARG, "create: null argument or n_nodes < 1");
-  keep_pool_memory();
   if (!valid_dtype(dtype)) return fail(CBC_ERR_INVALID_ARG, "create: bad dtype %d", dtype);
   net->kind = kind;
   net->n = n_nodes;
@@ -140,32 +156,44 @@ static int build_network(Net* net, int kind, int n_nodes, const int32_t* parent,
     off[i + 1] = off[i] + (ne + 31) / 32 * 32;
   }
   const int64_t total = off[n_nodes];
-  cudaError_t e = cudaMallocAsync(&net->block, total * es, s);
+  cudaError_t e = pool_malloc(&net->block, total * es, s);
   if (e != cudaSuccess) {
     net->block = nullptr;
     return cuda_fail(e, "create: device allocation");
   }
   for (int i = 0; i < n_nodes; ++i) net->data[i] = static_cast<char*>(net->block) + off[i] * es;
+  // the widening pass also flags NaN / Inf entries: such inputs are rejected here, before
+  // any sweep runs on them
+  int* flag = nullptr;
+  e = pool_malloc(reinterpret_cast<void**>(&flag), sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "create: alloc");
+  e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "create: memset");
   if (!data_on_device) {
     void* staging = nullptr;
-    e = cudaMallocAsync(&staging, total * hs, s);
+    e = pool_malloc(&staging, total * hs, s);
     if (e != cudaSuccess) return cuda_fail(e, "create: staging alloc");
+    // one widening pass over all nodes (the padding between them is zeroed, never read)
+    e = cudaMemsetAsync(staging, 0, total * hs, s);
     for (int i = 0; i < n_nodes && e == cudaSuccess; ++i)
       e = cudaMemcpyAsync(static_cast<char*>(staging) + off[i] * hs, node_data[i],
                           net->numel[i] * hs, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "create: H2D copy");
-    // one widening pass over all nodes (the padding between them is never read)
-    e = widen_to_f64(staging, dtype, net->block, total, s);
+    e = widen_to_f64(staging, dtype, net->block, total, s, flag);
     if (e != cudaSuccess) return cuda_fail(e, "create: widen");
     cudaFreeAsync(staging, s);
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "create: synchronize");
   } else {
     for (int i = 0; i < n_nodes; ++i) {
-      e = widen_to_f64(node_data[i], dtype, net->data[i], net->numel[i], s);
+      e = widen_to_f64(node_data[i], dtype, net->data[i], net->numel[i], s, flag);
       if (e != cudaSuccess) return cuda_fail(e, "create: widen");
     }
   }
+  int hflag = 0;
+  e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(flag, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "create: synchronize");
+  if (hflag) return fail(CBC_ERR_NUMERICAL, "create: a node tensor holds NaN or Inf");
   return CBC_OK;
 }
 
@@ -240,7 +268,8 @@ int ttno_destroy(ttno_t t) {
 
 const char* cbc_last_error(void) { return g_last_error.c_str(); }
 
-int ttn_get_info(ttn_t t, int32_t* n_nodes_out, int64_t* bond_dims_out, double* log_norm_out) {
+int ttn_get_info(ttn_t t, int32_t* n_nodes_out, int64_t* bond_dims_out, double* log_norm_out,
+                 double* discarded_weight_out) {
   if (!t) return fail(CBC_ERR_INVALID_ARG, "ttn_get_info: NULL handle");
   cudaError_t e = cudaStreamSynchronize(t->stream);
   if (e != cudaSuccess) return cuda_fail(e, "ttn_get_info");
@@ -248,6 +277,9 @@ int ttn_get_info(ttn_t t, int32_t* n_nodes_out, int64_t* bond_dims_out, double* 
   if (bond_dims_out)
     for (int i = 0; i < t->n; ++i) bond_dims_out[i] = t->bond[i];
   if (log_norm_out) *log_norm_out = t->log_norm;
+  if (discarded_weight_out)
+    for (int i = 0; i < t->n; ++i)
+      discarded_weight_out[i] = (i < (int)t->discarded.size()) ? t->discarded[i] : 0.0;
   return CBC_OK;
 }
 
@@ -270,7 +302,7 @@ int ttn_get_node(ttn_t t, int node, void* dst, int dst_on_device, int dtype) {
   } else {
     void* tmp = dst;
     if (!dst_on_device) {
-      e = cudaMallocAsync(&tmp, bytes, s);
+      e = pool_malloc(&tmp, bytes, s);
       if (e != cudaSuccess) return cuda_fail(e, "ttn_get_node: alloc");
     }
     e = narrow_from_f64(t->data[node], t->cplx, tmp, dtype, ne, s);
@@ -302,7 +334,7 @@ int ttn_get_network(ttn_t t, void* dst, int dst_on_device, int dtype) {
   char* gather = static_cast<char*>(dst);
   cudaError_t e = cudaSuccess;
   if (!dst_on_device) {
-    e = cudaMallocAsync(reinterpret_cast<void**>(&gather), total * hs, s);
+    e = pool_malloc(reinterpret_cast<void**>(&gather), total * hs, s);
     if (e != cudaSuccess) return cuda_fail(e, "ttn_get_network: alloc");
   }
   int64_t off = 0;
@@ -326,12 +358,13 @@ int ttn_get_network(ttn_t t, void* dst, int dst_on_device, int dtype) {
 static int parse_options(const cbc_options* opt, Options* o) {
   if (opt) {
     o->precision = opt->precision;
-    if (opt->eps_rank > 0) o->eps_rank = opt->eps_rank;
     if (opt->slices_fwd > 0) o->slices_fwd = opt->slices_fwd;
     if (opt->slices_bwd > 0) o->slices_bwd = opt->slices_bwd;
   }
   if (o->precision != CBC_PREC_FP64 && o->precision != CBC_PREC_MIXED)
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply: bad precision %d", o->precision);
+  o->eps_rank = (o->precision == CBC_PREC_MIXED) ? 1e-9 : 1e-12;
+  if (opt && opt->eps_rank > 0) o->eps_rank = opt->eps_rank;
   return CBC_OK;
 }
 
@@ -346,7 +379,6 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_op
 static int apply_one(ttn_t state, ttno_t op, int64_t max_bond, double tol,
                      const cbc_options* opt, bool concurrent, ttn_t* out) {
   if (!out) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: out is NULL");
-  keep_pool_memory();
   *out = nullptr;
   if (!state || !op) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: NULL network");
   if (state->kind != 0 || op->kind != 1) return fail(CBC_ERR_INVALID_ARG, "cbc_apply: wrong handle kinds");
@@ -373,7 +405,6 @@ int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply_batched: bad arguments");
   for (int j = 0; j < n; ++j) outs[j] = nullptr;
   if (n == 0) return CBC_OK;
-  keep_pool_memory();
   // groups: chains with identical shapes, max_bond and tol (at most kMaxGroup each) run
   // in lockstep, one launch per step for the whole group; the rest one by one
   constexpr int kMaxGroup = 32;
@@ -494,13 +525,13 @@ int cbc_gemm(int precision, int slices, int dtype, int M, int N, int K, const vo
   View vc = View::rowmajor(ldc);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* status = nullptr;
-  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&status), sizeof(int), s);
+  cudaError_t e = pool_malloc(reinterpret_cast<void**>(&status), sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(e, "cbc_gemm: alloc");
   e = cudaMemsetAsync(status, 0, sizeof(int), s);
   void* ws = nullptr;
   const bool cplx = dtype == CBC_C128;
   if (e == cudaSuccess && precision == CBC_PREC_MIXED) {
-    e = cudaMallocAsync(&ws, gemm_tc_workspace_bytes(M, N, K, cplx, slices), s);
+    e = pool_malloc(&ws, gemm_tc_workspace_bytes(M, N, K, cplx, slices), s);
     if (e == cudaSuccess) {
       e = cplx ? gemm_tc<zdbl>(M, N, K, (const zdbl*)A, va, conjA, (const zdbl*)B, vb, conjB,
                                (zdbl*)C, vc, slices, ws, status, s)

@@ -77,6 +77,28 @@ __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p) {
   return *((volatile const unsigned int*)p);
 }
 
+// Spin until the 32-bit word at p differs from `seen`, for at most `limit` SM clock
+// cycles (clock64).  Returns true when it changed; on time-out records CBC_ERR_TIMEOUT
+// in *status and returns false.  Also gives up (false) as soon as another thread has
+// recorded a time-out.  Every device-side wait of the library has this shape: no wait
+// runs unbounded, and a kernel that gave up returns so the host can read the status.
+__device__ __forceinline__ bool wait_word_change(const unsigned int* p, unsigned int seen,
+                                                 int* status, long long limit) {
+  const long long t0 = clock64();
+  unsigned int cur;
+  while (true) {
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(p) : "memory");
+    if (cur != seen) return true;
+    if (clock64() - t0 > limit) {
+      set_status(status, CBC_ERR_TIMEOUT);
+      return false;
+    }
+    if (status && *((volatile int*)status) == CBC_ERR_TIMEOUT) return false;
+  }
+}
+
+constexpr long long kBarrierWaitCycles = 4000000000LL;  // ~2 s at the boost clock
+
 // returns false if the barrier timed out (status already set).  Arrival is a release
 // add at GPU scope, waiting an acquire load of the generation word.
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status,
@@ -97,21 +119,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, int* status,
       asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&bar->count) : "memory");
       asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->gen) : "memory");
     } else {
-      long long t0 = clock64();
-      unsigned int cur;
-      while (true) {
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&bar->gen) : "memory");
-        if (cur != g) break;
-        if (clock64() - t0 > 4000000000LL) {  // ~2 s
-          set_status(status, CBC_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        if (*((volatile int*)status) == CBC_ERR_TIMEOUT) {
-          ok = 0;
-          break;
-        }
-      }
+      ok = wait_word_change(&bar->gen, g, status, kBarrierWaitCycles) ? 1 : 0;
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     s_ok = ok;

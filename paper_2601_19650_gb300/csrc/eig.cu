@@ -928,6 +928,8 @@ __global__ void invit_kernel(InvArgs a) {
 
 // rank rule on the Rayleigh quotients of the candidates; the discarded weight is the
 // exact trace of T minus the kept eigenvalues.  Writes k and the full eigenvalue list.
+// floor_rel < 0 keeps all kmax candidates (the caller decides the rank from weights it
+// measures on the factor itself).
 __global__ void rank_kernel(const double* d, const double* rq, const float* lam32, int m,
                             int kmax, long long max_bond, double tol, double floor_rel,
                             int* k_dev, double* lam, size_t wb) {
@@ -948,7 +950,9 @@ __global__ void rank_kernel(const double* d, const double* rq, const float* lam3
   if (threadIdx.x != 0) return;
   const double l0 = rq[0];
   int k = 1;
-  if (l0 > 0.0) {
+  if (floor_rel < 0.0) {
+    k = kmax;  // every candidate: the caller applies the rank rule itself
+  } else if (l0 > 0.0) {
     k = 0;
     while (k < kmax && rq[k] > floor_rel * l0) ++k;
     if (tol > 0.0) {

@@ -73,10 +73,10 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
 
 // ---- Hermitian eigensolver (FP64): A (m x m, row-major, overwritten) -----------------
 // Finds the eigenvalues in descending order and the eigenvectors of the `k` largest,
-// where k follows the rank rule of cbc_apply: k = min(max_bond (if > 0), #{lambda_j >
-// floor * lambda_0}, smallest k with sum_{j>=k} lambda_j <= tol^2 sum_j lambda_j (if tol
-// > 0)), at least 1.  Outputs: lam[m], U (m x kmax, row-major, column j = eigenvector j),
-// *k_dev.  Workspace: eig_workspace_bytes(m, kmax).
+// where k = min(max_bond (if > 0), #{lambda_j > floor * lambda_0}, smallest k with
+// sum_{j>=k} lambda_j <= tol^2 sum_j lambda_j (if tol > 0)), at least 1; floor < 0 gives
+// k = kmax (every candidate).  Outputs: lam[m], U (m x kmax, row-major, column j =
+// eigenvector j), *k_dev.  Workspace: eig_workspace_bytes(m, kmax).
 struct EigWork;
 size_t eig_workspace_bytes(int m, int kmax, bool cplx);
 template <typename T>
@@ -123,6 +123,31 @@ cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_
 template <typename T>
 cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const int* perm,
                     cudaStream_t s);
+// Squared 2-norms of the rows (out[b * rows + r]) or of the columns (out[b * cols + c])
+// of nb row-major matrices rows x cols with leading dimension ld, bs elements apart.
+template <typename T>
+cudaError_t row_norms2(const T* W, int rows, int cols, int64_t ld, int64_t bs, double* out,
+                       cudaStream_t s, int nb = 1);
+template <typename T>
+cudaError_t col_norms2(const T* W, int rows, int cols, int64_t ld, int64_t bs, double* out,
+                       cudaStream_t s, int nb = 1);
+// out[b] = sum_i |A_b[i] - B_b[i]|^2 over n contiguous elements (A_b = A + b * a_bs,
+// B_b = B + b * n); C_b = A_b - B_b as well when C is not NULL (C_b = C + b * n)
+template <typename T>
+cudaError_t diff_sumsq(const T* A, int64_t a_bs, const T* B, T* C, int64_t n, double* out,
+                       cudaStream_t s, int nb = 1);
+// sum of |x|^2 over n contiguous elements per problem (problems n apart) into out[b]
+template <typename T>
+cudaError_t sum_squares(const T* x, int64_t n, double* out, cudaStream_t s, int nb = 1);
+// L[r, c] = sqrt(w[r]) conj(V[c, r]) for r < k (V: n x ldv row-major), L: k x n; nb
+// problems with V n*ldv, w w_bs and L l_bs elements apart
+template <typename T>
+cudaError_t scaled_adjoint_w(const T* V, int ldv, const double* w, int64_t w_bs, int k, int n,
+                             T* L, int64_t l_bs, cudaStream_t s, int nb = 1);
+// dst_b[i] = src_b[i] for i < n, src_b = src + b * s_bs, dst_b = dst + b * d_bs
+template <typename T>
+cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n,
+                         cudaStream_t s, int nb = 1);
 // dst (n_elem) = identity rows r < n of an n x n matrix
 template <typename T>
 cudaError_t fill_identity(T* dst, int n, cudaStream_t s, int nb = 1);
@@ -131,9 +156,10 @@ cudaError_t fill_identity(T* dst, int n, cudaStream_t s, int nb = 1);
 template <typename T>
 cudaError_t group_copy(T* const* ptrs, T* buf, int64_t stride, int64_t n, int nb, bool to_group,
                        cudaStream_t s);
-// widen an input tensor to FP64 storage
+// widen an input tensor to FP64 storage; *nonfinite (if given) is set to 1 when a value
+// is NaN or infinite
 cudaError_t widen_to_f64(const void* src, int src_dtype, void* dst, int64_t n_elem,
-                         cudaStream_t s);
+                         cudaStream_t s, int* nonfinite = nullptr);
 // narrow FP64 storage to the requested dtype
 cudaError_t narrow_from_f64(const void* src, bool cplx, void* dst, int dst_dtype,
                             int64_t n_elem, cudaStream_t s);

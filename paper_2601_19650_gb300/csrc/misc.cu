@@ -39,8 +39,8 @@ __global__ void scale_kernel(T* x, int64_t n, const double* sumsq, double* log_a
   log_acc += blockIdx.y;
   double ss = *sumsq;
   bool ok = isfinite(ss) && ss > 0.0;
-  if (!ok) {
-    if (blockIdx.x == 0 && threadIdx.x == 0 && !isfinite(ss)) set_status(status, CBC_ERR_NUMERICAL);
+  if (!ok) {  // NaN / Inf, or an all-zero tensor (then O|psi> itself vanishes)
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_status(status, CBC_ERR_NUMERICAL);
     return;
   }
   double inv = rsqrt(ss);
@@ -93,7 +93,9 @@ __global__ void identity_kernel(T* dst, int n) {
   }
 }
 
-__global__ void widen_kernel(const void* src, int dt, double* dst, int64_t n_scalar) {
+__global__ void widen_kernel(const void* src, int dt, double* dst, int64_t n_scalar,
+                             int* nonfinite) {
+  bool bad = false;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_scalar;
        i += (int64_t)gridDim.x * blockDim.x) {
     double v;
@@ -101,8 +103,10 @@ __global__ void widen_kernel(const void* src, int dt, double* dst, int64_t n_sca
       v = (double)static_cast<const float*>(src)[i];
     else
       v = static_cast<const double*>(src)[i];
+    bad = bad || !isfinite(v);
     dst[i] = v;
   }
+  if (nonfinite && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *nonfinite = 1;
 }
 
 __global__ void narrow_kernel(const double* src, void* dst, int dt, int64_t n_scalar) {
@@ -136,6 +140,96 @@ __global__ void permute_kernel(const T* in, T* out, int64_t total, PermArgs a) {
 }
 
 int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + 255) / 256)); }
+
+// one warp per row; problem blockIdx.y
+template <typename T>
+__global__ void row_norms2_kernel(const T* W, int rows, int cols, int64_t ld, int64_t bs,
+                                  double* out) {
+  W += (int64_t)blockIdx.y * bs;
+  out += (int64_t)blockIdx.y * rows;
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += nw) {
+    const T* row = W + (int64_t)r * ld;
+    double acc = 0.0;
+    for (int c = lane; c < cols; c += 32) acc += ops<T>::abs2(row[c]);
+    acc = warp_sum(acc);
+    if (lane == 0) out[r] = acc;
+  }
+}
+
+// columns on threadIdx.x (32 per CTA, coalesced), rows split over threadIdx.y and the
+// CTAs of blockIdx.x's row chunks; partial sums added into out (zeroed before)
+template <typename T>
+__global__ void col_norms2_kernel(const T* W, int rows, int cols, int64_t ld, int64_t bs,
+                                  int rows_per_cta, double* out) {
+  W += (int64_t)blockIdx.y * bs;
+  out += (int64_t)blockIdx.y * cols;
+  __shared__ double part[8][33];
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(rows, r0 + rows_per_cta);
+  for (int c0 = 0; c0 < cols; c0 += 32) {
+    const int c = c0 + threadIdx.x;
+    double acc = 0.0;
+    if (c < cols)
+      for (int r = r0 + threadIdx.y; r < r1; r += blockDim.y) acc += ops<T>::abs2(W[(int64_t)r * ld + c]);
+    part[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < cols) {
+      double t = 0.0;
+      for (int q = 0; q < (int)blockDim.y; ++q) t += part[q][threadIdx.x];
+      atomicAdd(out + c, t);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void diff_sumsq_kernel(const T* A, int64_t a_bs, const T* B, T* C, int64_t n,
+                                  double* out) {
+  A += (int64_t)blockIdx.y * a_bs;
+  B += (int64_t)blockIdx.y * n;
+  if (C) C += (int64_t)blockIdx.y * n;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T d = A[i] - B[i];
+    if (C) C[i] = d;
+    acc += ops<T>::abs2(d);
+  }
+  acc = warp_sum(acc);
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = acc;
+  __syncthreads();
+  if (w == 0) {
+    acc = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+    acc = warp_sum(acc);
+    if (lane == 0) atomicAdd(out + blockIdx.y, acc);
+  }
+}
+
+template <typename T>
+__global__ void scaled_adjoint_w_kernel(const T* V, int ldv, const double* w, int64_t w_bs, int k,
+                                        int n, T* L, int64_t l_bs) {
+  V += (int64_t)blockIdx.y * n * ldv;
+  w += (int64_t)blockIdx.y * w_bs;
+  L += (int64_t)blockIdx.y * l_bs;
+  const int64_t total = (int64_t)k * n;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), c = (int)(t % n);
+    L[t] = ops<T>::scale(sqrt(fmax(w[r], 0.0)), ops<T>::conj(V[(int64_t)c * ldv + r]));
+  }
+}
+
+template <typename T>
+__global__ void copy_batched_kernel(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n) {
+  src += (int64_t)blockIdx.y * s_bs;
+  dst += (int64_t)blockIdx.y * d_bs;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
 
 }  // namespace
 
@@ -283,10 +377,11 @@ cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const
 }
 
 cudaError_t widen_to_f64(const void* src, int src_dtype, void* dst, int64_t n_elem,
-                         cudaStream_t s) {
+                         cudaStream_t s, int* nonfinite) {
   int64_t ns = n_elem * ((src_dtype == CBC_C64 || src_dtype == CBC_C128) ? 2 : 1);
   note_launches(CBC_K_AUX, 1);
-  widen_kernel<<<grid_for(ns), 256, 0, s>>>(src, src_dtype, static_cast<double*>(dst), ns);
+  widen_kernel<<<grid_for(ns), 256, 0, s>>>(src, src_dtype, static_cast<double*>(dst), ns,
+                                            nonfinite);
   return cudaGetLastError();
 }
 
@@ -297,6 +392,82 @@ cudaError_t narrow_from_f64(const void* src, bool cplx, void* dst, int dst_dtype
   narrow_kernel<<<grid_for(ns), 256, 0, s>>>(static_cast<const double*>(src), dst, dst_dtype, ns);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t row_norms2(const T* W, int rows, int cols, int64_t ld, int64_t bs, double* out,
+                       cudaStream_t s, int nb) {
+  note_launches(CBC_K_AUX, 1);
+  const int blocks = std::max(1, std::min(1024, (rows + 7) / 8));
+  row_norms2_kernel<T><<<dim3(blocks, nb), 256, 0, s>>>(W, rows, cols, ld, bs, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t col_norms2(const T* W, int rows, int cols, int64_t ld, int64_t bs, double* out,
+                       cudaStream_t s, int nb) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)cols * nb, s);
+  if (e != cudaSuccess) return e;
+  note_launches(CBC_K_AUX, 1);
+  const int chunks = std::max(1, std::min(std::max(1, 1024 / nb), (rows + 63) / 64));
+  const int per = (rows + chunks - 1) / chunks;
+  col_norms2_kernel<T><<<dim3(chunks, nb), dim3(32, 8), 0, s>>>(W, rows, cols, ld, bs, per, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t diff_sumsq(const T* A, int64_t a_bs, const T* B, T* C, int64_t n, double* out,
+                       cudaStream_t s, int nb) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * nb, s);
+  if (e != cudaSuccess) return e;
+  note_launches(CBC_K_AUX, 1);
+  diff_sumsq_kernel<T><<<dim3(std::min(grid_for(n), std::max(1, 1024 / nb)), nb), 256, 0, s>>>(
+      A, a_bs, B, C, n, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sum_squares(const T* x, int64_t n, double* out, cudaStream_t s, int nb) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * nb, s);
+  if (e != cudaSuccess) return e;
+  note_launches(CBC_K_AUX, 1);
+  sumsq_kernel<T><<<dim3(std::min(grid_for(n), std::max(1, 1024 / nb)), nb), 256, 0, s>>>(x, n, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t scaled_adjoint_w(const T* V, int ldv, const double* w, int64_t w_bs, int k, int n,
+                             T* L, int64_t l_bs, cudaStream_t s, int nb) {
+  note_launches(CBC_K_AUX, 1);
+  scaled_adjoint_w_kernel<T><<<dim3(grid_for((int64_t)k * n), nb), 256, 0, s>>>(V, ldv, w, w_bs,
+                                                                               k, n, L, l_bs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n,
+                         cudaStream_t s, int nb) {
+  if (n <= 0) return cudaSuccess;
+  note_launches(CBC_K_AUX, 1);
+  copy_batched_kernel<T><<<dim3(std::min(grid_for(n), std::max(1, 2048 / nb)), nb), 256, 0, s>>>(
+      src, s_bs, dst, d_bs, n);
+  return cudaGetLastError();
+}
+
+#define CBC_MISC_INST(T)                                                                     \
+  template cudaError_t row_norms2<T>(const T*, int, int, int64_t, int64_t, double*,          \
+                                     cudaStream_t, int);                                     \
+  template cudaError_t col_norms2<T>(const T*, int, int, int64_t, int64_t, double*,          \
+                                     cudaStream_t, int);                                     \
+  template cudaError_t diff_sumsq<T>(const T*, int64_t, const T*, T*, int64_t, double*,      \
+                                     cudaStream_t, int);                                     \
+  template cudaError_t sum_squares<T>(const T*, int64_t, double*, cudaStream_t, int);        \
+  template cudaError_t scaled_adjoint_w<T>(const T*, int, const double*, int64_t, int, int,  \
+                                           T*, int64_t, cudaStream_t, int);                  \
+  template cudaError_t copy_batched<T>(const T*, int64_t, T*, int64_t, int64_t, cudaStream_t, \
+                                       int);
+CBC_MISC_INST(double)
+CBC_MISC_INST(zdbl)
+#undef CBC_MISC_INST
 
 template cudaError_t normalize_inplace<double>(double*, int64_t, double*, int*, double*,
                                                cudaStream_t, int);

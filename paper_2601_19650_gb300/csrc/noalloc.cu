@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -103,7 +104,7 @@ template <typename T>
 int sweeps(const Args& a, Bump& b, bool dry) {
   const int L = a.L;
   cudaStream_t s = a.s;
-  const double floor_rel = 1e-12;  // eps_rank 1e-6 on singular values, as cbc_apply
+  const double floor_rel = 1e-12;  // cbc_apply's FP64 rank floor on singular values
   auto sb = [&](int i) { return (i < L && i > 0) ? (int)a.sbond[i] : 1; };
   auto ob = [&](int i) { return (i < L && i > 0) ? (int)a.obond[i] : 1; };
   NA_GET(d_int, int, 4);
@@ -127,10 +128,15 @@ int sweeps(const Args& a, Bump& b, bool dry) {
     NA_CK(cudaMemsetAsync(d_dbl, 0, 4 * sizeof(double), s));
     NA_CK(cudaMemcpyAsync(env0, &one, sizeof(T), cudaMemcpyHostToDevice, s));
   }
-  // ---- forward sweep, Eq. (tt_cbc_first_contraction) and the compression after it
+  // ---- forward sweep, Eq. (tt_cbc_first_contraction) and the compression after it,
+  // with cbc_apply's first-level truncation: every candidate direction of the Gram, the
+  // rank rule on the weights measured on M (pick_rank), the first k rows of U^H M (or
+  // diag(sqrt(w)) V^H) as the new environment.  A rank that would keep directions below
+  // the Gram's resolution needs cbc_apply's second level, which is not built here.
   for (int i = 0; i < L - 1; ++i) {
     const int c = chi[i], bb = ob(i), aa = sb(i), d = (int)a.phys[i], a2 = sb(i + 1), b2 = ob(i + 1);
     const int m = c * d, n = b2 * a2, g = std::min(m, n);
+    const bool rows = (m <= n);
     const int kmax = (int)((a.max_bond > 0) ? std::min<int64_t>(a.max_bond, g) : g);
     NA_GET(envn, T, (size_t)kmax * n);  // below this step's temporaries
     const size_t mark = b.used;
@@ -140,6 +146,9 @@ int sweeps(const Args& a, Bump& b, bool dry) {
     NA_GET(lam, double, g);
     NA_GET(U, T, (size_t)g * kmax);
     NA_GET(work, char, eig_workspace_bytes(g, kmax, ops<T>::cplx));
+    NA_GET(wv, double, kmax + 2);
+    NA_GET(Wc, T, rows ? 1 : (size_t)m * kmax);
+    NA_GET(P, T, a.tol > 0.0 ? (size_t)m * n : 1);
     int k = kmax;
     if (!dry) {
       const T* Ti = static_cast<const T*>(a.st[i]);
@@ -155,24 +164,48 @@ int sweeps(const Args& a, Bump& b, bool dry) {
       vl.rs_in = a2;
       vl.cols2(a2, (int64_t)d * b2 * a2, 1);
       NA_CK(gemm_f64<T>(d * b2, c * a2, bb * d, 1, Wi, vw, false, X, vx, false, Lp, vl, s));
-      if (m <= n)
+      if (rows)
         NA_CK(gemm_f64<T>(m, m, n, 1, Lp, View::rowmajor(n), false, Lp, View::transposed(n), true,
                           K, View::rowmajor(m), s));
       else
         NA_CK(gemm_f64<T>(n, n, m, 1, Lp, View::transposed(n), true, Lp, View::rowmajor(n), false,
                           K, View::rowmajor(n), s));
-      NA_CK(heev_top<T>(K, g, kmax, a.max_bond, a.tol, floor_rel, lam, U, k_dev, work, status,
-                        num_sms(), s));
-      int h[2] = {0, 0};
-      NA_CK(cudaMemcpyAsync(h, status, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-      NA_CK(cudaStreamSynchronize(s));
-      if (h[0] != 0) return fail(h[0], "cbc_apply_tt_noalloc: device status %d", h[0]);
-      k = h[1];
-      if (m <= n)
-        NA_CK(gemm_f64<T>(k, n, m, 1, U, View::transposed(kmax), true, Lp, View::rowmajor(n),
+      NA_CK(heev_top<T>(K, g, kmax, kmax, 0.0, -1.0, lam, U, k_dev, work, status, num_sms(), s));
+      if (rows) {  // U^H M, kmax x n, in the environment buffer
+        NA_CK(gemm_f64<T>(kmax, n, m, 1, U, View::transposed(kmax), true, Lp, View::rowmajor(n),
                           false, envn, View::rowmajor(n), s));
-      else
-        NA_CK(scaled_adjoint<T>(U, kmax, lam, k_dev, n, envn, s));
+        NA_CK(row_norms2<T>(envn, kmax, n, n, 0, wv, s));
+      } else {     // M V, m x kmax
+        NA_CK(gemm_f64<T>(m, kmax, n, 1, Lp, View::rowmajor(n), false, U, View::rowmajor(kmax),
+                          false, Wc, View::rowmajor(kmax), s));
+        NA_CK(col_norms2<T>(Wc, m, kmax, kmax, 0, wv, s));
+      }
+      if (a.tol > 0.0) {  // weight outside the candidates
+        if (rows)
+          NA_CK(gemm_f64<T>(m, n, kmax, 1, U, View::rowmajor(kmax), false, envn, View::rowmajor(n),
+                            false, P, View::rowmajor(n), s));
+        else
+          NA_CK(gemm_f64<T>(m, n, kmax, 1, Wc, View::rowmajor(kmax), false, U,
+                            View::transposed(kmax), true, P, View::rowmajor(n), s));
+        NA_CK(diff_sumsq<T>(Lp, (int64_t)m * n, P, nullptr, (int64_t)m * n, wv + kmax, s));
+      }
+      std::vector<double> hw(kmax + 1, -1.0);
+      int hs = 0;
+      NA_CK(cudaMemcpyAsync(hw.data(), wv, sizeof(double) * (kmax + (a.tol > 0.0 ? 1 : 0)),
+                            cudaMemcpyDeviceToHost, s));
+      NA_CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      NA_CK(cudaStreamSynchronize(s));
+      if (hs != 0) return fail(hs, "cbc_apply_tt_noalloc: device status %d", hs);
+      for (int j = 0; j < kmax + (a.tol > 0.0 ? 1 : 0); ++j)
+        if (!std::isfinite(hw[j]))
+          return fail(CBC_ERR_NUMERICAL, "cbc_apply_tt_noalloc: NaN or Inf in a truncation");
+      k = pick_rank(hw.data(), kmax, a.tol > 0.0 ? hw[kmax] : -1.0, a.max_bond, a.tol, floor_rel);
+      if (k > resolved_prefix(hw.data(), kmax, kResolvedFP64) && k < g)
+        return fail(CBC_ERR_UNSUPPORTED,
+                    "cbc_apply_tt_noalloc: the rank rule keeps directions below the Gram's "
+                    "resolution at site %d (singular values under 1e-5 of the largest); "
+                    "cbc_apply refines those, this entry point does not", i);
+      if (!rows) NA_CK(scaled_adjoint_w<T>(U, kmax, wv, kmax, k, n, envn, 0, s));
       NA_CK(normalize_inplace<T>(envn, (int64_t)k * n, log_fwd, status, dscr, s));
     }
     env[i + 1] = envn;
@@ -180,7 +213,30 @@ int sweeps(const Args& a, Bump& b, bool dry) {
     b.used = mark;
   }
   // ---- backward sweep, Eqs. (right_sweep_init_contr), (tt_cbc_qr_decomp),
-  // (tt_cbc_final_contraction); two R buffers alternate
+  // (tt_cbc_final_contraction); two R buffers alternate.  At a site whose S has at
+  // least as many rows as columns the new tensor is the identity (every unitary spans
+  // the whole row space, the rule cbc_apply follows), so S is only formed at the first
+  // site or when it has fewer rows than columns.
+  //
+  // Every rank is known once the forward sweep has run, so the size of the result is
+  // checked here, before the backward sweep launches anything; on failure the stream is
+  // drained first, so nothing still runs when the caller sees the error.
+  int64_t out_need = 0;
+  {
+    int cp = 1;
+    for (int i = L - 1; i >= 0; --i) {
+      const int m = chi[i], n = (int)a.phys[i] * cp;
+      const int cn = (m < n) ? m : n;
+      out_need += (int64_t)cn * n;
+      cp = cn;
+    }
+  }
+  if (!dry && out_need > a.out_cap) {
+    cudaStreamSynchronize(s);
+    return fail(CBC_ERR_INVALID_ARG,
+                "cbc_apply_tt_noalloc: out_capacity %lld elements is too small: the result "
+                "needs %lld", (long long)a.out_cap, (long long)out_need);
+  }
   size_t rmax = 1;
   for (int i = 0; i < L; ++i) rmax = std::max(rmax, (size_t)chi[i] * ob(i) * sb(i));
   NA_GET(Ra, T, rmax);
@@ -193,18 +249,13 @@ int sweeps(const Args& a, Bump& b, bool dry) {
   for (int i = L - 1; i >= 0; --i) {
     const int a_in = sb(i), b_in = ob(i), d = (int)a.phys[i], a_out = sb(i + 1), b_out = ob(i + 1);
     const int cp = chiR, c = chi[i], m = c, n = d * cp;
-    const int cn = (m <= n) ? m : n;
+    const int cn = (m < n) ? m : n;
+    const bool formed = (i == 0 || m < n);
     const size_t mark = b.used;
     NA_GET(Y, T, (size_t)a_in * d * cp * b_out);
     NA_GET(Z, T, (size_t)b_in * a_in * d * cp);
     NA_GET(G, T, (size_t)m * m);
-    const int64_t need = (int64_t)std::max(m, cn) * n;
     if (!dry) {
-      if (out_used + need > a.out_cap)
-        return fail(CBC_ERR_INVALID_ARG,
-                    "cbc_apply_tt_noalloc: out_capacity %lld elements is too small (site %d needs "
-                    "%lld more beyond %lld)", (long long)a.out_cap, i, (long long)need,
-                    (long long)out_used);
       T* node = reinterpret_cast<T*>(a.out) + out_used;
       a.out_off[i] = out_used;
       const T* Ti = static_cast<const T*>(a.st[i]);
@@ -217,7 +268,7 @@ int sweeps(const Args& a, Bump& b, bool dry) {
       vz.rows2(d, (int64_t)a_in * d * cp, cp).cols2(cp, (int64_t)d * cp, 1);
       NA_CK(gemm_f64<T>(b_in * d, a_in * cp, d * b_out, 1, Wi, View::rowmajor(d * b_out), false, Y,
                         vy, false, Z, vz, s));
-      if (i == 0 || m <= n)
+      if (formed)
         NA_CK(gemm_f64<T>(m, n, b_in * a_in, 1, env[i], View::rowmajor(b_in * a_in), false, Z,
                           View::rowmajor(n), false, node, View::rowmajor(n), s));
       if (i == 0) {
@@ -226,7 +277,7 @@ int sweeps(const Args& a, Bump& b, bool dry) {
         out_used += n;
         break;
       }
-      if (m <= n) {
+      if (m < n) {
         for (int rep = 0; rep < 2; ++rep) {
           NA_CK(gemm_f64<T>(m, m, n, 1, node, View::rowmajor(n), false, node, View::transposed(n),
                             true, G, View::rowmajor(m), s));
@@ -282,6 +333,25 @@ extern "C" int cbc_apply_tt_noalloc(int L, const int64_t* phys_dim, const int64_
       return fail(CBC_ERR_INVALID_ARG, "cbc_apply_tt_noalloc: site %d has a dimension < 1", i);
     if (!state_nodes[i] || !op_nodes[i])
       return fail(CBC_ERR_INVALID_ARG, "cbc_apply_tt_noalloc: node pointer %d is NULL", i);
+  }
+  // every extent the sweeps hand to a kernel is an int: reject chains whose dimension
+  // products (with each compressed bond at its upper bound) exceed that range
+  {
+    auto bond_of = [&](const int64_t* b, int i) -> int64_t { return (i > 0 && i < L) ? b[i] : 1; };
+    int64_t c = 1;  // upper bound of the compressed bond chi_i
+    for (int i = 0; i < L; ++i) {
+      const int64_t d = phys_dim[i], a_in = bond_of(state_bond, i), b_in = bond_of(op_bond, i);
+      const int64_t a_out = bond_of(state_bond, i + 1), b_out = bond_of(op_bond, i + 1);
+      const int64_t cn = std::min<int64_t>(c * d, a_out * b_out);  // chi_{i+1} and chi'_i bound
+      const double big = std::max({(double)a_in * d * a_out, (double)b_in * d * d * b_out,
+                                   (double)c * b_in * d * a_out, (double)c * d * b_out * a_out,
+                                   (double)a_in * d * cn * b_out, (double)b_in * a_in * d * cn,
+                                   (double)c * d * cn, (double)c * c});
+      if (big > (double)INT32_MAX)
+        return fail(CBC_ERR_INVALID_ARG,
+                    "cbc_apply_tt_noalloc: site %d has a dimension product beyond 2^31 - 1", i);
+      c = (max_bond > 0) ? std::min<int64_t>(cn, max_bond) : cn;
+    }
   }
   void* base = nullptr;
   int rc = scratch_base(&base);

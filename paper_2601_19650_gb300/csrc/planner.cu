@@ -27,7 +27,7 @@ struct Arena {
   T* get(size_t n) {
     void* p = nullptr;
     size_t bytes = std::max<size_t>(n * sizeof(T), 256);
-    cudaError_t e = cudaMallocAsync(&p, bytes, s);
+    cudaError_t e = pool_malloc(&p, bytes, s);
     if (e != cudaSuccess) {
       if (err == cudaSuccess) err = e;
       return nullptr;
@@ -74,7 +74,9 @@ int status_to_rc(int st) {
   switch (st) {
     case CBC_ERR_NOT_POSITIVE_DEFINITE:
       return fail(st, "cbc_apply: Cholesky met a non-positive pivot (rank-deficient S)");
-    case CBC_ERR_NUMERICAL: return fail(st, "cbc_apply: NaN or Inf in an intermediate");
+    case CBC_ERR_NUMERICAL:
+      return fail(st, "cbc_apply: NaN or Inf in an intermediate, or O|psi> vanishes (an "
+                      "environment of zero norm)");
     case CBC_ERR_TIMEOUT: return fail(st, "cbc_apply: a device-side wait timed out");
     default: return fail(st, "cbc_apply: device status %d", st);
   }
@@ -137,60 +139,250 @@ cudaError_t tgemm(const Prec& pr, bool fwd, bool gram, int M, int N, int K, cons
 }
 
 
-// read status and k after a compression (k of every instance of a group: they must
-// agree, else kGroupSplit)
-int read_k(const Scalars& sc, cudaStream_t s, int nb, int* k) {
-  std::vector<int> h(1 + nb, 0);
-  CK(cudaMemcpyAsync(h.data(), sc.status, (1 + nb) * sizeof(int), cudaMemcpyDeviceToHost, s));
+// ---- truncation of a fused leg (Sec. III A, text after Eq. (tt_cbc_first_contraction);
+// Sec. III B steps 1 and 2) --------------------------------------------------------------
+//
+// The paper compresses "for example via SVD".  Here the candidate directions come from the
+// Gram K = M M^H (or G = M^H M) and a Hermitian eigensolver, but the rank rule runs on
+// weights measured on M itself: w_j = ||u_j^H M||^2 (or ||M v_j||^2) and, in tolerance
+// mode, the exact weight outside the candidates ||M - U U^H M||_F^2.  A Gram holds the
+// small singular values only to about eps * s_0^2 in absolute terms, so its eigenvalues
+// cannot decide a tolerance of 1e-8 (discarded weight 1e-16 of the total); the weights
+// measured on M resolve it, and when the rule keeps directions below what the Gram
+// resolves, those directions are recomputed from the Gram of the residual
+// M - U_r U_r^H M beyond the well-resolved ones (a second level).
+
+// relative weight discarded by keeping the first k directions
+double discarded_rel(const double* w, int kmax, int k, double beyond, double total) {
+  if (!(total > 0.0)) return 0.0;
+  double tail;
+  if (beyond >= 0.0) {
+    tail = std::max(beyond, 0.0);
+    for (int j = k; j < kmax; ++j) tail += std::max(w[j], 0.0);
+  } else {
+    double kept = 0.0;
+    for (int j = 0; j < k; ++j) kept += std::max(w[j], 0.0);
+    tail = std::max(total - kept, 0.0);
+  }
+  return tail / total;
+}
+
+bool all_finite(const std::vector<double>& v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+// Second level for one instance, rows orientation: U1 (m x kmax, column j = direction j)
+// and W1 = U1^H M (kmax x n, the first kmax rows of the buffer that becomes L) from the
+// first level, j0 of them resolved.  Recomputes the directions beyond j0 from the Gram
+// of R = M - U1[:, :j0] W1[:j0] (orthogonalised against the resolved ones), writes their
+// W rows into W1 from row j0 on, and decides the rank on the combined weights.
+template <typename T>
+int refine_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int kmax, int j0,
+                const T* U1, T* W1, std::vector<double>& w, int64_t max_bond, double tol,
+                double floor_rel, const Options& o, const Scalars& sc, cudaStream_t s,
+                int* kout, double* disc) {
+  const int k2 = kmax - j0;
+  const int64_t mn = (int64_t)m * n;
+  T* P = ar.get<T>((size_t)mn);
+  T* R = ar.get<T>((size_t)mn);
+  T* K2 = ar.get<T>((size_t)m * m);
+  double* lam2 = ar.get<double>(m);
+  T* U2 = ar.get<T>((size_t)m * k2);
+  T* C = ar.get<T>((size_t)std::max(1, j0) * k2);
+  T* P2 = ar.get<T>((size_t)m * k2);
+  char* work = ar.get<char>(eig_workspace_bytes(m, k2, ops<T>::cplx));
+  double* dv = ar.get<double>(k2 + 4);
+  CKA(P); CKA(R); CKA(K2); CKA(lam2); CKA(U2); CKA(C); CKA(P2); CKA(work); CKA(dv);
+  // R = M - U1[:, :j0] W1[:j0]
+  if (j0 > 0) {
+    CK(tgemm<T>(pr, true, false, m, n, j0, U1, View::rowmajor(kmax), false, W1,
+                View::rowmajor(n), false, P, View::rowmajor(n), s));
+    CK(diff_sumsq<T>(M, mn, P, R, mn, dv + k2, s));
+  } else {
+    CK(cudaMemcpyAsync(R, M, sizeof(T) * mn, cudaMemcpyDeviceToDevice, s));
+  }
+  CK(tgemm<T>(pr, true, true, m, m, n, R, View::rowmajor(n), false, R, View::transposed(n), true,
+              K2, View::rowmajor(m), s));
+  CK(heev_top<T>(K2, m, k2, k2, 0.0, -1.0, lam2, U2, sc.k, work, sc.status, num_sms(), s, 1,
+                 o.concurrent, false));
+  if (j0 > 0) {  // U2 <- U2 - U1r (U1r^H U2)
+    CK(tgemm<T>(pr, true, false, j0, k2, m, U1, View::transposed(kmax), true, U2,
+                View::rowmajor(k2), false, C, View::rowmajor(k2), s));
+    CK(tgemm<T>(pr, true, false, m, k2, j0, U1, View::rowmajor(kmax), false, C,
+                View::rowmajor(k2), false, P2, View::rowmajor(k2), s));
+    CK(diff_sumsq<T>(U2, (int64_t)m * k2, P2, U2, (int64_t)m * k2, dv + k2 + 1, s));
+  }
+  T* W2 = W1 + (int64_t)j0 * n;  // rows j0 .. kmax-1 of the new factor
+  CK(tgemm<T>(pr, true, false, k2, n, m, U2, View::transposed(k2), true, M, View::rowmajor(n),
+              false, W2, View::rowmajor(n), s));
+  CK(row_norms2<T>(W2, k2, n, n, 0, dv, s));
+  // weight outside all kmax directions: ||R - U2 W2||^2
+  CK(tgemm<T>(pr, true, false, m, n, k2, U2, View::rowmajor(k2), false, W2, View::rowmajor(n),
+              false, P, View::rowmajor(n), s));
+  CK(diff_sumsq<T>(R, mn, P, nullptr, mn, dv + k2 + 2, s));
+  std::vector<double> h(k2 + 3);
+  int hs = 0;
+  CK(cudaMemcpyAsync(h.data(), dv, sizeof(double) * (k2 + 3), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hs, sc.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (h[0] != 0) return status_to_rc(h[0]);
-  for (int b = 1; b < nb; ++b)
-    if (h[1 + b] != h[1]) return kGroupSplit;
-  *k = h[1];
+  if (hs != 0) return status_to_rc(hs);
+  if (!all_finite(h)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
+  for (int j = 0; j < k2; ++j) w[j0 + j] = h[j];
+  const double beyond = h[k2 + 2];
+  const int k = pick_rank(w.data(), kmax, beyond, max_bond, tol, floor_rel);
+  double total = beyond;
+  for (int j = 0; j < kmax; ++j) total += std::max(w[j], 0.0);
+  *disc = discarded_rel(w.data(), kmax, k, beyond, total);
+  *kout = k;
   return CBC_OK;
 }
 
 // Compression of the row leg of M (m x n, row-major): writes the k x n factor whose
-// Gram reproduces the rank-k truncation of M^H M (Sec. III A, text after Eq.
-// (tt_cbc_first_contraction)), normalised, and returns k.
-// L (k x n per instance) comes from `keep` (default: ar); the rest is released on
-// return.
+// Gram reproduces the rank-k truncation of M^H M, normalised, and returns k (and the
+// relative discarded weight per instance in disc, if given).  L (k x n per instance)
+// comes from `keep` (default: ar); the rest is released on return when keep is given.
 template <typename T>
 int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t max_bond,
                   double tol, const Options& o, const Scalars& sc, cudaStream_t s, T** Lout,
-                  int* kout, Arena* keep = nullptr) {
-  const int kmax = (int)((max_bond > 0) ? std::min<int64_t>(max_bond, std::min(m, n)) : std::min(m, n));
-  const double floor_rel = o.eps_rank * o.eps_rank;
+                  int* kout, Arena* keep = nullptr, double* disc = nullptr) {
   const int g = std::min(m, n);
+  const int kmax = (int)((max_bond > 0) ? std::min<int64_t>(max_bond, g) : g);
   const int nb = pr.nb;
   const int64_t mbs = (int64_t)m * n;  // M of consecutive instances
+  const bool rows = (m <= n);          // K = M M^H, else G = M^H M
+  const double floor_rel = o.eps_rank;
+  const double res = pr.mixed ? kResolvedMixed : kResolvedFP64;
+  Arena& kp = keep ? *keep : ar;
   const size_t mk = ar.mark();
   T* K = ar.get<T>((size_t)nb * g * g);
   double* lam = ar.get<double>((size_t)nb * g);
   T* U = ar.get<T>((size_t)nb * g * kmax);
   char* work = ar.get<char>(nb * eig_workspace_bytes(g, kmax, ops<T>::cplx));
-  CKA(K); CKA(lam); CKA(U); CKA(work);
-  if (m <= n) {  // K = M M^H, eigenvectors = left singular vectors
+  double* dv = ar.get<double>((size_t)nb * (kmax + 2));  // w [nb][kmax], beyond [nb], total [nb]
+  CKA(K); CKA(lam); CKA(U); CKA(work); CKA(dv);
+  double* w_dev = dv;
+  double* beyond_dev = dv + (size_t)nb * kmax;
+  double* total_dev = beyond_dev + nb;
+  CK(sum_squares<T>(M, mbs, total_dev, s, nb));  // ||M||_F^2, the weight of the cut
+  if (rows) {
     CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n, mbs), false, M,
                 View::transposed(n, mbs), true, K, View::rowmajor(m, (int64_t)g * g), s));
-  } else {       // G = M^H M, eigenvectors = right singular vectors
+  } else {
     CK(tgemm<T>(pr, true, true, n, n, m, M, View::transposed(n, mbs), true, M,
                 View::rowmajor(n, mbs), false, K, View::rowmajor(n, (int64_t)g * g), s));
   }
-  // the mixed path reduces to tridiagonal form in double-float arithmetic
-  CK(heev_top<T>(K, g, kmax, max_bond, tol, floor_rel, lam, U, sc.k, work, sc.status, num_sms(),
-                 s, nb, o.concurrent, pr.mixed));
-  int k = 0;
-  int rc = read_k(sc, s, nb, &k);
-  if (rc != CBC_OK) return rc;
-  T* L = (keep ? keep : &ar)->get<T>((size_t)nb * k * n);
-  if (!L) return cuda_fail((keep ? keep : &ar)->err, "workspace allocation L");
+  // every candidate; the mixed path reduces batches to tridiagonal form in double-float
+  CK(heev_top<T>(K, g, kmax, kmax, 0.0, -1.0, lam, U, sc.k, work, sc.status, num_sms(), s, nb,
+                 o.concurrent, pr.mixed));
+  const int64_t ubs = (int64_t)g * kmax;
+  T* W = nullptr;
+  int64_t wbs;
+  if (rows) {  // W = U^H M (kmax x n): its first k rows are the new factor
+    wbs = (int64_t)kmax * n;
+    W = kp.get<T>((size_t)nb * wbs);
+    if (!W) return cuda_fail(kp.err, "workspace allocation L");
+    CK(tgemm<T>(pr, true, false, kmax, n, m, U, View::transposed(kmax, ubs), true, M,
+                View::rowmajor(n, mbs), false, W, View::rowmajor(n, wbs), s));
+    CK(row_norms2<T>(W, kmax, n, n, wbs, w_dev, s, nb));
+  } else {     // W = M V (m x kmax): column j has norm s_j
+    wbs = (int64_t)m * kmax;
+    W = ar.get<T>((size_t)nb * wbs);
+    CKA(W);
+    CK(tgemm<T>(pr, true, false, m, kmax, n, M, View::rowmajor(n, mbs), false, U,
+                View::rowmajor(kmax, ubs), false, W, View::rowmajor(kmax, wbs), s));
+    CK(col_norms2<T>(W, m, kmax, kmax, wbs, w_dev, s, nb));
+  }
+  if (tol > 0.0) {  // the exact weight outside the candidates, ||M - U U^H M||^2
+    T* P = ar.get<T>((size_t)nb * mbs);
+    CKA(P);
+    if (rows)
+      CK(tgemm<T>(pr, true, false, m, n, kmax, U, View::rowmajor(kmax, ubs), false, W,
+                  View::rowmajor(n, wbs), false, P, View::rowmajor(n, mbs), s));
+    else
+      CK(tgemm<T>(pr, true, false, m, n, kmax, W, View::rowmajor(kmax, wbs), false, U,
+                  View::transposed(kmax, ubs), true, P, View::rowmajor(n, mbs), s));
+    CK(diff_sumsq<T>(M, mbs, P, nullptr, mbs, beyond_dev, s, nb));
+  }
+  std::vector<double> h((size_t)nb * (kmax + 2));
+  int hs = 0;
+  CK(cudaMemcpyAsync(h.data(), dv, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hs, sc.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs != 0) return status_to_rc(hs);
+  if (!all_finite(h)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
+  for (int b = 0; b < nb; ++b)
+    if (!(h[(size_t)nb * (kmax + 1) + b] > 0.0))
+      return fail(CBC_ERR_NUMERICAL, "cbc_apply: O|psi> vanishes (a compression of zero weight)");
+  std::vector<int> kb(nb), j0(nb);
+  bool refine = false;
+  for (int b = 0; b < nb; ++b) {
+    const double* w = h.data() + (size_t)b * kmax;
+    const double beyond = (tol > 0.0) ? h[(size_t)nb * kmax + b] : -1.0;
+    kb[b] = pick_rank(w, kmax, beyond, max_bond, tol, floor_rel);
+    j0[b] = resolved_prefix(w, kmax, res);
+    // a real cut (k < g) among directions the Gram does not resolve; keeping every
+    // direction needs no choice of subspace
+    if (kb[b] > j0[b] && kb[b] < g) refine = true;
+    if (disc)
+      disc[b] = discarded_rel(w, kmax, kb[b], beyond, h[(size_t)nb * (kmax + 1) + b]);
+  }
+  for (int b = 1; b < nb; ++b)
+    if (kb[b] != kb[0]) return kGroupSplit;
+  if (refine && nb > 1) return kGroupSplit;
+  int k = kb[0];
+  if (refine) {
+    // one instance: the rule keeps directions the Gram does not resolve
+    std::vector<double> w(h.begin(), h.begin() + kmax);
+    T* U1 = U;
+    if (!rows) {  // restart in the rows orientation: K = M M^H (m x m), W = U^H M
+      T* Kr = ar.get<T>((size_t)m * m);
+      double* lamr = ar.get<double>(m);
+      T* Ur = ar.get<T>((size_t)m * kmax);
+      char* wr = ar.get<char>(eig_workspace_bytes(m, kmax, ops<T>::cplx));
+      W = kp.get<T>((size_t)kmax * n);
+      CKA(Kr); CKA(lamr); CKA(Ur); CKA(wr);
+      if (!W) return cuda_fail(kp.err, "workspace allocation L");
+      CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n), false, M, View::transposed(n),
+                  true, Kr, View::rowmajor(m), s));
+      CK(heev_top<T>(Kr, m, kmax, kmax, 0.0, -1.0, lamr, Ur, sc.k, wr, sc.status, num_sms(), s,
+                     1, o.concurrent, false));
+      CK(tgemm<T>(pr, true, false, kmax, n, m, Ur, View::transposed(kmax), true, M,
+                  View::rowmajor(n), false, W, View::rowmajor(n), s));
+      CK(row_norms2<T>(W, kmax, n, n, 0, w_dev, s));
+      CK(cudaMemcpyAsync(w.data(), w_dev, sizeof(double) * kmax, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (!all_finite(w)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
+      U1 = Ur;
+    }
+    const int jr = resolved_prefix(w.data(), kmax, res);
+    double d = 0.0;
+    int rc = refine_rows<T>(ar, pr, M, m, n, kmax, jr, U1, W, w, max_bond, tol, floor_rel, o, sc,
+                            s, &k, &d);
+    if (rc != CBC_OK) return rc;
+    if (disc) disc[0] = d;
+    T* L = W;  // rows orientation: the first k rows
+    CK(normalize_inplace<T>(L, (int64_t)k * n, sc.log_fwd, sc.status, sc.scratch, s, 1));
+    if (keep) ar.release(mk);
+    *Lout = L;
+    *kout = k;
+    return CBC_OK;
+  }
   const int64_t lbs = (int64_t)k * n;
-  if (m <= n) {  // L = U_k^H M
-    CK(tgemm<T>(pr, true, false, k, n, m, U, View::transposed(kmax, (int64_t)g * kmax), true, M,
-                View::rowmajor(n, mbs), false, L, View::rowmajor(n, lbs), s));
-  } else {       // L = diag(sqrt(lambda_k)) V_k^H
-    CK(scaled_adjoint<T>(U, kmax, lam, sc.k, n, L, s, nb, lbs));
+  T* L;
+  if (rows) {
+    L = W;
+    if (nb > 1 && k < kmax) {  // instances back to back, k rows each
+      L = kp.get<T>((size_t)nb * lbs);
+      if (!L) return cuda_fail(kp.err, "workspace allocation L");
+      CK(copy_batched<T>(W, wbs, L, lbs, lbs, s, nb));
+      kp.drop(W);
+    }
+  } else {     // L = diag(sqrt(w_k)) V_k^H
+    L = kp.get<T>((size_t)nb * lbs);
+    if (!L) return cuda_fail(kp.err, "workspace allocation L");
+    CK(scaled_adjoint_w<T>(U, kmax, w_dev, kmax, k, n, L, lbs, s, nb));
   }
   CK(normalize_inplace<T>(L, lbs, sc.log_fwd, sc.status, sc.scratch, s, nb));
   if (keep) ar.release(mk);
@@ -293,6 +485,8 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
   };
 
   // forward sweep: L^[0] = 1, Eq. (tt_cbc_first_contraction), compression of (chi, sigma')
+  std::vector<std::vector<double>> disc(nb, std::vector<double>(L, 0.0));
+  std::vector<double> dcut(nb, 0.0);
   std::vector<T*> env(L, nullptr);
   std::vector<int> chi(L, 1);
   env[0] = ar.get<T>(nb);
@@ -331,8 +525,9 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     // F3: compress M[(chi sigma'), (b' a')]
     int k = 0;
     rc = compress_rows<T>(tmp, pr, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k,
-                          &ar);
+                          &ar, dcut.data());
     if (rc != CBC_OK) return rc;
+    for (int b = 0; b < nb; ++b) disc[b][i + 1] = dcut[b];
     chi[i + 1] = k;
     tmp.release(mk);
   }
@@ -352,6 +547,7 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     out->stream = (nb == 1) ? s : sts[b]->stream;
     out->data.assign(L, nullptr);
     out->numel.assign(L, 0);
+    out->discarded = disc[b];
   }
   T* R = ar.get<T>(nb);
   CKA(R);
@@ -395,7 +591,7 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     const int64_t nbs = formed ? (int64_t)m * n : (int64_t)n * n;  // node stride in the group
     T* node = nullptr;
     if (nb == 1) {  // built in the output tensor itself
-      CK(cudaMallocAsync(reinterpret_cast<void**>(&node), sizeof(T) * std::max<size_t>((size_t)cn * n, (size_t)m * n), s));
+      CK(pool_malloc(reinterpret_cast<void**>(&node), sizeof(T) * std::max<size_t>((size_t)cn * n, (size_t)m * n), s));
       outs[0]->data[i] = node;
     } else {
       node = tmp.get<T>((size_t)nb * nbs);
@@ -411,7 +607,7 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
       if (nb == 1) return CBC_OK;
       std::vector<void*> h(nb);
       for (int b = 0; b < nb; ++b) {
-        CK(cudaMallocAsync(&h[b], sizeof(T) * (size_t)cn * n, s));
+        CK(pool_malloc(&h[b], sizeof(T) * (size_t)cn * n, s));
         outs[b]->data[i] = h[b];
       }
       T** tab = tmp.get<T*>(nb);
@@ -642,6 +838,7 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
   };
 
   // ---- step 1, Eq. (cbc_tree_first_contraction): subtree environments, leaves first
+  std::vector<double> disc(n, 0.0);  // per edge: steps 1 and 2
   std::vector<T*> Lsub(n, nullptr);
   std::vector<int64_t> chi_sub(n, 1);
   for (int i : post) {
@@ -661,9 +858,11 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
     int rc = contract_node(i, envs, lo, true, &M);
     if (rc != CBC_OK) return rc;
     int k = 0;
+    double dc = 0.0;
     rc = compress_rows<T>(ar, pr, M.p, (int)m, (int)(op.bond[i] * st.bond[i]), max_bond, tol, o,
-                          sc, s, &Lsub[i], &k);
+                          sc, s, &Lsub[i], &k, nullptr, &dc);
     if (rc != CBC_OK) return rc;
+    disc[i] += dc;
     chi_sub[i] = k;
   }
   // ---- step 2, Eq. (cbc_tree_second_contraction): complements, root first
@@ -692,9 +891,11 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
       int rc = contract_node(i, envs, lo, true, &M);
       if (rc != CBC_OK) return rc;
       int kk = 0;
+      double dc = 0.0;
       rc = compress_rows<T>(ar, pr, M.p, (int)m, (int)(op.bond[k] * st.bond[k]), max_bond, tol, o,
-                            sc, s, &Ldown[k], &kk);
+                            sc, s, &Ldown[k], &kk, nullptr, &dc);
       if (rc != CBC_OK) return rc;
+      disc[k] += dc;
       chi_down[k] = kk;
     }
   }
@@ -710,6 +911,7 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
   out->stream = s;
   out->data.assign(n, nullptr);
   out->numel.assign(n, 0);
+  out->discarded = disc;
   std::vector<T*> R(n, nullptr);
   std::vector<int64_t> chi_r(n, 1);
   for (int i : post) {
@@ -733,7 +935,7 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
     const int nzi = (int)nz;
     const int cn = (m < nzi) ? m : nzi;  // square or tall: Q = I (exact, as on chains)
     T* node = nullptr;
-    CK(cudaMallocAsync(reinterpret_cast<void**>(&node),
+    CK(pool_malloc(reinterpret_cast<void**>(&node),
                        sizeof(T) * std::max<size_t>((size_t)cn * nzi, (size_t)m * nzi), s));
     out->data[i] = node;
     out->numel[i] = (int64_t)cn * nzi;
@@ -779,6 +981,37 @@ bool is_chain(const Net& t) {
 }
 
 }  // namespace
+
+// The rank rule on weights w[0..kmax) in the order of the candidates (descending) and
+// the weight `beyond` outside them (used by the tolerance rule only): keep w_j >
+// floor^2 w_0 (a prefix), then the smallest k whose discarded weight sum_{j>=k} w_j +
+// beyond <= tol^2 (sum_j w_j + beyond) when tol > 0, then at most max_bond; at least 1.
+// This is the oracle's rule with w_j = s_j^2.
+int pick_rank(const double* w, int kmax, double beyond, int64_t max_bond, double tol,
+              double floor_rel) {
+  if (kmax <= 0 || !(w[0] > 0.0)) return 1;
+  int k = 0;
+  const double fl = floor_rel * floor_rel * w[0];
+  while (k < kmax && w[k] > fl) ++k;
+  if (tol > 0.0) {
+    std::vector<double> tail(kmax + 1);
+    tail[kmax] = std::max(beyond, 0.0);
+    for (int q = kmax - 1; q >= 0; --q) tail[q] = tail[q + 1] + std::max(w[q], 0.0);
+    const double thr = tol * tol * tail[0];
+    int kt = 0;
+    while (kt < kmax && tail[kt] > thr) ++kt;
+    k = std::min(k, std::max(kt, 1));
+  }
+  if (max_bond > 0 && k > max_bond) k = (int)max_bond;
+  return std::max(k, 1);
+}
+
+// number of leading directions with w_j > res * w_0
+int resolved_prefix(const double* w, int kmax, double res) {
+  int j = 0;
+  while (j < kmax && w[j] > res * w[0]) ++j;
+  return j;
+}
 
 int run_cbc_group(const std::vector<const Net*>& sts, const std::vector<const Net*>& ops,
                   int64_t max_bond, double tol, const Options& o, const std::vector<Net*>& outs) {

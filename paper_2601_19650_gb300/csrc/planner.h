@@ -23,6 +23,9 @@ struct Net {
   std::vector<int64_t> numel;
   void* block = nullptr;  // when set, data[i] point into this one allocation
   double log_norm = 0.0;
+  // outputs of cbc_apply: relative weight discarded on the edge of node i to its parent
+  // (the forward compression on a chain; steps 1 and 2 added on a tree), 0 at the root
+  std::vector<double> discarded;
   cudaStream_t stream = nullptr;
   size_t elem_bytes() const { return cplx ? 16 : 8; }
   virtual ~Net();
@@ -30,7 +33,10 @@ struct Net {
 
 struct Options {
   int precision = CBC_PREC_FP64;
-  double eps_rank = 1e-6;
+  // rank floor: singular values s_j <= eps_rank * s_0 are dropped.  FP64 keeps the
+  // oracle's floor; the mixed path's products resolve s only to ~3e-11 s_0, so its floor
+  // sits above that (set by parse_options when the caller gives none)
+  double eps_rank = 1e-12;
   int slices_fwd = 5;
   int slices_bwd = 4;
   // set for instances that run next to others on their own streams (cbc_apply_batched):
@@ -41,6 +47,21 @@ struct Options {
 
 int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
             Net* out);
+
+// Truncation rank rule shared by the planners (planner.cu): weights w[0..kmax) of the
+// candidate directions of a compression in descending order (w_j = s_j^2 measured on
+// the factor), `beyond` the weight outside them (used when tol > 0): keep w_j > floor^2
+// w_0 (a prefix), then the smallest k with sum_{j>=k} w_j + beyond <= tol^2 (sum_j w_j +
+// beyond), then at most max_bond, at least 1.
+int pick_rank(const double* w, int kmax, double beyond, int64_t max_bond, double tol,
+              double floor_rel);
+// number of leading candidates with w_j > res * w_0 (directions the Gram resolves)
+int resolved_prefix(const double* w, int kmax, double res);
+// Directions whose weight is below kResolved * w_0 are not trusted as singular
+// directions: the Gram's own rounding (FP64: ~m eps w_0; mixed: ~1e-12 w_0 from the
+// operand slices and the double-float reduction) is too close.
+constexpr double kResolvedFP64 = 1e-10;
+constexpr double kResolvedMixed = 1e-8;
 
 // A group (see run_cbc_group) that cannot run in lockstep: shapes differ, a tree, or the
 // instances chose different ranks at some cut.  The caller runs the members one by one.
@@ -62,6 +83,10 @@ struct KTimer {
 
 void note_launches(int cls, int n);
 void note_flops(int cls, double flops);
+
+// stream-ordered device allocation from the library's own pool on the current device
+// (freed with cudaFreeAsync); the caller's default pool is never touched
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
 
 int fail(int code, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
