@@ -49,7 +49,7 @@ WORKLOADS = {
                   input_dtype="complex64"),
 }
 DEFAULT_B = {"mpo_mps": 32, "tree": 8, "serving": 256, "large": 1}
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 figure in MEASURED_PEAKS)
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64, nominal: the fallback when the DGEMM probe fails
 # DRAM bytes per launch of a class's dominant kernel, read from an ncu capture of this
 # workload; each entry names the summary under profiles/ it comes from.  A class whose
 # kernel changed after its capture has no entry (traffic null).
@@ -177,6 +177,30 @@ def oracle_time(prob, reps: int = 1):
     return (time.perf_counter() - t0) / reps, res
 
 
+def measure_fp64_peak(device, n: int = 8192, reps: int = 3):
+    """FP64 throughput of a cuBLAS DGEMM (torch.matmul, n^3, 2 n^3 flops) on this GPU:
+    the best of `reps` back-to-back runs after one warm-up, timed with CUDA events.  The
+    FP64 rooflines of the report use it as their peak (no FP64 figure is driver-written)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device=device)
+    b = torch.randn(n, n, dtype=torch.float64, device=device)
+    c = a @ b
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b, c
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12, {"gemm": f"cuBLAS DGEMM via torch.matmul, {n}^3",
+                                               "best_ms": best, "reps": reps}
+
+
 def blas_threads() -> int:
     try:
         from threadpoolctl import threadpool_info
@@ -232,6 +256,10 @@ def main():
                     help="mpo_mps (the headline), tree, serving, large")
     ap.add_argument("--sites", type=int, default=0,
                     help="shorter chains for profiling captures (default: the workload's 64)")
+    ap.add_argument("--no-fp64-arm", action="store_true",
+                    help="skip timing the same step in plain FP64 (the ratio's denominator)")
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="timed steps of the FP64 arm (after one warm-up step)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -288,6 +316,14 @@ def main():
         prec_name = "mixed"
     prec = _cbc.CBC_PREC_MIXED if prec_name == "mixed" else _cbc.CBC_PREC_FP64
 
+    # FP64 peak for the FP64 rooflines: a cuBLAS DGEMM on this GPU (untimed region)
+    try:
+        fp64_peak, fp64_peak_info = measure_fp64_peak(f"cuda:{local}")
+        fp64_note = "of measured cuBLAS DGEMM"
+    except Exception as exc:  # e.g. out of memory: the nominal figure, said so
+        fp64_peak, fp64_peak_info = FP64_NOMINAL_TFLOPS, {"error": str(exc)[:120]}
+        fp64_note = "of nominal (152 SMs x 2 DFMA/clk x ~2.06 GHz)"
+
     # L2 flush buffer (larger than the 129 MB L2), written between timed steps
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
 
@@ -304,35 +340,42 @@ def main():
             gpu_index = local
     clocks = ClockSampler(gpu_index)
 
+    def timed_arm(prec_arm, steps, single=False):
+        """`steps` timed steps (L2 flushed before each, untimed); each step is the B
+        instances through cbc_apply_batched, or instance 0 alone through cbc_apply.
+        Returns the summed CUDA-event time and the last step's outputs."""
+        t_ms, last_outs = 0.0, None
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            for sm in streams[1:]:
+                sm.wait_event(e0)
+            if single:
+                outs = [_cbc.cbc_apply(hs, ho, prob.max_bond, 0.0, _cbc.make_options(prec_arm))]
+            else:
+                outs = apply_once(prec_arm)
+            for sm in streams[1:]:
+                ev = torch.cuda.Event()
+                ev.record(sm)
+                stream.wait_event(ev)
+            e1.record(stream)
+            e1.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            if last_outs is not None:
+                destroy(last_outs)
+            last_outs = outs
+        return t_ms, last_outs
+
     _cbc.cbc_stats_reset()
     _cbc.cbc_stats_enable(True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    total_ms = 0.0
-    last = None
-    for k in range(args.steps):
-        # flush L2 (untimed), then time the step from a point all streams wait on to the
-        # point where all of them are done
-        with torch.cuda.stream(stream):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        for sm in streams[1:]:
-            sm.wait_event(e0)
-        outs = apply_once(prec)
-        for sm in streams[1:]:
-            ev = torch.cuda.Event()
-            ev.record(sm)
-            stream.wait_event(ev)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        if last is not None:
-            destroy(last)
-        last = outs
+    total_ms, last = timed_arm(prec, args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -375,8 +418,9 @@ def main():
             achieved = issued / (d["ms"] / 1e3) / 1e12
             note = f"bf16 slice products issued on the tensor pipe, {bf16_note}"
         else:
-            peak, bound = FP64_PEAK_TFLOPS, "alu"
-            note = "FP64 pipe, nominal 1.25 TFLOP/s (152 SMs x 2 DFMA/clk x ~2.06 GHz)"
+            peak, bound = fp64_peak, "alu"
+            note = (f"FP64-equivalent flops over the class's event time, {fp64_note} "
+                    f"({fp64_peak:.3f} TFLOP/s)")
         # the captured traffic belongs to the default step (32 instances, 64 sites)
         default_step = args.workload == "mpo_mps" and B == 32 and args.sites == 0
         prof = PROFILED_TRAFFIC.get(dom, {}) if default_step else {}
@@ -407,24 +451,30 @@ def main():
             "roofline": roofline,
             "roofline_tensor": roofline_tc,
             "gpu_launches": int(sum(v["launches"] for v in stats.values())),
-            "clocks": clock_info}
+            "clocks": clock_info,
+            "fp64_peak": dict(fp64_peak_info, tflops=fp64_peak, note=fp64_note)}
 
     if args.sites > 0:  # a shortened chain: not the headline workload
         line["config"]["L"] = args.sites
         line["config"]["workload"] = line["config"]["workload"].replace("L=64", f"L={args.sites}")
     # parity of this run's output with the oracle, and the oracle's own time
+    ref = None
+    shape0 = _cbc.output_shape_fn(st.parent, st.phys)
+    cplx0 = bool(np.iscomplexobj(st.tensors[0]))
+
+    def err_vs_oracle(out):
+        from oracle import metrics
+        tens, bonds, log_norm = _cbc.fetch_network(out, shape0, cplx0)
+        return metrics.rel_err(st.parent, tens, ref.tensors, log_norm, 0.0)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "large":
         line["cpu_baseline"] = None
         line["cpu_baseline_note"] = "not timed: the FP64 oracle needs hours per application here"
     elif rank == 0 and world == 1 and not args.no_cpu_baseline:
-        from oracle import metrics
         # instance 0 against the oracle; the oracle timed on instances 0, 1, ... until about
         # 20 s of host time (a bounded sample of the step's instances)
         t_or, ref = oracle_time(prob)
-        shape = _cbc.output_shape_fn(st.parent, st.phys)
-        tens, bonds, log_norm = _cbc.fetch_network(last[0], shape,
-                                                   bool(np.iscomplexobj(st.tensors[0])))
-        line["rel_err_vs_oracle"] = metrics.rel_err(st.parent, tens, ref.tensors, log_norm, 0.0)
+        line["rel_err_vs_oracle"] = err_vs_oracle(last[0])
         n_or, t_sum = 1, t_or
         while t_sum < 20.0 and n_or < len(probs):
             t_sum += oracle_time(probs[n_or])[0]
@@ -435,6 +485,34 @@ def main():
                                           f"step (seeds {rank * B}..{rank * B + n_or - 1})"}
     if last is not None:
         destroy(last)
+
+    # the denominator of the headline ratio: the same B instances in plain FP64 through
+    # cbc_apply_batched, and instance 0 alone through cbc_apply ("plain FP64 GPU CBC"),
+    # timed like the headline step
+    if (prec == _cbc.CBC_PREC_MIXED and not args.no_fp64_arm
+            and args.workload in ("mpo_mps", "tree")):
+        f64 = _cbc.CBC_PREC_FP64
+        destroy(timed_arm(f64, 1)[1])
+        t64, out64 = timed_arm(f64, args.fp64_steps)
+        t64 = max_over_ranks(t64, dist, f"cuda:{local}")
+        n1 = max(3, args.fp64_steps)
+        destroy(timed_arm(f64, 1, single=True)[1])
+        t1, out1 = timed_arm(f64, n1, single=True)
+        t1 = max_over_ranks(t1, dist, f"cuda:{local}")
+        fp64_value = whole_job_value(world, B, args.fp64_steps, t64)
+        fp64_single = world * n1 / (t1 / 1e3)
+        line["fp64"] = {"value": fp64_value, "unit": "applications/s",
+                        "ms_per_step": t64 / args.fp64_steps, "steps": args.fp64_steps,
+                        "warmup": 1, "batching": line["config"]["batching"],
+                        "single_application_value": fp64_single,
+                        "single_application_ms": t1 / n1}
+        line["mixed_over_fp64"] = value / fp64_value
+        line["mixed_over_fp64_single"] = value / fp64_single
+        if ref is not None:
+            line["fp64"]["rel_err_vs_oracle"] = err_vs_oracle(out64[0])
+            line["fp64"]["single_rel_err_vs_oracle"] = err_vs_oracle(out1[0])
+        destroy(out64)
+        destroy(out1)
 
     # end to end through the C ABI with host buffers: H2D of the inputs, the application,
     # D2H of every output tensor, each step

@@ -68,11 +68,16 @@ int cholqr2_t(int m, int n, int nb, T* S, cudaStream_t s) {
   T* G = nullptr;
   int* status = nullptr;
   void* bar = nullptr;
+  double* rn = nullptr;
   cudaError_t e = pool_malloc(reinterpret_cast<void**>(&G), sizeof(T) * (size_t)m * m * nb, s);
   if (e == cudaSuccess) e = pool_malloc(reinterpret_cast<void**>(&status), sizeof(int), s);
   if (e == cudaSuccess) e = pool_malloc(&bar, sizeof(GridBarrier) * nb, s);
+  if (e == cudaSuccess) e = pool_malloc(reinterpret_cast<void**>(&rn), sizeof(double) * m * nb, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), s);
   const int64_t sbs = (int64_t)m * n;
+  // unit rows first (the sweeps do the same): same row space, better conditioned Gram
+  if (e == cudaSuccess) e = row_norms2<T>(S, m, n, n, sbs, rn, s, nb);
+  if (e == cudaSuccess) e = scale_rows<T>(S, m, n, sbs, rn, s, nb);
   for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
     e = gemm_f64<T>(m, m, n, nb, S, View::rowmajor(n, sbs), false, S, View::transposed(n, sbs),
                     true, G, View::rowmajor(m, (int64_t)m * m), s);
@@ -84,6 +89,7 @@ int cholqr2_t(int m, int n, int nb, T* S, cudaStream_t s) {
   if (G) cudaFreeAsync(G, s);
   if (status) cudaFreeAsync(status, s);
   if (bar) cudaFreeAsync(bar, s);
+  if (rn) cudaFreeAsync(rn, s);
   cudaError_t e2 = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "cbc_cholqr2");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cbc_cholqr2: synchronize");

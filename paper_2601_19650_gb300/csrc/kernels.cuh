@@ -131,6 +131,11 @@ cudaError_t row_norms2(const T* W, int rows, int cols, int64_t ld, int64_t bs, d
 template <typename T>
 cudaError_t col_norms2(const T* W, int rows, int cols, int64_t ld, int64_t bs, double* out,
                        cudaStream_t s, int nb = 1);
+// rows r of nb row-major matrices (rows x cols, bs elements apart) scaled by
+// 1 / sqrt(norms2[b * rows + r]) (rows of zero norm are left alone)
+template <typename T>
+cudaError_t scale_rows(T* X, int rows, int cols, int64_t bs, const double* norms2,
+                       cudaStream_t s, int nb = 1);
 // out[b] = sum_i |A_b[i] - B_b[i]|^2 over n contiguous elements (A_b = A + b * a_bs,
 // B_b = B + b * n); C_b = A_b - B_b as well when C is not NULL (C_b = C + b * n)
 template <typename T>

@@ -223,6 +223,18 @@ __global__ void scaled_adjoint_w_kernel(const T* V, int ldv, const double* w, in
 }
 
 template <typename T>
+__global__ void scale_rows_kernel(T* X, int rows, int cols, int64_t bs, const double* norms2) {
+  X += (int64_t)blockIdx.y * bs;
+  norms2 += (int64_t)blockIdx.y * rows;
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double nr = norms2[t / cols];
+    if (nr > 0.0) X[t] = ops<T>::scale(rsqrt(nr), X[t]);
+  }
+}
+
+template <typename T>
 __global__ void copy_batched_kernel(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n) {
   src += (int64_t)blockIdx.y * s_bs;
   dst += (int64_t)blockIdx.y * d_bs;
@@ -444,6 +456,15 @@ cudaError_t scaled_adjoint_w(const T* V, int ldv, const double* w, int64_t w_bs,
 }
 
 template <typename T>
+cudaError_t scale_rows(T* X, int rows, int cols, int64_t bs, const double* norms2,
+                       cudaStream_t s, int nb) {
+  note_launches(CBC_K_AUX, 1);
+  scale_rows_kernel<T><<<dim3(std::min(grid_for((int64_t)rows * cols), std::max(1, 2048 / nb)),
+                              nb), 256, 0, s>>>(X, rows, cols, bs, norms2);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n,
                          cudaStream_t s, int nb) {
   if (n <= 0) return cudaSuccess;
@@ -464,7 +485,8 @@ cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64
   template cudaError_t scaled_adjoint_w<T>(const T*, int, const double*, int64_t, int, int,  \
                                            T*, int64_t, cudaStream_t, int);                  \
   template cudaError_t copy_batched<T>(const T*, int64_t, T*, int64_t, int64_t, cudaStream_t, \
-                                       int);
+                                       int);                                                 \
+  template cudaError_t scale_rows<T>(T*, int, int, int64_t, const double*, cudaStream_t, int);
 CBC_MISC_INST(double)
 CBC_MISC_INST(zdbl)
 #undef CBC_MISC_INST

@@ -153,6 +153,7 @@ int sweeps(const Args& a, Bump& b, bool dry) {
     if (!dry) {
       const T* Ti = static_cast<const T*>(a.st[i]);
       const T* Wi = static_cast<const T*>(a.op[i]);
+      NA_CK(cudaMemsetAsync(wv, 0, sizeof(double) * (kmax + 2), s));
       NA_CK(gemm_f64<T>(c * bb, d * a2, aa, 1, env[i], View::rowmajor(aa), false, Ti,
                         View::rowmajor(d * a2), false, X, View::rowmajor(d * a2), s));
       View vw;
@@ -180,6 +181,7 @@ int sweeps(const Args& a, Bump& b, bool dry) {
                           false, Wc, View::rowmajor(kmax), s));
         NA_CK(col_norms2<T>(Wc, m, kmax, kmax, 0, wv, s));
       }
+      NA_CK(sum_squares<T>(Lp, (int64_t)m * n, wv + kmax + 1, s));  // the cut's weight
       if (a.tol > 0.0) {  // weight outside the candidates
         if (rows)
           NA_CK(gemm_f64<T>(m, n, kmax, 1, U, View::rowmajor(kmax), false, envn, View::rowmajor(n),
@@ -189,22 +191,28 @@ int sweeps(const Args& a, Bump& b, bool dry) {
                             View::transposed(kmax), true, P, View::rowmajor(n), s));
         NA_CK(diff_sumsq<T>(Lp, (int64_t)m * n, P, nullptr, (int64_t)m * n, wv + kmax, s));
       }
-      std::vector<double> hw(kmax + 1, -1.0);
+      std::vector<double> hw(kmax + 2, 0.0);
+      double w_next = 0.0;
       int hs = 0;
-      NA_CK(cudaMemcpyAsync(hw.data(), wv, sizeof(double) * (kmax + (a.tol > 0.0 ? 1 : 0)),
-                            cudaMemcpyDeviceToHost, s));
+      NA_CK(cudaMemcpyAsync(hw.data(), wv, sizeof(double) * (kmax + 2), cudaMemcpyDeviceToHost, s));
+      if (kmax < g)
+        NA_CK(cudaMemcpyAsync(&w_next, lam + kmax, sizeof(double), cudaMemcpyDeviceToHost, s));
       NA_CK(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, s));
       NA_CK(cudaStreamSynchronize(s));
       if (hs != 0) return fail(hs, "cbc_apply_tt_noalloc: device status %d", hs);
-      for (int j = 0; j < kmax + (a.tol > 0.0 ? 1 : 0); ++j)
+      if (hw[kmax + 1] == 0.0)
+        return fail(CBC_ERR_NUMERICAL, "cbc_apply_tt_noalloc: O|psi> vanishes");
+      for (int j = 0; j < kmax + 2; ++j)
         if (!std::isfinite(hw[j]))
           return fail(CBC_ERR_NUMERICAL, "cbc_apply_tt_noalloc: NaN or Inf in a truncation");
       k = pick_rank(hw.data(), kmax, a.tol > 0.0 ? hw[kmax] : -1.0, a.max_bond, a.tol, floor_rel);
-      if (k > resolved_prefix(hw.data(), kmax, kResolvedFP64) && k < g)
+      const double nu = 4.0 * std::sqrt((double)g) * 1.1102230246251565e-16;
+      if (refine_start(hw.data(), kmax, g, k, w_next, hw[kmax + 1], a.tol, nu, 1e-11,
+                       kResolvedFP64) >= 0)
         return fail(CBC_ERR_UNSUPPORTED,
-                    "cbc_apply_tt_noalloc: the rank rule keeps directions below the Gram's "
-                    "resolution at site %d (singular values under 1e-5 of the largest); "
-                    "cbc_apply refines those, this entry point does not", i);
+                    "cbc_apply_tt_noalloc: the cut at site %d falls among directions the "
+                    "Gram does not resolve (small singular values close together); cbc_apply "
+                    "refines those, this entry point does not", i);
       if (!rows) NA_CK(scaled_adjoint_w<T>(U, kmax, wv, kmax, k, n, envn, 0, s));
       NA_CK(normalize_inplace<T>(envn, (int64_t)k * n, log_fwd, status, dscr, s));
     }
@@ -255,6 +263,7 @@ int sweeps(const Args& a, Bump& b, bool dry) {
     NA_GET(Y, T, (size_t)a_in * d * cp * b_out);
     NA_GET(Z, T, (size_t)b_in * a_in * d * cp);
     NA_GET(G, T, (size_t)m * m);
+    NA_GET(rn, double, m);
     if (!dry) {
       T* node = reinterpret_cast<T*>(a.out) + out_used;
       a.out_off[i] = out_used;
@@ -278,6 +287,9 @@ int sweeps(const Args& a, Bump& b, bool dry) {
         break;
       }
       if (m < n) {
+        // unit rows first (same row space, a well-conditioned Gram), as cbc_apply does
+        NA_CK(row_norms2<T>(node, m, n, n, 0, rn, s));
+        NA_CK(scale_rows<T>(node, m, n, 0, rn, s));
         for (int rep = 0; rep < 2; ++rep) {
           NA_CK(gemm_f64<T>(m, m, n, 1, node, View::rowmajor(n), false, node, View::transposed(n),
                             true, G, View::rowmajor(m), s));

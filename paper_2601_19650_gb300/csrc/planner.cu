@@ -195,6 +195,7 @@ int refine_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int kmax, i
   char* work = ar.get<char>(eig_workspace_bytes(m, k2, ops<T>::cplx));
   double* dv = ar.get<double>(k2 + 4);
   CKA(P); CKA(R); CKA(K2); CKA(lam2); CKA(U2); CKA(C); CKA(P2); CKA(work); CKA(dv);
+  CK(cudaMemsetAsync(dv, 0, sizeof(double) * (k2 + 4), s));
   // R = M - U1[:, :j0] W1[:j0]
   if (j0 > 0) {
     CK(tgemm<T>(pr, true, false, m, n, j0, U1, View::rowmajor(kmax), false, W1,
@@ -265,6 +266,7 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
   double* w_dev = dv;
   double* beyond_dev = dv + (size_t)nb * kmax;
   double* total_dev = beyond_dev + nb;
+  CK(cudaMemsetAsync(dv, 0, sizeof(double) * (size_t)nb * (kmax + 2), s));
   CK(sum_squares<T>(M, mbs, total_dev, s, nb));  // ||M||_F^2, the weight of the cut
   if (rows) {
     CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n, mbs), false, M,
@@ -306,63 +308,85 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
     CK(diff_sumsq<T>(M, mbs, P, nullptr, mbs, beyond_dev, s, nb));
   }
   std::vector<double> h((size_t)nb * (kmax + 2));
+  std::vector<double> hl(kmax < g ? (size_t)nb * g : 0);
   int hs = 0;
   CK(cudaMemcpyAsync(h.data(), dv, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+  if (!hl.empty())
+    CK(cudaMemcpyAsync(hl.data(), lam, sizeof(double) * hl.size(), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(&hs, sc.status, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (hs != 0) return status_to_rc(hs);
-  if (!all_finite(h)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
   for (int b = 0; b < nb; ++b)
-    if (!(h[(size_t)nb * (kmax + 1) + b] > 0.0))
+    if (h[(size_t)nb * (kmax + 1) + b] == 0.0)
       return fail(CBC_ERR_NUMERICAL, "cbc_apply: O|psi> vanishes (a compression of zero weight)");
-  std::vector<int> kb(nb), j0(nb);
-  bool refine = false;
+  if (!all_finite(h)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
+  // the Gram's relative error (FP64: accumulation over the sqrt(g)-ish random walk of
+  // g products; mixed: the operand slices and the double-float reduction) and the state
+  // error a cut may add (a fraction of each path's bar, 1e-10 and 1e-6)
+  const double nu = pr.mixed ? 5e-12 : 4.0 * std::sqrt((double)g) * 1.1102230246251565e-16;
+  const double target = pr.mixed ? 1e-7 : 1e-11;
+  std::vector<int> kb(nb), jlo(nb);
+  std::vector<std::vector<double>> wb(nb);
+  bool any_refine = false;
   for (int b = 0; b < nb; ++b) {
-    const double* w = h.data() + (size_t)b * kmax;
+    wb[b].assign(h.begin() + (size_t)b * kmax, h.begin() + (size_t)(b + 1) * kmax);
     const double beyond = (tol > 0.0) ? h[(size_t)nb * kmax + b] : -1.0;
-    kb[b] = pick_rank(w, kmax, beyond, max_bond, tol, floor_rel);
-    j0[b] = resolved_prefix(w, kmax, res);
-    // a real cut (k < g) among directions the Gram does not resolve; keeping every
-    // direction needs no choice of subspace
-    if (kb[b] > j0[b] && kb[b] < g) refine = true;
-    if (disc)
-      disc[b] = discarded_rel(w, kmax, kb[b], beyond, h[(size_t)nb * (kmax + 1) + b]);
+    const double total = h[(size_t)nb * (kmax + 1) + b];
+    kb[b] = pick_rank(wb[b].data(), kmax, beyond, max_bond, tol, floor_rel);
+    const double w_next = (kmax < g) ? hl[(size_t)b * g + kmax] : 0.0;
+    jlo[b] = refine_start(wb[b].data(), kmax, g, kb[b], w_next, total, tol, nu, target, res);
+    if (jlo[b] >= 0) any_refine = true;
+    if (disc) disc[b] = discarded_rel(wb[b].data(), kmax, kb[b], beyond, total);
+  }
+  bool restarted = false;  // cols orientation redone in rows orientation (one instance)
+  if (any_refine) {
+    if (!rows && nb > 1) return kGroupSplit;
+    Prec p1 = pr;
+    p1.nb = 1;
+    Scalars s1 = sc;
+    for (int b = 0; b < nb; ++b) {
+      if (jlo[b] < 0) continue;
+      const T* Mb = M + (size_t)b * mbs;
+      T* U1 = U + (size_t)b * ubs;
+      T* Wb = W + (size_t)b * wbs;
+      std::vector<double>& w = wb[b];
+      if (!rows) {  // restart in the rows orientation: K = M M^H (m x m), W = U^H M
+        T* Kr = ar.get<T>((size_t)m * m);
+        double* lamr = ar.get<double>(m);
+        T* Ur = ar.get<T>((size_t)m * kmax);
+        char* wr = ar.get<char>(eig_workspace_bytes(m, kmax, ops<T>::cplx));
+        Wb = kp.get<T>((size_t)kmax * n);
+        CKA(Kr); CKA(lamr); CKA(Ur); CKA(wr);
+        if (!Wb) return cuda_fail(kp.err, "workspace allocation L");
+        CK(tgemm<T>(p1, true, true, m, m, n, Mb, View::rowmajor(n), false, Mb, View::transposed(n),
+                    true, Kr, View::rowmajor(m), s));
+        CK(heev_top<T>(Kr, m, kmax, kmax, 0.0, -1.0, lamr, Ur, sc.k, wr, sc.status, num_sms(), s,
+                       1, o.concurrent, false));
+        CK(tgemm<T>(p1, true, false, kmax, n, m, Ur, View::transposed(kmax), true, Mb,
+                    View::rowmajor(n), false, Wb, View::rowmajor(n), s));
+        CK(row_norms2<T>(Wb, kmax, n, n, 0, w_dev, s));
+        CK(cudaMemcpyAsync(w.data(), w_dev, sizeof(double) * kmax, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!all_finite(w)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
+        int j = 0;
+        while (j < kmax && w[j] > 100.0 * w[std::max(0, kb[b] - 1)]) ++j;
+        jlo[b] = std::max(1, std::min(j, resolved_prefix(w.data(), kmax, res)));
+        U1 = Ur;
+        W = Wb;
+        restarted = true;
+      }
+      double d = 0.0;
+      int rc = refine_rows<T>(ar, p1, Mb, m, n, kmax, jlo[b], U1, Wb, w, max_bond, tol, floor_rel,
+                              o, s1, s, &kb[b], &d);
+      if (rc != CBC_OK) return rc;
+      if (disc) disc[b] = d;
+    }
   }
   for (int b = 1; b < nb; ++b)
     if (kb[b] != kb[0]) return kGroupSplit;
-  if (refine && nb > 1) return kGroupSplit;
   int k = kb[0];
-  if (refine) {
-    // one instance: the rule keeps directions the Gram does not resolve
-    std::vector<double> w(h.begin(), h.begin() + kmax);
-    T* U1 = U;
-    if (!rows) {  // restart in the rows orientation: K = M M^H (m x m), W = U^H M
-      T* Kr = ar.get<T>((size_t)m * m);
-      double* lamr = ar.get<double>(m);
-      T* Ur = ar.get<T>((size_t)m * kmax);
-      char* wr = ar.get<char>(eig_workspace_bytes(m, kmax, ops<T>::cplx));
-      W = kp.get<T>((size_t)kmax * n);
-      CKA(Kr); CKA(lamr); CKA(Ur); CKA(wr);
-      if (!W) return cuda_fail(kp.err, "workspace allocation L");
-      CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n), false, M, View::transposed(n),
-                  true, Kr, View::rowmajor(m), s));
-      CK(heev_top<T>(Kr, m, kmax, kmax, 0.0, -1.0, lamr, Ur, sc.k, wr, sc.status, num_sms(), s,
-                     1, o.concurrent, false));
-      CK(tgemm<T>(pr, true, false, kmax, n, m, Ur, View::transposed(kmax), true, M,
-                  View::rowmajor(n), false, W, View::rowmajor(n), s));
-      CK(row_norms2<T>(W, kmax, n, n, 0, w_dev, s));
-      CK(cudaMemcpyAsync(w.data(), w_dev, sizeof(double) * kmax, cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      if (!all_finite(w)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
-      U1 = Ur;
-    }
-    const int jr = resolved_prefix(w.data(), kmax, res);
-    double d = 0.0;
-    int rc = refine_rows<T>(ar, pr, M, m, n, kmax, jr, U1, W, w, max_bond, tol, floor_rel, o, sc,
-                            s, &k, &d);
-    if (rc != CBC_OK) return rc;
-    if (disc) disc[0] = d;
-    T* L = W;  // rows orientation: the first k rows
+  if (restarted) {  // one instance, rows orientation now: the first k rows of W
+    T* L = W;
     CK(normalize_inplace<T>(L, (int64_t)k * n, sc.log_fwd, sc.status, sc.scratch, s, 1));
     if (keep) ar.release(mk);
     *Lout = L;
@@ -401,8 +425,13 @@ int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars
   const size_t mk = ar.mark();
   T* G = ar.get<T>((size_t)nb * m * m);
   void* bar = ar.get<GridBarrier>(nb);
-  CKA(G); CKA(bar);
+  double* rn = ar.get<double>((size_t)nb * m);
+  CKA(G); CKA(bar); CKA(rn);
   const int64_t sbs = (int64_t)m * n;
+  // rows of S carry the graded singular values of the forward compression; scaling them
+  // to unit norm keeps the row space (hence Q) and keeps the Gram well conditioned
+  CK(row_norms2<T>(S, m, n, n, sbs, rn, s, nb));
+  CK(scale_rows<T>(S, m, n, sbs, rn, s, nb));
   for (int rep = 0; rep < 2; ++rep) {
     CK(tgemm<T>(pr, false, true, m, m, n, S, View::rowmajor(n, sbs), false, S,
                 View::transposed(n, sbs), true, G, View::rowmajor(m, (int64_t)m * m), s));
@@ -1011,6 +1040,30 @@ int resolved_prefix(const double* w, int kmax, double res) {
   int j = 0;
   while (j < kmax && w[j] > res * w[0]) ++j;
   return j;
+}
+
+int refine_start(const double* w, int kmax, int g, int k, double w_next, double total,
+                 double tol, double nu, double target, double res) {
+  if (k < g) {
+    // a direction at the cut is off by an angle ~ nu w_0 / (w_{k-1} - w_k); it mixes the
+    // first dropped direction (weight w_k) into the kept ones, which moves the state by
+    // about that angle times sqrt(w_k / total).  (A cut against zero-weight directions
+    // moves nothing.)
+    const double wk = (k < kmax) ? std::max(w[k], 0.0) : std::max(w_next, 0.0);
+    const double gap = w[k - 1] - wk;
+    const double est = (gap > 0.0) ? nu * w[0] / gap * std::sqrt(wk / total) : HUGE_VAL;
+    if (!(est > target)) return -1;
+    // the second level starts two orders of magnitude above the cut: its Gram's error
+    // then scales with the weights near the cut instead of w_0
+    int j = 0;
+    while (j < k && w[j] > 100.0 * w[k - 1]) ++j;
+    return (j >= 1) ? j : -1;
+  }
+  if (tol > 0.0) {  // nothing dropped, but the tolerance may cut among unresolved directions
+    const int j0 = resolved_prefix(w, kmax, res);
+    return (j0 >= 1 && j0 < g) ? j0 : -1;
+  }
+  return -1;
 }
 
 int run_cbc_group(const std::vector<const Net*>& sts, const std::vector<const Net*>& ops,

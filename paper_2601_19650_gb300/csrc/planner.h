@@ -57,6 +57,13 @@ int pick_rank(const double* w, int kmax, double beyond, int64_t max_bond, double
               double floor_rel);
 // number of leading candidates with w_j > res * w_0 (directions the Gram resolves)
 int resolved_prefix(const double* w, int kmax, double res);
+// Whether the first-level directions (from a Gram with relative error nu) decide the cut
+// at k accurately enough (state error below target), and if not, the first direction of
+// the second level (the residual's Gram recomputes directions from there on); -1: no
+// second level.  g = min(m, n); w_next estimates the weight of the first direction after
+// the kmax candidates; total is the cut's whole weight.
+int refine_start(const double* w, int kmax, int g, int k, double w_next, double total,
+                 double tol, double nu, double target, double res);
 // Directions whose weight is below kResolved * w_0 are not trusted as singular
 // directions: the Gram's own rounding (FP64: ~m eps w_0; mixed: ~1e-12 w_0 from the
 // operand slices and the double-float reduction) is too close.
