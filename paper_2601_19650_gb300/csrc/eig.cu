@@ -25,6 +25,7 @@
 #include <type_traits>
 #include <cstdlib>
 
+#include "df.cuh"
 #include "kernels.cuh"
 #include "planner.h"
 
@@ -260,57 +261,6 @@ __device__ __forceinline__ bool ld_pub(const zdbl* p, zdbl* v) {
   return __double_as_longlong(x) != kSentinel && __double_as_longlong(y) != kSentinel;
 }
 
-// ---- double-float arithmetic (value = h + l, two FP32 numbers, ~2^-46 relative) -----
-// On this part FP32 issues ~64x faster than FP64, so the mixed path keeps the rows of
-// the tridiagonal reduction as double-float pairs and runs its two O(m^2)-per-column
-// loops (p = A v and the rank-2 update) in FP32 with error-free transformations
-// (TwoProduct by fma, TwoSum; Dekker and Knuth).  The rounded intrinsics keep the
-// compiler from contracting them.
-struct df1 {
-  float h, l;
-};
-struct dfz {
-  df1 re, im;
-};
-template <typename T>
-struct dfof;
-template <>
-struct dfof<double> {
-  using type = df1;
-};
-template <>
-struct dfof<zdbl> {
-  using type = dfz;
-};
-__device__ __forceinline__ df1 df_make(double x) {
-  const float h = __double2float_rn(x);
-  return {h, __double2float_rn(x - (double)h)};
-}
-__device__ __forceinline__ df1 df_neg(df1 a) { return {-a.h, -a.l}; }
-// c + a b
-__device__ __forceinline__ df1 df_fma(df1 a, df1 b, df1 c) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  const float s = __fadd_rn(c.h, p);
-  const float bb = __fsub_rn(s, c.h);
-  float t = __fadd_rn(__fsub_rn(c.h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  t = __fadd_rn(t, __fadd_rn(c.l, e));
-  const float h = __fadd_rn(s, t);
-  return {h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-__device__ __forceinline__ df1 to_df(double x) { return df_make(x); }
-__device__ __forceinline__ dfz to_df(zdbl x) { return {df_make(x.re), df_make(x.im)}; }
-__device__ __forceinline__ double from_df(df1 a) { return (double)a.h + (double)a.l; }
-__device__ __forceinline__ zdbl from_df(dfz a) { return {from_df(a.re), from_df(a.im)}; }
-__device__ __forceinline__ df1 dff(df1 a, df1 b, df1 c) { return df_fma(a, b, c); }
-__device__ __forceinline__ dfz dff(dfz a, dfz b, dfz c) {  // c + a b, complex
-  return {df_fma(df_neg(a.im), b.im, df_fma(a.re, b.re, c.re)),
-          df_fma(a.im, b.re, df_fma(a.re, b.im, c.im))};
-}
-__device__ __forceinline__ df1 dfconj(df1 a) { return a; }
-__device__ __forceinline__ dfz dfconj(dfz a) { return {a.re, df_neg(a.im)}; }
 
 // dst[lo, hi) <- src[lo, hi) as the entries get published (and their double-float forms
 // into ddst when given).  False (for the whole CTA) when a wait ran out or another CTA
@@ -1236,7 +1186,13 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
     cluster = cluster_ctas(ksm, P, TPB, shm_for(P)) == P;
   }
   if (!cluster && Pw <= 0) P = std::max(1, std::min(num_sms, m / 4));
-  const bool in_smem = cluster || shm_for(P) <= shm_cap;
+  // batches (and concurrent instances) use the cluster reduction with the rows' lower
+  // triangles in shared memory and the exchanges through distributed shared memory
+  // (tridiag_cluster.cu); CBC_TRIDIAG_CTAS selects the polling kernels above instead
+  int Pc = 0;
+  if ((nb > 1 || prefer_cluster) && Pw <= 0 && m >= 2) Pc = tridiag_cluster_size<T>(m, df);
+  if (Pc > 0) cluster = false;
+  const bool in_smem = Pc == 0 && (cluster || shm_for(P) <= shm_cap);
   {
     // barrier, tau and e[0] start at zero; with the rows in shared memory the exchange
     // buffers start as all-ones bit patterns (the "not yet written" mark)
@@ -1263,8 +1219,10 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
     if (err != cudaSuccess) return err;
   }
   {
-  KTimer tt(CBC_K_TRIDIAG, s, cluster ? 1 : nb, fl_tri);
-  if (cluster) {
+  KTimer tt(CBC_K_TRIDIAG, s, (cluster || Pc > 0) ? 1 : nb, fl_tri);
+  if (Pc > 0) {
+    err = tridiag_cluster<T>(A, m, d, e, tau, V, (int64_t)m * m, wb, nb, Pc, df, s);
+  } else if (cluster) {
     Tri2Args<T> ta{A, m, d, e, tau, V, Pg, Dg, status, P, (int64_t)m * m, wb};
     void* args[] = {&ta};
     err = launch_cluster(ksm, P, nb * P, TPB, shm_for(P), args, s);

@@ -85,6 +85,17 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
                      cudaStream_t s, int nb = 1, bool prefer_cluster = false,
                      bool df = false);
 
+// Householder tridiagonalisation by one thread-block cluster per matrix (rows in shared
+// memory, exchanges through distributed shared memory; tridiag_cluster.cu).  Outputs as
+// the eigensolver's first stage: d, e, tau, V (row j = [tau_j, 1, v_j...] from column j),
+// per matrix wb bytes apart; A: nb matrices a_bs elements apart.  df: double-float rows.
+// tridiag_cluster_size returns the cluster size that fits (4, 8 or 16), 0 if none.
+template <typename T>
+int tridiag_cluster_size(int m, bool df);
+template <typename T>
+cudaError_t tridiag_cluster(const T* A, int m, double* d, double* e, T* tau, T* V, int64_t a_bs,
+                            size_t wb, int nb, int P, bool df, cudaStream_t s);
+
 // ---- Cholesky QR (FP64) ------------------------------------------------------------
 // Q = C^{-1} S with G = S S^H = C C^H, S: m x n (m <= n), row-major, in place on S.
 // nb problems: G, C m*m and S m*n elements apart; `bar` holds nb GridBarriers.

@@ -173,55 +173,74 @@ bool all_finite(const std::vector<double>& v) {
   return true;
 }
 
-// Second level for one instance, rows orientation: U1 (m x kmax, column j = direction j)
-// and W1 = U1^H M (kmax x n, the first kmax rows of the buffer that becomes L) from the
-// first level, j0 of them resolved.  Recomputes the directions beyond j0 from the Gram
-// of R = M - U1[:, :j0] W1[:j0] (orthogonalised against the resolved ones), writes their
-// W rows into W1 from row j0 on, and decides the rank on the combined weights.
+// Second level for one instance.  First level (rows orientation, m <= n): U1 (m x kmax,
+// column j = direction j) and W1 = U1^H M (kmax x n).  Columns orientation (m > n): V1
+// (n x kmax, the right directions, passed as U1) and W1 = M V1 (m x kmax).  jlo leading
+// directions are kept as they are; k2 new candidates are recomputed from the Gram of the
+// residual R = M - (the part of M along the kept ones), on the short side, orthogonalised
+// against the kept ones.  Rows: their W rows replace W1's rows jlo .. jlo+k2-1.  Columns:
+// their vectors replace V1's columns jlo .. jlo+k2-1 (the factor is then
+// diag(sqrt(w)) V^H).  The rank is decided again on the combined weights (w is updated;
+// w_dev receives them in the columns orientation).
 template <typename T>
-int refine_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int kmax, int j0,
-                const T* U1, T* W1, std::vector<double>& w, int64_t max_bond, double tol,
-                double floor_rel, const Options& o, const Scalars& sc, cudaStream_t s,
-                int* kout, double* disc) {
-  const int k2 = kmax - j0;
+int refine_level2(Arena& ar, const Prec& pr, const T* M, int m, int n, int kmax, int jlo, int k2,
+                  bool rows, T* U1, T* W1, std::vector<double>& w, double* w_dev, int64_t max_bond,
+                  double tol, double floor_rel, const Options& o, const Scalars& sc,
+                  cudaStream_t s, int* kout, double* disc) {
   const int64_t mn = (int64_t)m * n;
+  const int g = rows ? m : n;  // the short side: the residual's Gram is g x g
   T* P = ar.get<T>((size_t)mn);
   T* R = ar.get<T>((size_t)mn);
-  T* K2 = ar.get<T>((size_t)m * m);
-  double* lam2 = ar.get<double>(m);
-  T* U2 = ar.get<T>((size_t)m * k2);
-  T* C = ar.get<T>((size_t)std::max(1, j0) * k2);
-  T* P2 = ar.get<T>((size_t)m * k2);
-  char* work = ar.get<char>(eig_workspace_bytes(m, k2, ops<T>::cplx));
+  T* K2 = ar.get<T>((size_t)g * g);
+  double* lam2 = ar.get<double>(g);
+  T* U2 = ar.get<T>((size_t)g * k2);
+  T* C = ar.get<T>((size_t)std::max(1, jlo) * k2);
+  T* P2 = ar.get<T>((size_t)g * k2);
+  T* W2c = rows ? nullptr : ar.get<T>((size_t)m * k2);
+  char* work = ar.get<char>(eig_workspace_bytes(g, k2, ops<T>::cplx));
   double* dv = ar.get<double>(k2 + 4);
   CKA(P); CKA(R); CKA(K2); CKA(lam2); CKA(U2); CKA(C); CKA(P2); CKA(work); CKA(dv);
+  if (!rows) CKA(W2c);
   CK(cudaMemsetAsync(dv, 0, sizeof(double) * (k2 + 4), s));
-  // R = M - U1[:, :j0] W1[:j0]
-  if (j0 > 0) {
-    CK(tgemm<T>(pr, true, false, m, n, j0, U1, View::rowmajor(kmax), false, W1,
+  // R = M - (the part along the kept directions)
+  if (rows)   // U1r W1r
+    CK(tgemm<T>(pr, true, false, m, n, jlo, U1, View::rowmajor(kmax), false, W1,
                 View::rowmajor(n), false, P, View::rowmajor(n), s));
-    CK(diff_sumsq<T>(M, mn, P, R, mn, dv + k2, s));
-  } else {
-    CK(cudaMemcpyAsync(R, M, sizeof(T) * mn, cudaMemcpyDeviceToDevice, s));
-  }
-  CK(tgemm<T>(pr, true, true, m, m, n, R, View::rowmajor(n), false, R, View::transposed(n), true,
-              K2, View::rowmajor(m), s));
-  CK(heev_top<T>(K2, m, k2, k2, 0.0, -1.0, lam2, U2, sc.k, work, sc.status, num_sms(), s, 1,
+  else        // W1r V1r^H
+    CK(tgemm<T>(pr, true, false, m, n, jlo, W1, View::rowmajor(kmax), false, U1,
+                View::transposed(kmax), true, P, View::rowmajor(n), s));
+  CK(diff_sumsq<T>(M, mn, P, R, mn, dv + k2, s));
+  if (rows)   // R R^H
+    CK(tgemm<T>(pr, true, true, m, m, n, R, View::rowmajor(n), false, R, View::transposed(n),
+                true, K2, View::rowmajor(m), s));
+  else        // R^H R
+    CK(tgemm<T>(pr, true, true, n, n, m, R, View::transposed(n), true, R, View::rowmajor(n),
+                false, K2, View::rowmajor(n), s));
+  CK(heev_top<T>(K2, g, k2, k2, 0.0, -1.0, lam2, U2, sc.k, work, sc.status, num_sms(), s, 1,
                  o.concurrent, false));
-  if (j0 > 0) {  // U2 <- U2 - U1r (U1r^H U2)
-    CK(tgemm<T>(pr, true, false, j0, k2, m, U1, View::transposed(kmax), true, U2,
-                View::rowmajor(k2), false, C, View::rowmajor(k2), s));
-    CK(tgemm<T>(pr, true, false, m, k2, j0, U1, View::rowmajor(kmax), false, C,
-                View::rowmajor(k2), false, P2, View::rowmajor(k2), s));
-    CK(diff_sumsq<T>(U2, (int64_t)m * k2, P2, U2, (int64_t)m * k2, dv + k2 + 1, s));
+  // U2 <- U2 - U1r (U1r^H U2)
+  CK(tgemm<T>(pr, true, false, jlo, k2, g, U1, View::transposed(kmax), true, U2,
+              View::rowmajor(k2), false, C, View::rowmajor(k2), s));
+  CK(tgemm<T>(pr, true, false, g, k2, jlo, U1, View::rowmajor(kmax), false, C,
+              View::rowmajor(k2), false, P2, View::rowmajor(k2), s));
+  CK(diff_sumsq<T>(U2, (int64_t)g * k2, P2, U2, (int64_t)g * k2, dv + k2 + 1, s));
+  if (rows) {
+    T* W2 = W1 + (int64_t)jlo * n;  // rows jlo .. jlo+k2-1 of the new factor
+    CK(tgemm<T>(pr, true, false, k2, n, m, U2, View::transposed(k2), true, M, View::rowmajor(n),
+                false, W2, View::rowmajor(n), s));
+    CK(row_norms2<T>(W2, k2, n, n, 0, dv, s));
+    CK(tgemm<T>(pr, true, false, m, n, k2, U2, View::rowmajor(k2), false, W2, View::rowmajor(n),
+                false, P, View::rowmajor(n), s));
+  } else {
+    CK(tgemm<T>(pr, true, false, m, k2, n, M, View::rowmajor(n), false, U2, View::rowmajor(k2),
+                false, W2c, View::rowmajor(k2), s));
+    CK(col_norms2<T>(W2c, m, k2, k2, 0, dv, s));
+    CK(tgemm<T>(pr, true, false, m, n, k2, W2c, View::rowmajor(k2), false, U2,
+                View::transposed(k2), true, P, View::rowmajor(n), s));
+    // the new right directions become V1's columns jlo .. jlo+k2-1
+    CK(copy_batched<T>(U2, k2, U1 + jlo, kmax, k2, s, n));
   }
-  T* W2 = W1 + (int64_t)j0 * n;  // rows j0 .. kmax-1 of the new factor
-  CK(tgemm<T>(pr, true, false, k2, n, m, U2, View::transposed(k2), true, M, View::rowmajor(n),
-              false, W2, View::rowmajor(n), s));
-  CK(row_norms2<T>(W2, k2, n, n, 0, dv, s));
-  // weight outside all kmax directions: ||R - U2 W2||^2
-  CK(tgemm<T>(pr, true, false, m, n, k2, U2, View::rowmajor(k2), false, W2, View::rowmajor(n),
-              false, P, View::rowmajor(n), s));
+  // weight outside all the directions: ||R - (the part along the new ones)||^2
   CK(diff_sumsq<T>(R, mn, P, nullptr, mn, dv + k2 + 2, s));
   std::vector<double> h(k2 + 3);
   int hs = 0;
@@ -230,12 +249,15 @@ int refine_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int kmax, i
   CK(cudaStreamSynchronize(s));
   if (hs != 0) return status_to_rc(hs);
   if (!all_finite(h)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
-  for (int j = 0; j < k2; ++j) w[j0 + j] = h[j];
+  const int kn = jlo + k2;
+  for (int j = 0; j < k2; ++j) w[jlo + j] = h[j];
   const double beyond = h[k2 + 2];
-  const int k = pick_rank(w.data(), kmax, beyond, max_bond, tol, floor_rel);
+  const int k = pick_rank(w.data(), kn, beyond, max_bond, tol, floor_rel);
   double total = beyond;
-  for (int j = 0; j < kmax; ++j) total += std::max(w[j], 0.0);
-  *disc = discarded_rel(w.data(), kmax, k, beyond, total);
+  for (int j = 0; j < kn; ++j) total += std::max(w[j], 0.0);
+  *disc = discarded_rel(w.data(), kn, k, beyond, total);
+  if (!rows && w_dev)
+    CK(cudaMemcpyAsync(w_dev, w.data(), sizeof(double) * kn, cudaMemcpyHostToDevice, s));
   *kout = k;
   return CBC_OK;
 }
@@ -338,46 +360,18 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
     if (jlo[b] >= 0) any_refine = true;
     if (disc) disc[b] = discarded_rel(wb[b].data(), kmax, kb[b], beyond, total);
   }
-  bool restarted = false;  // cols orientation redone in rows orientation (one instance)
   if (any_refine) {
     if (!rows && nb > 1) return kGroupSplit;
     Prec p1 = pr;
     p1.nb = 1;
-    Scalars s1 = sc;
     for (int b = 0; b < nb; ++b) {
       if (jlo[b] < 0) continue;
-      const T* Mb = M + (size_t)b * mbs;
-      T* U1 = U + (size_t)b * ubs;
-      T* Wb = W + (size_t)b * wbs;
-      std::vector<double>& w = wb[b];
-      if (!rows) {  // restart in the rows orientation: K = M M^H (m x m), W = U^H M
-        T* Kr = ar.get<T>((size_t)m * m);
-        double* lamr = ar.get<double>(m);
-        T* Ur = ar.get<T>((size_t)m * kmax);
-        char* wr = ar.get<char>(eig_workspace_bytes(m, kmax, ops<T>::cplx));
-        Wb = kp.get<T>((size_t)kmax * n);
-        CKA(Kr); CKA(lamr); CKA(Ur); CKA(wr);
-        if (!Wb) return cuda_fail(kp.err, "workspace allocation L");
-        CK(tgemm<T>(p1, true, true, m, m, n, Mb, View::rowmajor(n), false, Mb, View::transposed(n),
-                    true, Kr, View::rowmajor(m), s));
-        CK(heev_top<T>(Kr, m, kmax, kmax, 0.0, -1.0, lamr, Ur, sc.k, wr, sc.status, num_sms(), s,
-                       1, o.concurrent, false));
-        CK(tgemm<T>(p1, true, false, kmax, n, m, Ur, View::transposed(kmax), true, Mb,
-                    View::rowmajor(n), false, Wb, View::rowmajor(n), s));
-        CK(row_norms2<T>(Wb, kmax, n, n, 0, w_dev, s));
-        CK(cudaMemcpyAsync(w.data(), w_dev, sizeof(double) * kmax, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        if (!all_finite(w)) return fail(CBC_ERR_NUMERICAL, "cbc_apply: NaN or Inf in a truncation");
-        int j = 0;
-        while (j < kmax && w[j] > 100.0 * w[std::max(0, kb[b] - 1)]) ++j;
-        jlo[b] = std::max(1, std::min(j, resolved_prefix(w.data(), kmax, res)));
-        U1 = Ur;
-        W = Wb;
-        restarted = true;
-      }
+      const int k2 = second_level_size(kmax, kb[b], jlo[b]);
       double d = 0.0;
-      int rc = refine_rows<T>(ar, p1, Mb, m, n, kmax, jlo[b], U1, Wb, w, max_bond, tol, floor_rel,
-                              o, s1, s, &kb[b], &d);
+      int rc = refine_level2<T>(ar, p1, M + (size_t)b * mbs, m, n, kmax, jlo[b], k2, rows,
+                                U + (size_t)b * ubs, W + (size_t)b * wbs, wb[b],
+                                w_dev + (size_t)b * kmax, max_bond, tol, floor_rel, o, sc, s,
+                                &kb[b], &d);
       if (rc != CBC_OK) return rc;
       if (disc) disc[b] = d;
     }
@@ -385,14 +379,6 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
   for (int b = 1; b < nb; ++b)
     if (kb[b] != kb[0]) return kGroupSplit;
   int k = kb[0];
-  if (restarted) {  // one instance, rows orientation now: the first k rows of W
-    T* L = W;
-    CK(normalize_inplace<T>(L, (int64_t)k * n, sc.log_fwd, sc.status, sc.scratch, s, 1));
-    if (keep) ar.release(mk);
-    *Lout = L;
-    *kout = k;
-    return CBC_OK;
-  }
   const int64_t lbs = (int64_t)k * n;
   T* L;
   if (rows) {
@@ -1061,9 +1047,14 @@ int refine_start(const double* w, int kmax, int g, int k, double w_next, double 
   }
   if (tol > 0.0) {  // nothing dropped, but the tolerance may cut among unresolved directions
     const int j0 = resolved_prefix(w, kmax, res);
-    return (j0 >= 1 && j0 < g) ? j0 : -1;
+    return (j0 >= 1 && j0 < g && g - j0 <= kMaxSecondLevel) ? j0 : -1;
   }
   return -1;
+}
+
+int second_level_size(int kmax, int k, int jlo) {
+  const int near = std::max(k - jlo, 1);
+  return std::min(kmax - jlo, near + std::max(16, near));
 }
 
 int run_cbc_group(const std::vector<const Net*>& sts, const std::vector<const Net*>& ops,

@@ -69,6 +69,13 @@ int refine_start(const double* w, int kmax, int g, int k, double w_next, double 
 // operand slices and the double-float reduction) is too close.
 constexpr double kResolvedFP64 = 1e-10;
 constexpr double kResolvedMixed = 1e-8;
+// A tolerance that keeps every candidate while some are unresolved is checked by a second
+// level only when at most this many are unresolved (the second level's eigensolver pays
+// for each one); larger blocks are kept whole.
+constexpr int kMaxSecondLevel = 256;
+// candidates of the second level for a first-level cut at k that starts at jlo: the
+// directions up to the cut and as many again (at least 16) beyond it, within kmax
+int second_level_size(int kmax, int k, int jlo);
 
 // A group (see run_cbc_group) that cannot run in lockstep: shapes differ, a tree, or the
 // instances chose different ranks at some cut.  The caller runs the members one by one.
