@@ -110,6 +110,7 @@ T host_one() {
 // copies, View::bs elements apart.
 struct Prec {
   bool mixed = false;
+  bool cholqr_f64 = false;  // CholeskyQR2's Gram in FP64 even on the mixed path
   int s_fwd = 5, s_bwd = 4;
   Arena* ar = nullptr;
   int* status = nullptr;
@@ -418,8 +419,12 @@ int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars
   // to unit norm keeps the row space (hence Q) and keeps the Gram well conditioned
   CK(row_norms2<T>(S, m, n, n, sbs, rn, s, nb));
   CK(scale_rows<T>(S, m, n, sbs, rn, s, nb));
+  // the Gram with the first sweep's (finer) slices: CholeskyQR squares the condition
+  // number, so it needs more of the product's bits than the contractions do
+  Prec pg = pr;
+  if (pr.cholqr_f64) pg.mixed = false;
   for (int rep = 0; rep < 2; ++rep) {
-    CK(tgemm<T>(pr, false, true, m, m, n, S, View::rowmajor(n, sbs), false, S,
+    CK(tgemm<T>(pg, true, true, m, m, n, S, View::rowmajor(n, sbs), false, S,
                 View::transposed(n, sbs), true, G, View::rowmajor(m, (int64_t)m * m), s));
     KTimer t(CBC_K_CHOLQR, s, 0,
              nb * (ops<T>::cplx ? 4.0 : 1.0) * ((double)m * m * m / 3.0 + (double)m * m * n));
@@ -463,6 +468,7 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
   Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + nb, d_dbl + 2 * nb};
   Prec pr;
   pr.mixed = (o.precision == CBC_PREC_MIXED);
+  pr.cholqr_f64 = o.cholqr_f64;
   pr.s_fwd = o.slices_fwd;
   pr.s_bwd = o.slices_bwd;
   pr.ar = &tmp;
@@ -779,6 +785,7 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
   Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + 1, d_dbl + 2};
   Prec pr;
   pr.mixed = (o.precision == CBC_PREC_MIXED);
+  pr.cholqr_f64 = o.cholqr_f64;
   pr.s_fwd = o.slices_fwd;
   pr.s_bwd = o.slices_bwd;
   pr.ar = &ar;
@@ -1057,6 +1064,21 @@ int second_level_size(int kmax, int k, int jlo) {
   return std::min(kmax - jlo, near + std::max(16, near));
 }
 
+// frees what a failed run left in an output network, so it can be filled again
+void release_outputs(Net* out) {
+  bool any = false;
+  for (void*& p : out->data)
+    if (p) {
+      cudaFreeAsync(p, out->stream);
+      p = nullptr;
+      any = true;
+    }
+  if (any) cudaStreamSynchronize(out->stream);
+  cudaGetLastError();
+  out->data.clear();
+  out->numel.clear();
+}
+
 int run_cbc_group(const std::vector<const Net*>& sts, const std::vector<const Net*>& ops,
                   int64_t max_bond, double tol, const Options& o, const std::vector<Net*>& outs) {
   if (sts.empty() || sts.size() != ops.size() || sts.size() != outs.size())
@@ -1072,8 +1094,12 @@ int run_cbc_group(const std::vector<const Net*>& sts, const std::vector<const Ne
   if (o.precision == CBC_PREC_MIXED && (o.slices_fwd < 2 || o.slices_fwd > 5 || o.slices_bwd < 2 ||
                                         o.slices_bwd > 5))
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply: slice counts must be in [2, 5]");
-  if (st.cplx) return run_tt_group<zdbl>(sts, ops, max_bond, tol, o, outs);
-  return run_tt_group<double>(sts, ops, max_bond, tol, o, outs);
+  int rc = st.cplx ? run_tt_group<zdbl>(sts, ops, max_bond, tol, o, outs)
+                   : run_tt_group<double>(sts, ops, max_bond, tol, o, outs);
+  // a Cholesky breakdown on the mixed path: the members run one by one, each with the
+  // FP64 fallback of run_cbc
+  if (rc == CBC_ERR_NOT_POSITIVE_DEFINITE && o.precision == CBC_PREC_MIXED) return kGroupSplit;
+  return rc;
 }
 
 int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
@@ -1083,12 +1109,24 @@ int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Op
   if (o.precision == CBC_PREC_MIXED && (o.slices_fwd < 2 || o.slices_fwd > 5 || o.slices_bwd < 2 ||
                                         o.slices_bwd > 5))
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply: slice counts must be in [2, 5]");
-  if (is_chain(st)) {
-    if (st.cplx) return run_tt<zdbl>(st, op, max_bond, tol, o, out);
-    return run_tt<double>(st, op, max_bond, tol, o, out);
+  auto once = [&](const Options& oo) {
+    if (is_chain(st)) {
+      if (st.cplx) return run_tt<zdbl>(st, op, max_bond, tol, oo, out);
+      return run_tt<double>(st, op, max_bond, tol, oo, out);
+    }
+    if (st.cplx) return run_tree<zdbl>(st, op, max_bond, tol, oo, out);
+    return run_tree<double>(st, op, max_bond, tol, oo, out);
+  };
+  int rc = once(o);
+  if (rc == CBC_ERR_NOT_POSITIVE_DEFINITE && o.precision == CBC_PREC_MIXED && !o.cholqr_f64) {
+    // the slices' Gram of some backward factor S was too coarse for its condition
+    // number: run the application again with FP64 Gram matrices in CholeskyQR2
+    release_outputs(out);
+    Options o2 = o;
+    o2.cholqr_f64 = true;
+    rc = once(o2);
   }
-  if (st.cplx) return run_tree<zdbl>(st, op, max_bond, tol, o, out);
-  return run_tree<double>(st, op, max_bond, tol, o, out);
+  return rc;
 }
 
 }  // namespace cbc

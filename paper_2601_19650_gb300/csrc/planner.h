@@ -43,6 +43,10 @@ struct Options {
   // kernels whose CTAs wait on each other then use cluster launches, which run
   // concurrently with other streams' work, instead of cooperative ones, which do not
   bool concurrent = false;
+  // mixed path: the Gram matrices of CholeskyQR2 in FP64 instead of on the tensor cores
+  // (set by the planner when the tensor-core Gram met a Cholesky breakdown: a backward
+  // factor S too ill conditioned for the slices' precision)
+  bool cholqr_f64 = false;
 };
 
 int run_cbc(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
@@ -72,7 +76,7 @@ constexpr double kResolvedMixed = 1e-8;
 // A tolerance that keeps every candidate while some are unresolved is checked by a second
 // level only when at most this many are unresolved (the second level's eigensolver pays
 // for each one); larger blocks are kept whole.
-constexpr int kMaxSecondLevel = 256;
+constexpr int kMaxSecondLevel = 64;
 // candidates of the second level for a first-level cut at k that starts at jlo: the
 // directions up to the cut and as many again (at least 16) beyond it, within kmax
 int second_level_size(int kmax, int k, int jlo);

@@ -250,7 +250,10 @@ def test_group_wide_batch(precision, bar):
     probs = [make_problem(2, seed=60 + j, L=16, chi=64, D=4, max_bond=128) for j in range(20)]
     res, stats = _apply_batched(probs, precision)
     _check_against_oracle(probs, res, bar)
-    assert stats["eig"]["groups"] == 16 - 1, stats["eig"]
+    # one eigensolver launch group per cut for the whole group; a cut whose truncation one
+    # instance refines (second level, on that instance alone) adds one group of its own
+    assert 16 - 1 <= stats["eig"]["groups"] <= 16 - 1 + 2 * len(probs), stats["eig"]
+    assert stats["tridiag"]["launches"] >= 16 - 1
 
 
 def test_group_mixed_shapes_and_real():
