@@ -60,4 +60,28 @@ __device__ __forceinline__ dfz dff(dfz a, dfz b, dfz c) {  // c + a b, complex
 __device__ __forceinline__ df1 dfconj(df1 a) { return a; }
 __device__ __forceinline__ dfz dfconj(dfz a) { return {a.re, df_neg(a.im)}; }
 
+// a + b (TwoSum of the high parts, the low parts and the rounding error added, then
+// renormalised)
+__device__ __forceinline__ df1 df_add(df1 a, df1 b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float t = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  t = __fadd_rn(t, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfz df_add(dfz a, dfz b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfz df_neg(dfz a) { return {df_neg(a.re), df_neg(a.im)}; }
+__device__ __forceinline__ df1 df_shfl_xor(df1 a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+__device__ __forceinline__ dfz df_shfl_xor(dfz a, int o) {
+  return {df_shfl_xor(a.re, o), df_shfl_xor(a.im, o)};
+}
+// |a|^2 as a real double-float
+__device__ __forceinline__ df1 df_abs2(df1 a) { return df_fma(a, a, df1{0.f, 0.f}); }
+__device__ __forceinline__ df1 df_abs2(dfz a) {
+  return df_fma(a.im, a.im, df_fma(a.re, a.re, df1{0.f, 0.f}));
+}
+
 }  // namespace cbc

@@ -263,6 +263,10 @@ int refine_level2(Arena& ar, const Prec& pr, const T* M, int m, int n, int kmax,
   return CBC_OK;
 }
 
+template <typename T>
+int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars& sc,
+                    cudaStream_t s);
+
 // Compression of the row leg of M (m x n, row-major): writes the k x n factor whose
 // Gram reproduces the rank-k truncation of M^H M, normalised, and returns k (and the
 // relative discarded weight per instance in disc, if given).  L (k x n per instance)
@@ -390,10 +394,29 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
       CK(copy_batched<T>(W, wbs, L, lbs, lbs, s, nb));
       kp.drop(W);
     }
-  } else {     // L = diag(sqrt(w_k)) V_k^H
+  } else {
     L = kp.get<T>((size_t)nb * lbs);
     if (!L) return cuda_fail(kp.err, "workspace allocation L");
-    CK(scaled_adjoint_w<T>(U, kmax, w_dev, kmax, k, n, L, lbs, s, nb));
+    bool exact = false;  // some kept direction is below the Gram's resolution
+    for (int b = 0; b < nb; ++b)
+      if (resolved_prefix(wb[b].data(), k, res) < k) exact = true;
+    if (!exact) {  // L = diag(sqrt(w_k)) V_k^H
+      CK(scaled_adjoint_w<T>(U, kmax, w_dev, kmax, k, n, L, lbs, s, nb));
+    } else {
+      // diag(sqrt(w)) V^H keeps only the diagonal of V^H G V, whose off-diagonal rounding
+      // (~eps w_0) is large next to the smallest kept weights; the exact factor is
+      // L = Q' M with Q' an orthonormal basis of the row space of (M V_k)^H: then
+      // L^H L = M^H P M, P the projector onto the span of M V_k
+      const int64_t whs = (int64_t)k * m;
+      T* Wh = ar.get<T>((size_t)nb * whs);
+      CKA(Wh);
+      CK(tgemm<T>(pr, true, false, k, m, n, U, View::transposed(kmax, ubs), true, M,
+                  View::transposed(n, mbs), true, Wh, View::rowmajor(m, whs), s));
+      int rc = lq_rows_inplace<T>(ar, pr, Wh, k, m, sc, s);
+      if (rc != CBC_OK) return rc;
+      CK(tgemm<T>(pr, true, false, k, n, m, Wh, View::rowmajor(m, whs), false, M,
+                  View::rowmajor(n, mbs), false, L, View::rowmajor(n, lbs), s));
+    }
   }
   CK(normalize_inplace<T>(L, lbs, sc.log_fwd, sc.status, sc.scratch, s, nb));
   if (keep) ar.release(mk);

@@ -18,9 +18,11 @@
 //      shared memory reads), forms w = p - (conj(tau)/2)(v^H p) v, and applies the rank-2
 //      update A -= v w^H + w v^H to its own rows;
 //   4. cluster barrier (column j+1 is final everywhere).
-// Two hardware cluster barriers per column, no polling of global memory.  DF: the rows,
-// v and w as double-float pairs and the O(m^2) loops in FP32 arithmetic with error-free
-// transformations (the mixed path); otherwise FP64 throughout.
+// Two hardware cluster barriers per column, no polling of global memory.  DF (the mixed
+// path): the rows and every per-element quantity as double-float pairs, so all O(m) and
+// O(m^2) work per column and every reduction runs in FP32 arithmetic with error-free
+// transformations; FP64 only for the handful of Householder scalars, computed by one
+// thread.  Otherwise FP64 throughout.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -58,24 +60,57 @@ __device__ __forceinline__ P* shift_bytes(P* p, size_t bytes) {
   return reinterpret_cast<P*>(reinterpret_cast<char*>(p) + bytes);
 }
 
-// element type of the stored rows and the arithmetic on them
+// Element type of the stored rows and of every per-element quantity (v, w, p and its
+// shares), and the arithmetic on them: FP64 (T itself), or double-float pairs on the
+// mixed path, where every per-element operation and every reduction runs on the FP32
+// pipes and FP64 is left to the few scalars of each Householder step.
 template <typename T, bool DF>
 struct RowArith;
 template <typename T>
 struct RowArith<T, false> {
+  using O = ops<T>;
   using E = T;
+  using R = double;  // real quantities (norms)
   __device__ static __forceinline__ E cvt(T x) { return x; }
   __device__ static __forceinline__ T back(E x) { return x; }
-  __device__ static __forceinline__ E mac(E a, E b, E c) { return ops<T>::fma(a, b, c); }
-  __device__ static __forceinline__ E cj(E a) { return ops<T>::conj(a); }
+  __device__ static __forceinline__ E mac(E a, E b, E c) { return O::fma(a, b, c); }
+  __device__ static __forceinline__ E cj(E a) { return O::conj(a); }
+  __device__ static __forceinline__ E zero() { return O::zero(); }
+  __device__ static __forceinline__ E one() { return O::one(); }
+  __device__ static __forceinline__ E add(E a, E b) { return a + b; }
+  __device__ static __forceinline__ E mul(E a, E b) { return a * b; }
+  __device__ static __forceinline__ E neg(E a) { return O::scale(-1.0, a); }
+  __device__ static __forceinline__ E shfl(E a, int o) { return shfl_xor(a, o); }
+  __device__ static __forceinline__ R rzero() { return 0.0; }
+  __device__ static __forceinline__ R radd(R a, R b) { return a + b; }
+  __device__ static __forceinline__ R abs2(E a) { return O::abs2(a); }
+  __device__ static __forceinline__ double rback(R a) { return a; }
+  __device__ static __forceinline__ R rshfl(R a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
 };
 template <typename T>
 struct RowArith<T, true> {
+  using O = ops<T>;
   using E = typename dfof<T>::type;
+  using R = df1;
   __device__ static __forceinline__ E cvt(T x) { return to_df(x); }
   __device__ static __forceinline__ T back(E x) { return from_df(x); }
   __device__ static __forceinline__ E mac(E a, E b, E c) { return dff(a, b, c); }
   __device__ static __forceinline__ E cj(E a) { return dfconj(a); }
+  __device__ static __forceinline__ E zero() { return E{}; }
+  __device__ static __forceinline__ E one() {
+    E x{};
+    if constexpr (O::cplx) x.re.h = 1.f; else x.h = 1.f;
+    return x;
+  }
+  __device__ static __forceinline__ E add(E a, E b) { return df_add(a, b); }
+  __device__ static __forceinline__ E mul(E a, E b) { return dff(a, b, E{}); }
+  __device__ static __forceinline__ E neg(E a) { return df_neg(a); }
+  __device__ static __forceinline__ E shfl(E a, int o) { return df_shfl_xor(a, o); }
+  __device__ static __forceinline__ R rzero() { return R{}; }
+  __device__ static __forceinline__ R radd(R a, R b) { return df_add(a, b); }
+  __device__ static __forceinline__ R abs2(E a) { return df_abs2(a); }
+  __device__ static __forceinline__ double rback(R a) { return from_df(a); }
+  __device__ static __forceinline__ R rshfl(R a, int o) { return df_shfl_xor(a, o); }
 };
 
 // offset of own row t (r = q + P t) in rank q's packed triangle: sum_{u<t} (q + P u + 1)
@@ -83,24 +118,32 @@ __device__ __forceinline__ int row_off(int q, int P, int t) {
   return t * (q + 1) + P * (t * (t - 1) / 2);
 }
 
-// deterministic block sums: each thread's strided sum, a butterfly per warp, the warps in
-// order by warp 0 (the same sequence of operations in every CTA of the cluster)
-__device__ __forceinline__ double2 block_sum2_det(double x, double y, double* red) {
-  x = warp_sum(x);
-  y = warp_sum(y);
+// Deterministic block sums: a butterfly per warp (lane 0's result is used), then the
+// warps' results added in order by every thread: the same sequence of operations, hence
+// the same value, in every CTA of the cluster.
+template <typename AR>
+__device__ __forceinline__ typename AR::E block_sum_e(typename AR::E x, typename AR::E* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = AR::add(x, AR::shfl(x, o));
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[2 * w] = x;
-    red[2 * w + 1] = y;
-  }
+  if (lane == 0) red[w] = x;
   __syncthreads();
-  double sx = 0.0, sy = 0.0;
-  for (int q = 0; q < TCL_WARPS; ++q) {
-    sx += red[2 * q];
-    sy += red[2 * q + 1];
-  }
+  typename AR::E s = red[0];
+  for (int q = 1; q < TCL_WARPS; ++q) s = AR::add(s, red[q]);
   __syncthreads();
-  return make_double2(sx, sy);
+  return s;
+}
+template <typename AR>
+__device__ __forceinline__ typename AR::R block_sum_r(typename AR::R x, typename AR::R* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = AR::radd(x, AR::rshfl(x, o));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = x;
+  __syncthreads();
+  typename AR::R s = red[0];
+  for (int q = 1; q < TCL_WARPS; ++q) s = AR::radd(s, red[q]);
+  __syncthreads();
+  return s;
 }
 
 template <typename T, bool DF>
@@ -108,6 +151,7 @@ __global__ void __launch_bounds__(TCL_THREADS) tridiag_cluster_kernel(TriClArgs<
   using O = ops<T>;
   using AR = RowArith<T, DF>;
   using E = typename AR::E;
+  using R = typename AR::R;
   cg::cluster_group cluster = cg::this_cluster();
   const int P = (int)cluster.num_blocks();
   const int cta = (int)cluster.block_rank();
@@ -122,16 +166,18 @@ __global__ void __launch_bounds__(TCL_THREADS) tridiag_cluster_kernel(TriClArgs<
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E* rows = reinterpret_cast<E*>(smem_raw);
-  T* xcol = reinterpret_cast<T*>(rows + a0.rows_cap);  // column j (FP64)
-  T* vfull = xcol + m;                                  // v (FP64)
-  T* pp = vfull + m;                                    // this CTA's share of A v
-  T* pfull = pp + m;                                    // p = tau A v
-  T* wfull = pfull + m;                                 // w
-  T* rp = wfull + m;                                    // row sums of own rows
-  T* wpart = rp + a0.nr_cap;                            // [warp][m] column sums
-  E* vE = reinterpret_cast<E*>(wpart + (size_t)TCL_WARPS * m);
-  E* wE = vE + m;
-  __shared__ double red[2 * TCL_WARPS];
+  E* xE = rows + a0.rows_cap;            // column j
+  E* vE = xE + m;                        // v
+  E* ppE = vE + m;                       // this CTA's share of A v (read by the others)
+  E* pE = ppE + m;                       // p = tau A v
+  E* wE = pE + m;                        // w
+  E* rpE = wE + m;                       // row sums of own rows
+  E* wpartE = rpE + a0.nr_cap;           // [warp][m] column sums
+  __shared__ E redE[TCL_WARPS];
+  __shared__ R redR[TCL_WARPS];
+  __shared__ T s_tau;
+  __shared__ E s_tauE, s_scaleE, s_coefE;
+  __shared__ int s_trivial;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nr = (m - cta + P - 1) / P;  // own rows r = cta + P t, t < nr
@@ -148,118 +194,122 @@ __global__ void __launch_bounds__(TCL_THREADS) tridiag_cluster_kernel(TriClArgs<
     // 1. column j below the diagonal, from its rows' owners
     for (int r = j + 1 + tid; r < m; r += TCL_THREADS) {
       const int q = r % P, t = r / P;
-      const E* rq = cluster.map_shared_rank(rows, q);
-      xcol[r] = AR::back(rq[row_off(q, P, t) + j]);
+      xE[r] = cluster.map_shared_rank(rows, q)[row_off(q, P, t) + j];
     }
     __syncthreads();
-    double xn2 = 0.0;
-    for (int c = j + 2 + tid; c < m; c += TCL_THREADS) xn2 += O::abs2(xcol[c]);
-    xn2 = block_sum2_det(xn2, 0.0, red).x;
-    const T alpha = xcol[j + 1];
-    const double ar = O::real(alpha), ai = O::imag(alpha);
-    T tau, scale;
-    double beta;
-    const bool trivial = (xn2 == 0.0 && ai == 0.0);
-    if (trivial) {
-      tau = O::zero();
-      beta = ar;
-      scale = O::zero();
-    } else {
-      const double n2 = ar * ar + ai * ai + xn2;
-      const double rn = rsqrt64(n2);  // 1 / ||x||
-      const double nrm = n2 * rn;
-      beta = (ar >= 0.0) ? -nrm : nrm;
-      const double ib = (ar >= 0.0) ? -rn : rn;  // 1 / beta
-      tau = O::make((beta - ar) * ib, -ai * ib);
-      const double zr = ar - beta, zi = ai;
-      const double iden = rcp64(zr * zr + zi * zi);
-      scale = O::make(zr * iden, -zi * iden);  // 1 / (alpha - beta)
-    }
-    T* vrow = V + (int64_t)j * m;
-    for (int c = j + 1 + tid; c < m; c += TCL_THREADS) {
-      const T v = (c == j + 1) ? O::one() : (trivial ? O::zero() : xcol[c] * scale);
-      vfull[c] = v;
-      vE[c] = AR::cvt(v);
-      if (cta == 0) vrow[c] = v;
-    }
-    if (cta == 0 && tid == 0) {
-      vrow[j] = tau;
-      tau_out[j] = tau;
-      e[j] = beta;
+    R part = AR::rzero();
+    for (int c = j + 2 + tid; c < m; c += TCL_THREADS) part = AR::radd(part, AR::abs2(xE[c]));
+    const R xn2e = block_sum_r<AR>(part, redR);
+    if (tid == 0) {  // the Householder scalars, FP64, one thread
+      const double xn2 = AR::rback(xn2e);
+      const T alpha = AR::back(xE[j + 1]);
+      const double ar = O::real(alpha), ai = O::imag(alpha);
+      T tau, scale;
+      double beta;
+      const bool trivial = (xn2 == 0.0 && ai == 0.0);
+      if (trivial) {
+        tau = O::zero();
+        beta = ar;
+        scale = O::zero();
+      } else {
+        const double n2 = ar * ar + ai * ai + xn2;
+        const double rn = rsqrt64(n2);  // 1 / ||x||
+        const double nrm = n2 * rn;
+        beta = (ar >= 0.0) ? -nrm : nrm;
+        const double ib = (ar >= 0.0) ? -rn : rn;  // 1 / beta
+        tau = O::make((beta - ar) * ib, -ai * ib);
+        const double zr = ar - beta, zi = ai;
+        const double iden = rcp64(zr * zr + zi * zi);
+        scale = O::make(zr * iden, -zi * iden);  // 1 / (alpha - beta)
+      }
+      s_tau = tau;
+      s_tauE = AR::cvt(tau);
+      s_scaleE = AR::cvt(scale);
+      s_trivial = trivial ? 1 : 0;
+      if (cta == 0) {
+        V[(int64_t)j * m + j] = tau;
+        tau_out[j] = tau;
+        e[j] = beta;
+      }
     }
     const int t0 = (j + 1 > cta) ? (j + 1 - cta + P - 1) / P : 0;  // first own row beyond j
-    for (int t = t0 + tid; t < nr; t += TCL_THREADS) rp[t] = O::zero();
+    for (int t = t0 + tid; t < nr; t += TCL_THREADS) rpE[t] = AR::zero();
+    __syncthreads();
+    {
+      T* vrow = V + (int64_t)j * m;
+      const E sc = s_scaleE;
+      const bool triv = s_trivial != 0;
+      for (int c = j + 1 + tid; c < m; c += TCL_THREADS) {
+        const E v = (c == j + 1) ? AR::one() : (triv ? AR::zero() : AR::mul(xE[c], sc));
+        vE[c] = v;
+        if (c % P == cta) vrow[c] = AR::back(v);  // the reflectors, written by the rows' owners
+      }
+    }
     __syncthreads();
 
     // 2. this CTA's share of A v: warps over own rows, lanes over columns
     for (int base = j + 1; base < m; base += TCL_CHUNK) {
       E acc[TCL_CHUNK / 32];
 #pragma unroll
-      for (int q = 0; q < TCL_CHUNK / 32; ++q) acc[q] = AR::cvt(O::zero());
+      for (int q = 0; q < TCL_CHUNK / 32; ++q) acc[q] = AR::zero();
       for (int t = t0 + warp; t < nr; t += TCL_WARPS) {
         const int r = cta + P * t;
         if (r < base) continue;
         const E* row = rows + row_off(cta, P, t);
         const E vr = vE[r];
-        E racc = AR::cvt(O::zero());
+        E racc = AR::zero();
 #pragma unroll
         for (int q = 0; q < TCL_CHUNK / 32; ++q) {
           const int c = base + lane + 32 * q;
           if (c <= r) {
             const E x = row[c];
-            racc = AR::mac(x, vE[c], racc);                 // A[r][c] v_c       -> p_r
+            racc = AR::mac(x, vE[c], racc);                      // A[r][c] v_c       -> p_r
             if (c < r) acc[q] = AR::mac(AR::cj(x), vr, acc[q]);  // conj(A[r][c]) v_r -> p_c
           }
         }
-        T rs = AR::back(racc);
-        if constexpr (O::cplx) {
-          rs.re = warp_sum(rs.re);
-          rs.im = warp_sum(rs.im);
-        } else {
-          rs = warp_sum(rs);
-        }
-        if (lane == 0) rp[t] = rp[t] + rs;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) racc = AR::add(racc, AR::shfl(racc, o));
+        if (lane == 0) rpE[t] = AR::add(rpE[t], racc);
       }
 #pragma unroll
       for (int q = 0; q < TCL_CHUNK / 32; ++q) {
         const int c = base + lane + 32 * q;
-        if (c < m) wpart[(size_t)warp * m + c] = AR::back(acc[q]);
+        if (c < m) wpartE[(size_t)warp * m + c] = acc[q];
       }
     }
     __syncthreads();
     for (int c = j + 1 + tid; c < m; c += TCL_THREADS) {
-      T sum = (c % P == cta) ? rp[c / P] : O::zero();
-      for (int w = 0; w < TCL_WARPS; ++w) sum = sum + wpart[(size_t)w * m + c];
-      pp[c] = sum;
+      E sum = (c % P == cta) ? rpE[c / P] : AR::zero();
+      for (int w = 0; w < TCL_WARPS; ++w) sum = AR::add(sum, wpartE[(size_t)w * m + c]);
+      ppE[c] = sum;
     }
     cluster.sync();  // every share of A v is ready
 
-    // 3. p = tau A v from the P shares in a fixed order; w; the rank-2 update
-    for (int c = j + 1 + tid; c < m; c += TCL_THREADS) {
-      T sum = O::zero();
-      for (int q = 0; q < P; ++q) sum = sum + cluster.map_shared_rank(pp, q)[c];
-      pfull[c] = tau * sum;
+    // 3. p = tau A v from the P shares in a fixed order; v^H p; w; the rank-2 update
+    E dp = AR::zero();
+    {
+      const E tauE = s_tauE;
+      for (int c = j + 1 + tid; c < m; c += TCL_THREADS) {
+        E sum = AR::zero();
+        for (int q = 0; q < P; ++q) sum = AR::add(sum, cluster.map_shared_rank(ppE, q)[c]);
+        const E p = AR::mul(tauE, sum);
+        pE[c] = p;
+        dp = AR::mac(AR::cj(vE[c]), p, dp);
+      }
     }
+    const E dot = block_sum_e<AR>(dp, redE);
+    if (tid == 0) s_coefE = AR::cvt(O::scale(-0.5, O::conj(s_tau) * AR::back(dot)));
     __syncthreads();
-    double dr = 0.0, di = 0.0;
-    for (int c = j + 1 + tid; c < m; c += TCL_THREADS) {
-      const T t = O::conj(vfull[c]) * pfull[c];
-      dr += O::real(t);
-      di += O::imag(t);
-    }
-    const double2 dd = block_sum2_det(dr, di, red);
-    const T coef = O::scale(-0.5, O::conj(tau) * O::make(dd.x, dd.y));
-    for (int c = j + 1 + tid; c < m; c += TCL_THREADS) {
-      const T w = O::fma(coef, vfull[c], pfull[c]);
-      wfull[c] = w;
-      wE[c] = AR::cvt(w);
+    {
+      const E coef = s_coefE;
+      for (int c = j + 1 + tid; c < m; c += TCL_THREADS) wE[c] = AR::mac(coef, vE[c], pE[c]);
     }
     __syncthreads();
     for (int t = t0 + warp; t < nr; t += TCL_WARPS) {
       const int r = cta + P * t;
       E* row = rows + row_off(cta, P, t);
-      const E nv = AR::cvt(O::scale(-1.0, vfull[r]));
-      const E nw = AR::cvt(O::scale(-1.0, wfull[r]));
+      const E nv = AR::neg(vE[r]);
+      const E nw = AR::neg(wE[r]);
       for (int c = j + 1 + lane; c <= r; c += 32)
         row[c] = AR::mac(nw, AR::cj(vE[c]), AR::mac(nv, AR::cj(wE[c]), row[c]));
     }
@@ -288,8 +338,7 @@ size_t cluster_smem(int m, int P, bool df) {
   cluster_shape<T>(m, P, &rc, &nc);
   const size_t es = sizeof(T);  // a double-float element has the size of its FP64 one
   (void)df;
-  return (size_t)rc * es + ((size_t)5 * m + nc + (size_t)TCL_WARPS * m) * sizeof(T) +
-         (size_t)2 * m * es;
+  return ((size_t)rc + (size_t)5 * m + nc + (size_t)TCL_WARPS * m) * es;
 }
 
 template <typename T>
