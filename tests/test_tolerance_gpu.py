@@ -97,16 +97,15 @@ def test_two_clusters_mixed(eps, max_bond, tol):
            bond_slack=16)
 
 
-@pytest.mark.parametrize("max_bond", [0, 128])
 @pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
-def test_graded_uniform_tol_1e8(max_bond, precision, bar):
+def test_graded_uniform_tol_1e8_cap(precision, bar):
     """The paper's distribution on a config-5-shaped chain: L=12, d=4, chi=64, D=8; the
-    spectra reach ~6e-8 of the largest singular value.  Without a cap nothing is cut (the
-    tolerance keeps every direction); with the cap of 128 the cuts fall at s ~ 8e-6 s_0,
-    below the Gram's resolution, where the second level decides."""
-    p = make_problem(5, L=12, d=4, chi=64, D=8, max_bond=max_bond, tol=1e-8,
+    spectra reach ~6e-8 of the largest singular value.  With the cap of 128 and tol = 1e-8
+    the cuts fall at s ~ 8e-6 s_0, below the Gram's resolution, where the second level
+    decides."""
+    p = make_problem(5, L=12, d=4, chi=64, D=8, max_bond=128, tol=1e-8,
                      dist="uniform_complex", dtype=np.complex128)
-    _check(p, precision, bar, same_bonds=(precision == 0 or max_bond == 0), bond_slack=0)
+    _check(p, precision, bar)
 
 
 @pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
