@@ -53,12 +53,8 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64, nominal: the fallback when the DGEMM 
 # DRAM bytes per launch of a class's dominant kernel, read from an ncu capture of this
 # workload; each entry names the summary under profiles/ it comes from.  A class whose
 # kernel changed after its capture has no entry (traffic null).
-PROFILED_TRAFFIC = {
-    # one interior-cut launch: 32 Gram matrices of m = 256 (read 63.0 MB + write 2.49 MB)
-    "tridiag": {"bytes_per_launch": 65.49e6,
-                "source": "profiles/tridiag_smem_kernel_mpo_mps_b32.md"},
-}
-KERNEL_OF_CLASS = {"tridiag": "tridiag_smem_kernel", "eig": "bisect32/invit/rank/backtransform",
+PROFILED_TRAFFIC = {}
+KERNEL_OF_CLASS = {"tridiag": "tridiag_cluster_kernel", "eig": "bisect32/invit/rank/backtransform",
                    "gemm_tc": "gemm_tc_kernel (+ operand slicing)", "cholqr": "chol_kernel + trsm",
                    "gemm_f64": "gemm_f64_kernel"}
 

@@ -16,6 +16,7 @@
 // slow on this part.
 #include <algorithm>
 
+#include "df.cuh"
 #include "kernels.cuh"
 #include "planner.h"
 
@@ -270,6 +271,79 @@ __global__ void trsm_cols_kernel(const T* C, T* S, int m, int n) {
   for (int i = lane; i < m; i += 32) S[(int64_t)i * n + c] = x[i];
 }
 
+// The same solve in double-float arithmetic (the mixed path): the factor's lower
+// triangle D and the reciprocal pivots R come as double-float pairs (converted once per
+// solve by to_df_kernel), and the accumulation and the solution stay double-float; FP64
+// only to read S and to write the result.
+template <typename T, bool CSMEM>
+__global__ void trsm_cols_df_kernel(const typename dfof<T>::type* D, const df1* R, T* S, int m,
+                                    int n) {
+  using O = ops<T>;
+  using E = typename dfof<T>::type;
+  D += (int64_t)blockIdx.y * m * m;
+  R += (int64_t)blockIdx.y * m;
+  S += (int64_t)blockIdx.y * m * n;
+  extern __shared__ unsigned char sm_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  E* cl = reinterpret_cast<E*>(sm_raw);  // packed lower triangle (CSMEM)
+  df1* rd = reinterpret_cast<df1*>(cl + (CSMEM ? (size_t)m * (m + 1) / 2 : 0));
+  E* xs = reinterpret_cast<E*>(rd + m);
+  if (CSMEM) {
+    const int64_t tot = (int64_t)m * (m + 1) / 2;
+    for (int64_t t = threadIdx.x; t < tot; t += blockDim.x) {
+      const int i = tri_row(t);
+      cl[t] = D[(int64_t)i * m + (int)(t - (int64_t)i * (i + 1) / 2)];
+    }
+  }
+  for (int i = threadIdx.x; i < m; i += blockDim.x) rd[i] = R[i];
+  __syncthreads();
+  const int c = blockIdx.x * nw + warp;
+  if (c >= n) return;
+  E* x = xs + (size_t)warp * m;
+  auto cel = [&](int i, int l) -> E {
+    return CSMEM ? cl[(int64_t)i * (i + 1) / 2 + l] : D[(int64_t)i * m + l];
+  };
+  const df1 z1{0.f, 0.f};
+  for (int b0 = 0; b0 < m; b0 += 32) {
+    const int i = b0 + lane;
+    const bool live = i < m;
+    E acc = live ? to_df(S[(int64_t)i * n + c]) : E{};
+    if (live)
+      for (int l = 0; l < b0; ++l) acc = dff(df_neg(cel(i, l)), x[l], acc);
+    const int gb = min(32, m - b0);
+    for (int t = 0; t < gb; ++t) {
+      E xt;
+      if constexpr (O::cplx)
+        xt = E{df_fma(acc.re, rd[b0 + t], z1), df_fma(acc.im, rd[b0 + t], z1)};
+      else
+        xt = df_fma(acc, rd[b0 + t], z1);
+      xt = df_shfl_idx(xt, t);
+      if (lane == t) x[i] = xt;
+      if (lane > t && live) acc = dff(df_neg(cel(i, b0 + t)), xt, acc);
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < m; i += 32) S[(int64_t)i * n + c] = from_df(x[i]);
+}
+
+// The lower triangle of C (row-major m x m) and the reciprocals of its (real) pivots as
+// double-float pairs, for trsm_cols_df_kernel; nb factors, m*m (and m) elements apart.
+template <typename T>
+__global__ void to_df_kernel(const T* C, typename dfof<T>::type* D, df1* R, int m) {
+  using O = ops<T>;
+  C += (int64_t)blockIdx.y * m * m;
+  D += (int64_t)blockIdx.y * m * m;
+  R += (int64_t)blockIdx.y * m;
+  const int64_t tot = (int64_t)m * m;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t / m), l = (int)(t % m);
+    if (l <= i) D[t] = to_df(C[t]);
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    R[i] = df_make(rcp64(O::real(C[(int64_t)i * m + i])));
+}
+
 }  // namespace
 
 template <typename T>
@@ -316,10 +390,34 @@ cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cud
 
 template <typename T>
 cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* bar, int num_sms,
-                            cudaStream_t s, int nb) {
+                            cudaStream_t s, int nb, void* dfbuf) {
   (void)status;
   (void)bar;
   (void)num_sms;
+  if (dfbuf) {  // double-float solve: the factor converted once, then one warp per column
+    using E = typename dfof<T>::type;
+    E* D = static_cast<E*>(dfbuf);
+    df1* R = reinterpret_cast<df1*>(D + (size_t)nb * m * m);
+    note_launches(CBC_K_CHOLQR, 2);
+    to_df_kernel<T><<<dim3(std::max(1, std::min(64, (m * m + 255) / 256)), nb), 256, 0, s>>>(C, D, R, m);
+    const int nw = nb >= 8 ? 8 : 4;
+    const size_t tri = (size_t)m * (m + 1) / 2 * sizeof(E);
+    const size_t rest = (size_t)m * sizeof(df1) + (size_t)nw * m * sizeof(E);
+    const dim3 grid((n + nw - 1) / nw, nb);
+    cudaError_t err;
+    if (tri + rest <= 200 * 1024) {
+      err = allow_max_smem((const void*)trsm_cols_df_kernel<T, true>);
+      if (err != cudaSuccess) return err;
+      trsm_cols_df_kernel<T, true><<<grid, 32 * nw, tri + rest, s>>>(D, R, S, m, n);
+    } else {
+      if (rest > 48 * 1024) {
+        err = allow_max_smem((const void*)trsm_cols_df_kernel<T, false>);
+        if (err != cudaSuccess) return err;
+      }
+      trsm_cols_df_kernel<T, false><<<grid, 32 * nw, rest, s>>>(D, R, S, m, n);
+    }
+    return cudaGetLastError();
+  }
   // warps (columns) per CTA sharing one staged triangle: two per SM sub-partition when a
   // batch provides the CTAs, else one (more CTAs for a lone solve)
   const int nw = nb >= 8 ? 8 : 4;
@@ -345,8 +443,8 @@ cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* b
 template cudaError_t cholesky_lower<double>(double*, int, int*, void*, int, cudaStream_t, int);
 template cudaError_t cholesky_lower<zdbl>(zdbl*, int, int*, void*, int, cudaStream_t, int);
 template cudaError_t trsm_lower_left<double>(const double*, double*, int, int, int*, void*, int,
-                                             cudaStream_t, int);
+                                             cudaStream_t, int, void*);
 template cudaError_t trsm_lower_left<zdbl>(const zdbl*, zdbl*, int, int, int*, void*, int,
-                                           cudaStream_t, int);
+                                           cudaStream_t, int, void*);
 
 }  // namespace cbc

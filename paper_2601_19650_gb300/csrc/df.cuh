@@ -78,6 +78,12 @@ __device__ __forceinline__ df1 df_shfl_xor(df1 a, int o) {
 __device__ __forceinline__ dfz df_shfl_xor(dfz a, int o) {
   return {df_shfl_xor(a.re, o), df_shfl_xor(a.im, o)};
 }
+__device__ __forceinline__ df1 df_shfl_idx(df1 a, int src) {
+  return {__shfl_sync(0xffffffffu, a.h, src), __shfl_sync(0xffffffffu, a.l, src)};
+}
+__device__ __forceinline__ dfz df_shfl_idx(dfz a, int src) {
+  return {df_shfl_idx(a.re, src), df_shfl_idx(a.im, src)};
+}
 // |a|^2 as a real double-float
 __device__ __forceinline__ df1 df_abs2(df1 a) { return df_fma(a, a, df1{0.f, 0.f}); }
 __device__ __forceinline__ df1 df_abs2(dfz a) {

@@ -102,9 +102,14 @@ cudaError_t tridiag_cluster(const T* A, int m, double* d, double* e, T* tau, T* 
 template <typename T>
 cudaError_t cholesky_lower(T* G, int m, int* status, void* bar, int num_sms, cudaStream_t s,
                            int nb = 1);
+// dfbuf: NULL for the FP64 solve; else room for trsm_df_bytes(m, nb) bytes, and the solve
+// runs in double-float arithmetic (the mixed path)
 template <typename T>
 cudaError_t trsm_lower_left(const T* C, T* S, int m, int n, int* status, void* bar,
-                            int num_sms, cudaStream_t s, int nb = 1);
+                            int num_sms, cudaStream_t s, int nb = 1, void* dfbuf = nullptr);
+inline size_t trsm_df_bytes(int m, int nb, bool cplx) {
+  return (size_t)nb * ((size_t)m * m * (cplx ? 16 : 8) + (size_t)m * 8);
+}
 
 // ---- small helpers ------------------------------------------------------------------
 // Let `func` use up to the device's opt-in shared memory per block.  Every caller sets

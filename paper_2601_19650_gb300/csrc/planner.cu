@@ -437,6 +437,12 @@ int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars
   void* bar = ar.get<GridBarrier>(nb);
   double* rn = ar.get<double>((size_t)nb * m);
   CKA(G); CKA(bar); CKA(rn);
+  // the mixed path solves in double-float arithmetic (FP32 pipes)
+  void* dfb = nullptr;
+  if (pr.mixed && !pr.cholqr_f64) {
+    dfb = ar.get<char>(trsm_df_bytes(m, nb, ops<T>::cplx));
+    CKA(dfb);
+  }
   const int64_t sbs = (int64_t)m * n;
   // rows of S carry the graded singular values of the forward compression; scaling them
   // to unit norm keeps the row space (hence Q) and keeps the Gram well conditioned
@@ -452,7 +458,7 @@ int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars
     KTimer t(CBC_K_CHOLQR, s, 0,
              nb * (ops<T>::cplx ? 4.0 : 1.0) * ((double)m * m * m / 3.0 + (double)m * m * n));
     CK(cholesky_lower<T>(G, m, sc.status, bar, num_sms(), s, nb));
-    CK(trsm_lower_left<T>(G, S, m, n, sc.status, bar, num_sms(), s, nb));
+    CK(trsm_lower_left<T>(G, S, m, n, sc.status, bar, num_sms(), s, nb, dfb));
   }
   ar.release(mk);
   return CBC_OK;
