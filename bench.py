@@ -11,6 +11,7 @@ collective on the data path); the step time is the maximum over ranks.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
     python bench.py --impl reference ...   # the FP64 CPU oracle, timed on the host
+    python bench.py --sweep                # error vs runtime, the paper's benchmark (Sec. IV A)
 
 Prints one JSON line (rank 0).
 """
@@ -43,12 +44,16 @@ WORKLOADS = {
     "serving": dict(workload="independent MPO.MPS instances, L ~ U{16..64}, chi in "
                              "{32,64,128,256}, D in {4,8,16,32}, d=2, max_bond = chi, float32",
                     input_dtype="float32"),
+    # the paper's own random benchmark (Sec. IV A), MPS part: the error-vs-runtime sweep
+    "paper": dict(workload="MPO on MPS, L=50, d=3, D_S=D_O=40, complex128 entries with real "
+                           "and imaginary parts iid U[-0.5, 1], max_bond swept 2..40 step 2",
+                  L=50, d=3, chi=40, D=40, input_dtype="complex128"),
     # the large tensor train (config 5)
     "large": dict(workload="MPO on MPS, L=100, d=4, chi=1024, D=32, max_bond=1024, complex64 "
                            "Gaussian entries", L=100, d=4, chi=1024, D=32, max_bond=1024,
                   input_dtype="complex64"),
 }
-DEFAULT_B = {"mpo_mps": 32, "tree": 8, "serving": 256, "large": 1}
+DEFAULT_B = {"mpo_mps": 32, "tree": 8, "serving": 256, "large": 1, "paper": 1}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64, nominal: the fallback when the DGEMM probe fails
 # DRAM bytes per launch of a class's dominant kernel, read from an ncu capture of this
 # workload; each entry names the summary under profiles/ it comes from.  A class whose
@@ -149,7 +154,7 @@ class ClockSampler:
 def make_workload(seed: int, sites: int = 0, workload: str = "mpo_mps"):
     """One instance of a tensor-train or tree workload (`sites` shortens a chain)."""
     from synth import make_problem
-    cfg = {"mpo_mps": 2, "tree": 3, "large": 5}[workload]
+    cfg = {"mpo_mps": 2, "tree": 3, "large": 5, "paper": "P"}[workload]
     over = {"L": sites} if (sites > 0 and workload != "tree") else {}
     return make_problem(cfg, seed=seed, **over)
 
@@ -208,6 +213,67 @@ def blas_threads() -> int:
     return os.cpu_count() or 1
 
 
+def run_sweep(args, local):
+    """Error against runtime of one application of the paper's benchmark MPS/MPO (Sec. IV A)
+    for max_bond = 2, 4, ..., 40, in both precisions.  The error is ||O psi - psi'|| /
+    ||O psi||: the output is the orthogonal projection of O psi onto the new isometries, so
+    ||O psi - psi'||^2 = ||O psi||^2 - ||psi'||^2, with ||O psi||^2 from one exact FP64
+    sandwich contraction (the oracle's chain_applied_norm2)."""
+    import numpy as np
+    import torch
+
+    from oracle import metrics
+    from paper_2601_19650_gb300 import _cbc, build as _build
+    from synth import make_problem
+
+    _build.build()
+    torch.cuda.set_device(local)
+    p = make_problem("P", seed=0)
+    st, op = p.state, p.op
+    t0 = time.perf_counter()
+    n2 = metrics.chain_applied_norm2(st.tensors, op.tensors)
+    t_norm = time.perf_counter() - t0
+    hs = _cbc.create_from_host(st.parent, st.phys, st.bond, st.tensors, "state")
+    ho = _cbc.create_from_host(op.parent, op.phys, op.bond, op.tensors, "op")
+    shape = _cbc.output_shape_fn(st.parent, st.phys)
+    rows = []
+    for mb in range(2, 41, 2):
+        row = {"max_bond": mb}
+        for name, prec in (("mixed", _cbc.CBC_PREC_MIXED), ("fp64", _cbc.CBC_PREC_FP64)):
+            opt = _cbc.make_options(prec)
+            _cbc.ttn_destroy(_cbc.cbc_apply(hs, ho, mb, 0.0, opt))  # warm-up
+            times = []
+            out = None
+            for _ in range(3):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                if out is not None:
+                    _cbc.ttn_destroy(out)
+                out = _cbc.cbc_apply(hs, ho, mb, 0.0, opt)
+                e1.record()
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+            tens, bonds, log_norm = _cbc.fetch_network(out, shape, True)
+            _cbc.ttn_destroy(out)
+            out2 = float(np.exp(2.0 * log_norm) * np.linalg.norm(tens[0].reshape(-1)) ** 2)
+            err = float(np.sqrt(max(0.0, 1.0 - out2 / n2)))
+            row[name] = {"ms": statistics.median(times), "rel_err": err,
+                         "max_out_bond": int(max(bonds))}
+        rows.append(row)
+    _cbc.ttn_destroy(hs)
+    _cbc.ttno_destroy(ho)
+    line = {"metric": "CBC relative error ||O psi - psi'|| / ||O psi|| against runtime, paper "
+                      "benchmark (Sec. IV A)", "unit": "ms per application",
+            "n_gpus": 1, "data": "synthetic", "dtype": "bf16-slices+f64 | f64",
+            "config": dict(WORKLOADS["paper"], seed=0),
+            "norm_note": f"||O psi||^2 by an exact FP64 sandwich contraction on the host "
+                         f"({t_norm:.1f} s); errors below ~1e-8 sit at FP64 cancellation",
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -254,6 +320,9 @@ def main():
                     help="shorter chains for profiling captures (default: the workload's 64)")
     ap.add_argument("--no-fp64-arm", action="store_true",
                     help="skip timing the same step in plain FP64 (the ratio's denominator)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="error-vs-runtime sweep of the paper's benchmark (max_bond 2..40) "
+                         "instead of the throughput step; prints one line of rows")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="timed steps of the FP64 arm (after one warm-up step)")
     args = ap.parse_args()
@@ -262,6 +331,8 @@ def main():
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.sweep:
+        return run_sweep(args, local) if rank == 0 else 0
 
     import numpy as np
     import torch

@@ -95,3 +95,26 @@ def rel_err(parent, ta, tb, log_a: float = 0.0, log_b: float = 0.0) -> float:
     nb = tree_norm(parent, tb)
     diff = direct_sum_difference(parent, ta, tb, float(np.exp(log_a - log_b)), 1.0)
     return tree_norm(parent, diff) / nb
+
+
+def chain_applied_norm2(state, op) -> float:
+    """||O |psi>||^2 for an MPO applied to an MPS (chain rooted at site 0, canonical
+    layouts), by contracting the sandwich <psi| O^H O |psi> site by site from the left in
+    FP64: the environment E[a, b, b', a'] carries the open bonds of psi, O, conj(O) and
+    conj(psi) (Eqs. (ttns), (ttno); no truncation).  Together with the projection identity
+    ||O psi - psi'||^2 = ||O psi||^2 - ||psi'||^2 it gives the error of a CBC result
+    without densifying O |psi>."""
+    L = len(state)
+    E = np.ones((1, 1, 1, 1), dtype=np.complex128)
+    for i in range(L):
+        t = np.asarray(state[i], dtype=np.complex128)
+        w = np.asarray(op[i], dtype=np.complex128)
+        if i == L - 1:
+            t = t[..., None]
+            w = w[..., None]
+        # E[a, b, c, e] with a: psi, b: O, c: conj(O), e: conj(psi)
+        X = np.einsum("abce,asA->bcesA", E, t, optimize=True)          # sum a
+        Y = np.einsum("bcesA,bPsB->cePAB", X, w, optimize=True)         # sum b, s
+        Z = np.einsum("cePAB,cPtC->etABC", Y, w.conj(), optimize=True)  # sum c, P
+        E = np.einsum("etABC,etD->ABCD", Z, t.conj(), optimize=True)    # sum e, t
+    return float(E.reshape(-1)[0].real)

@@ -86,3 +86,15 @@ def test_metric_single_node():
     a = [np.array([[1.0, 2.0]])]
     b = [np.array([[1.0, 2.5]])]
     assert abs(metrics.rel_err([-1], a, b) - 0.5 / np.linalg.norm([1.0, 2.5])) < 1e-15
+
+
+def test_chain_applied_norm_matches_brute_force():
+    """The sandwich <psi|O^H O|psi> equals ||O psi||^2 of the dense vector (Eqs. (ttns),
+    (ttno)), real and complex, d = 2 and 3."""
+    from oracle import brute, metrics
+    for kw in [dict(L=6, chi=6, D=3, dtype=np.complex128), dict(L=7, chi=8, D=4, d=3,
+                                                              dtype=np.float64, seed=2)]:
+        p = make_problem(2, max_bond=0, **kw)
+        ex = brute.apply_dense(p.state.parent, p.state.tensors, p.op.tensors)
+        got = metrics.chain_applied_norm2(p.state.tensors, p.op.tensors)
+        assert abs(got - np.linalg.norm(ex) ** 2) <= 1e-13 * np.linalg.norm(ex) ** 2
