@@ -126,19 +126,21 @@ cudaError_t launch_cluster(const void* func, int cluster, int grid, int threads,
 // x[i] (i < n) scaled in place to unit Frobenius norm; log of the old norm added to
 // *log_acc; non-finite norm sets CBC_ERR_NUMERICAL.  nb problems: x n elements apart,
 // log_acc and scratch one double apart.
+// shared_log: every problem's log is added into log_acc[0] (atomically) instead of
+// log_acc[b]; scratch still needs nb doubles
 template <typename T>
 cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, double* scratch,
-                              cudaStream_t s, int nb = 1);
+                              cudaStream_t s, int nb = 1, bool shared_log = false);
 // L[r, c] = sqrt(lam[r]) * conj(V[c, r]) for r < k (V: n x ldv row-major), L: k x n;
 // nb problems: V n*ldv, lam n, k_dev 1 and L l_bs elements apart
 template <typename T>
 cudaError_t scaled_adjoint(const T* V, int ldv, const double* lam, const int* k_dev, int n,
                            T* L, cudaStream_t s, int nb = 1, int64_t l_bs = 0);
 // out = in with its axes permuted: out dims are in dims[perm[0]], in dims[perm[1]], ...
-// (row-major, rank <= 8)
+// (row-major, rank <= 8); nb tensors of the same shape, back to back in in and out
 template <typename T>
 cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const int* perm,
-                    cudaStream_t s);
+                    cudaStream_t s, int nb = 1);
 // Squared 2-norms of the rows (out[b * rows + r]) or of the columns (out[b * cols + c])
 // of nb row-major matrices rows x cols with leading dimension ld, bs elements apart.
 template <typename T>

@@ -33,10 +33,11 @@ __global__ void sumsq_kernel(const T* x, int64_t n, double* out) {
 }
 
 template <typename T>
-__global__ void scale_kernel(T* x, int64_t n, const double* sumsq, double* log_acc, int* status) {
+__global__ void scale_kernel(T* x, int64_t n, const double* sumsq, double* log_acc, int* status,
+                             int shared_log) {
   x += (int64_t)blockIdx.y * n;
   sumsq += blockIdx.y;
-  log_acc += blockIdx.y;
+  if (!shared_log) log_acc += blockIdx.y;
   double ss = *sumsq;
   bool ok = isfinite(ss) && ss > 0.0;
   if (!ok) {  // NaN / Inf, or an all-zero tensor (then O|psi> itself vanishes)
@@ -44,7 +45,12 @@ __global__ void scale_kernel(T* x, int64_t n, const double* sumsq, double* log_a
     return;
   }
   double inv = rsqrt(ss);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *log_acc += 0.5 * log(ss);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (shared_log)
+      atomicAdd(log_acc, 0.5 * log(ss));
+    else
+      *log_acc += 0.5 * log(ss);
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     x[i] = ops<T>::scale(inv, x[i]);
@@ -127,6 +133,8 @@ struct PermArgs {
 
 template <typename T>
 __global__ void permute_kernel(const T* in, T* out, int64_t total, PermArgs a) {
+  in += (int64_t)blockIdx.y * total;  // tensor blockIdx.y of a batch
+  out += (int64_t)blockIdx.y * total;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     int64_t rem = t, off = 0;
@@ -332,13 +340,13 @@ cudaError_t launch_cluster(const void* func, int cluster, int grid, int threads,
 
 template <typename T>
 cudaError_t normalize_inplace(T* x, int64_t n, double* log_acc, int* status, double* scratch,
-                              cudaStream_t s, int nb) {
+                              cudaStream_t s, int nb, bool shared_log) {
   cudaError_t err = cudaMemsetAsync(scratch, 0, sizeof(double) * nb, s);
   if (err != cudaSuccess) return err;
   const dim3 g(std::min(grid_for(n), std::max(1, 1024 / nb)), nb);
   note_launches(CBC_K_AUX, 2);
   sumsq_kernel<T><<<g, 256, 0, s>>>(x, n, scratch);
-  scale_kernel<T><<<g, 256, 0, s>>>(x, n, scratch, log_acc, status);
+  scale_kernel<T><<<g, 256, 0, s>>>(x, n, scratch, log_acc, status, shared_log ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -369,7 +377,7 @@ cudaError_t fill_identity(T* dst, int n, cudaStream_t s, int nb) {
 
 template <typename T>
 cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const int* perm,
-                    cudaStream_t s) {
+                    cudaStream_t s, int nb) {
   if (rank < 1 || rank > 8) return cudaErrorInvalidValue;
   int64_t in_stride[8];
   in_stride[rank - 1] = 1;
@@ -384,7 +392,8 @@ cudaError_t permute(const T* in, T* out, int rank, const int64_t* in_dims, const
   }
   if (total == 0) return cudaSuccess;
   note_launches(CBC_K_AUX, 1);
-  permute_kernel<T><<<grid_for(total), 256, 0, s>>>(in, out, total, a);
+  permute_kernel<T><<<dim3(std::min(grid_for(total), std::max(1, 2048 / nb)), nb), 256, 0, s>>>(
+      in, out, total, a);
   return cudaGetLastError();
 }
 
@@ -492,17 +501,17 @@ CBC_MISC_INST(zdbl)
 #undef CBC_MISC_INST
 
 template cudaError_t normalize_inplace<double>(double*, int64_t, double*, int*, double*,
-                                               cudaStream_t, int);
+                                               cudaStream_t, int, bool);
 template cudaError_t normalize_inplace<zdbl>(zdbl*, int64_t, double*, int*, double*, cudaStream_t,
-                                             int);
+                                             int, bool);
 template cudaError_t scaled_adjoint<double>(const double*, int, const double*, const int*, int,
                                             double*, cudaStream_t, int, int64_t);
 template cudaError_t scaled_adjoint<zdbl>(const zdbl*, int, const double*, const int*, int, zdbl*,
                                           cudaStream_t, int, int64_t);
 template cudaError_t permute<double>(const double*, double*, int, const int64_t*, const int*,
-                                     cudaStream_t);
+                                     cudaStream_t, int);
 template cudaError_t permute<zdbl>(const zdbl*, zdbl*, int, const int64_t*, const int*,
-                                   cudaStream_t);
+                                   cudaStream_t, int);
 template cudaError_t group_copy<double>(double* const*, double*, int64_t, int64_t, int, bool,
                                         cudaStream_t);
 template cudaError_t group_copy<zdbl>(zdbl* const*, zdbl*, int64_t, int64_t, int, bool,

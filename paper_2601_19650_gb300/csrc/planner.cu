@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <utility>
 #include <vector>
 
@@ -713,12 +714,20 @@ int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Opt
 }
 
 // ---- trees (Sec. III B) ---------------------------------------------------------------
-// A device tensor with named legs, row-major in the order of `legs`.
+// Nodes with identical shapes at the same depth (and, in step 2, edges with identical
+// shapes at the same depth) form groups that run in lockstep like the instances of a
+// chain group: every contraction, Gram product, eigensolve, CholeskyQR and normalisation
+// of a group is one launch, on node tensors and environments gathered into contiguous
+// buffers.  In a perfect binary tree every depth is one group (two in step 2, one per
+// child slot).  A group whose members choose different ranks runs one node at a time.
+
+// nb tensors with named legs, row-major in the order of `legs`, size() elements apart
 template <typename T>
 struct DT {
   T* p = nullptr;
   std::vector<int> legs;
   std::vector<int64_t> dims;
+  int nb = 1;
   int64_t size() const {
     int64_t n = 1;
     for (int64_t d : dims) n *= d;
@@ -741,14 +750,15 @@ int reorder(Arena& ar, const DT<T>& t, const std::vector<int>& order, DT<T>* out
   std::vector<int> perm(order.size());
   DT<T> r;
   r.legs = order;
+  r.nb = t.nb;
   for (size_t i = 0; i < order.size(); ++i) {
     perm[i] = t.pos(order[i]);
     if (perm[i] < 0) return fail(CBC_ERR_INVALID_ARG, "tree planner: leg %d missing", order[i]);
     r.dims.push_back(t.dims[perm[i]]);
   }
-  r.p = ar.get<T>((size_t)t.size());
+  r.p = ar.get<T>((size_t)t.size() * t.nb);
   CKA(r.p);
-  CK(permute<T>(t.p, r.p, (int)t.legs.size(), t.dims.data(), perm.data(), s));
+  CK(permute<T>(t.p, r.p, (int)t.legs.size(), t.dims.data(), perm.data(), s, t.nb));
   *out = r;
   return CBC_OK;
 }
@@ -771,6 +781,7 @@ int contract(Arena& ar, const Prec& pr, bool fwd, const DT<T>& A, const DT<T>& B
   if (rc != CBC_OK) return rc;
   int64_t M = 1, K = 1, N = 1;
   DT<T> c;
+  c.nb = A.nb;
   for (int l : fa) {
     M *= A.dims[A.pos(l)];
     c.legs.push_back(l);
@@ -784,11 +795,31 @@ int contract(Arena& ar, const Prec& pr, bool fwd, const DT<T>& A, const DT<T>& B
   }
   if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX)
     return fail(CBC_ERR_UNSUPPORTED, "tree planner: contraction dimension beyond 2^31");
-  c.p = ar.get<T>((size_t)(M * N));
+  c.p = ar.get<T>((size_t)(M * N) * c.nb);
   CKA(c.p);
-  CK(tgemm<T>(pr, fwd, false, (int)M, (int)N, (int)K, A2.p, View::rowmajor(K), false, B2.p,
-              View::rowmajor(N), false, c.p, View::rowmajor(N), s));
+  Prec pg = pr;
+  pg.nb = c.nb;
+  CK(tgemm<T>(pg, fwd, false, (int)M, (int)N, (int)K, A2.p, View::rowmajor(K, M * K), false, B2.p,
+              View::rowmajor(N, K * N), false, c.p, View::rowmajor(N, M * N), s));
   *C = c;
+  return CBC_OK;
+}
+
+// nb tensors of ne elements (device pointers) back to back: one gather launch, none for
+// a single tensor
+template <typename T>
+int gather(Arena& ar, const std::vector<const T*>& ptrs, int64_t ne, cudaStream_t s, T** out) {
+  const int nb = (int)ptrs.size();
+  if (nb == 1) {
+    *out = const_cast<T*>(ptrs[0]);
+    return CBC_OK;
+  }
+  T** tab = ar.get<T*>(nb);
+  T* g = ar.get<T>((size_t)nb * ne);
+  CKA(tab); CKA(g);
+  CK(cudaMemcpyAsync(tab, ptrs.data(), sizeof(T*) * nb, cudaMemcpyHostToDevice, s));
+  CK(group_copy<T>(tab, g, ne, ne, nb, true, s));
+  *out = g;
   return CBC_OK;
 }
 
@@ -798,159 +829,300 @@ inline int lg_a(int j) { return 10 + 3 * j; }
 inline int lg_b(int j) { return 11 + 3 * j; }
 inline int lg_x(int j) { return 12 + 3 * j; }
 
+// groups of equal signature, in order of first appearance
+std::vector<std::vector<int>> group_by(const std::vector<std::vector<int64_t>>& sig) {
+  std::vector<std::vector<int>> groups;
+  std::vector<int> rep;
+  for (int q = 0; q < (int)sig.size(); ++q) {
+    int g = -1;
+    for (size_t h = 0; h < rep.size(); ++h)
+      if (sig[rep[h]] == sig[q]) {
+        g = (int)h;
+        break;
+      }
+    if (g < 0) {
+      rep.push_back(q);
+      groups.push_back({q});
+    } else {
+      groups[g].push_back(q);
+    }
+  }
+  return groups;
+}
+
 template <typename T>
 int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
              Net* out) {
   cudaStream_t s = st.stream;
   const int n = st.n;
   const auto& ch = st.children;
-  Arena ar(s);
-  int* d_int = ar.get<int>(4);
-  double* d_dbl = ar.get<double>(4);
+  Arena ar(s);   // environments and scalars: the whole call
+  Arena tmp(s);  // per group: gathers, contractions, workspaces
+  // scalars: status, k per group member, the output's log scale, and per member the
+  // forward log scales (unused) and the normalisation scratch
+  int* d_int = ar.get<int>(1 + n);
+  double* d_dbl = ar.get<double>(1 + 2 * (size_t)n);
   CKA(d_int);
   CKA(d_dbl);
-  CK(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
-  CK(cudaMemsetAsync(d_dbl, 0, 4 * sizeof(double), s));
-  Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + 1, d_dbl + 2};
+  CK(cudaMemsetAsync(d_int, 0, (1 + n) * sizeof(int), s));
+  CK(cudaMemsetAsync(d_dbl, 0, (1 + 2 * (size_t)n) * sizeof(double), s));
+  Scalars sc{d_int, d_int + 1, d_dbl + 1, d_dbl, d_dbl + 1 + n};
   Prec pr;
   pr.mixed = (o.precision == CBC_PREC_MIXED);
   pr.cholqr_f64 = o.cholqr_f64;
   pr.s_fwd = o.slices_fwd;
   pr.s_bwd = o.slices_bwd;
-  pr.ar = &ar;
+  pr.ar = &tmp;
   pr.status = sc.status;
   const T one = host_one<T>();
-  // post-order (children first)
-  std::vector<int> post;
+  std::vector<int> depth(n, 0);
+  int maxd = 0;
   {
-    std::vector<std::pair<int, bool>> stack{{st.root, false}};
+    std::vector<int> stack{st.root};
     while (!stack.empty()) {
-      auto [v, done] = stack.back();
+      const int v = stack.back();
       stack.pop_back();
-      if (done) {
-        post.push_back(v);
-      } else {
-        stack.push_back({v, true});
-        for (int j = (int)ch[v].size() - 1; j >= 0; --j) stack.push_back({ch[v][j], false});
+      for (int c : ch[v]) {
+        depth[c] = depth[v] + 1;
+        maxd = std::max(maxd, depth[c]);
+        stack.push_back(c);
       }
     }
   }
-  auto tensT = [&](int i) {
-    DT<T> t;
-    t.p = static_cast<T*>(st.data[i]);
-    t.legs = {LG_AP, LG_SIN};
-    t.dims = {st.bond[i], st.phys[i]};
+  // node tensors of a group, gathered
+  auto tensT = [&](const std::vector<int>& G, DT<T>* t) -> int {
+    const int i = G[0];
+    std::vector<const T*> ptrs;
+    for (int g : G) ptrs.push_back(static_cast<const T*>(st.data[g]));
+    t->legs = {LG_AP, LG_SIN};
+    t->dims = {st.bond[i], st.phys[i]};
     for (size_t j = 0; j < ch[i].size(); ++j) {
-      t.legs.push_back(lg_a((int)j));
-      t.dims.push_back(st.bond[ch[i][j]]);
+      t->legs.push_back(lg_a((int)j));
+      t->dims.push_back(st.bond[ch[i][j]]);
     }
-    return t;
+    t->nb = (int)G.size();
+    return gather<T>(tmp, ptrs, st.numel[i], s, &t->p);
   };
-  auto tensW = [&](int i) {
-    DT<T> t;
-    t.p = static_cast<T*>(op.data[i]);
-    t.legs = {LG_BP, LG_SOUT, LG_SIN};
-    t.dims = {op.bond[i], op.phys[i], op.phys[i]};
+  auto tensW = [&](const std::vector<int>& G, DT<T>* t) -> int {
+    const int i = G[0];
+    std::vector<const T*> ptrs;
+    for (int g : G) ptrs.push_back(static_cast<const T*>(op.data[g]));
+    t->legs = {LG_BP, LG_SOUT, LG_SIN};
+    t->dims = {op.bond[i], op.phys[i], op.phys[i]};
     for (size_t j = 0; j < ch[i].size(); ++j) {
-      t.legs.push_back(lg_b((int)j));
-      t.dims.push_back(op.bond[ch[i][j]]);
+      t->legs.push_back(lg_b((int)j));
+      t->dims.push_back(op.bond[ch[i][j]]);
     }
-    return t;
+    t->nb = (int)G.size();
+    return gather<T>(tmp, ptrs, op.numel[i], s, &t->p);
   };
-  // an environment (chi, b, a) of node c seen from its parent's child slot j (or parent)
-  auto env_on = [&](T* p, int64_t chi, int c, int x, int b, int a) {
-    DT<T> t;
-    t.p = p;
-    t.legs = {x, b, a};
-    t.dims = {chi, op.bond[c], st.bond[c]};
-    return t;
+  // environments (chi, b, a) of node c (per member: envs[b]), gathered
+  auto env_on = [&](const std::vector<const T*>& envs, int64_t chi, int c, int x, int b, int a,
+                    DT<T>* t) -> int {
+    t->legs = {x, b, a};
+    t->dims = {chi, op.bond[c], st.bond[c]};
+    t->nb = (int)envs.size();
+    return gather<T>(tmp, envs, chi * op.bond[c] * st.bond[c], s, &t->p);
   };
   // T, the first environment, W, the remaining environments (pairwise, in this order)
-  auto contract_node = [&](int i, const std::vector<DT<T>>& envs, const std::vector<int>& legs_out,
-                           bool fwd, DT<T>* res) -> int {
-    DT<T> cur = tensT(i), nxt;
+  auto contract_node = [&](const DT<T>& Tt, const DT<T>& Wt, const std::vector<DT<T>>& envs,
+                           const std::vector<int>& legs_out, bool fwd, DT<T>* res) -> int {
+    DT<T> cur = Tt, nxt;
     int rc;
     size_t e = 0;
     if (!envs.empty()) {
-      rc = contract(ar, pr, fwd, cur, envs[0], &nxt, s);
+      rc = contract(tmp, pr, fwd, cur, envs[0], &nxt, s);
       if (rc != CBC_OK) return rc;
       cur = nxt;
       e = 1;
     }
-    rc = contract(ar, pr, fwd, cur, tensW(i), &nxt, s);
+    rc = contract(tmp, pr, fwd, cur, Wt, &nxt, s);
     if (rc != CBC_OK) return rc;
     cur = nxt;
     for (; e < envs.size(); ++e) {
-      rc = contract(ar, pr, fwd, cur, envs[e], &nxt, s);
+      rc = contract(tmp, pr, fwd, cur, envs[e], &nxt, s);
       if (rc != CBC_OK) return rc;
       cur = nxt;
     }
-    return reorder(ar, cur, legs_out, res, s);
+    return reorder(tmp, cur, legs_out, res, s);
+  };
+  std::vector<double> disc(n, 0.0);  // per edge: steps 1 and 2
+  std::vector<double> dcut(n, 0.0);
+  // a group, then its members one by one when they choose different ranks
+  auto run_groups = [&](const std::vector<std::vector<int>>& groups,
+                        const std::function<int(const std::vector<int>&)>& step) -> int {
+    for (const auto& G : groups) {
+      const size_t mk = tmp.mark();
+      int rc = step(G);
+      tmp.release(mk);
+      if (rc == kGroupSplit) {
+        for (int g : G) {
+          const size_t mk2 = tmp.mark();
+          rc = step({g});
+          tmp.release(mk2);
+          if (rc != CBC_OK) return rc;
+        }
+      } else if (rc != CBC_OK) {
+        return rc;
+      }
+    }
+    return CBC_OK;
   };
 
-  // ---- step 1, Eq. (cbc_tree_first_contraction): subtree environments, leaves first
-  std::vector<double> disc(n, 0.0);  // per edge: steps 1 and 2
+  // ---- step 1, Eq. (cbc_tree_first_contraction): subtree environments, deepest first
   std::vector<T*> Lsub(n, nullptr);
   std::vector<int64_t> chi_sub(n, 1);
-  for (int i : post) {
-    if (i == st.root) continue;
+  auto step1 = [&](const std::vector<int>& G) -> int {
+    const int i = G[0];
+    const int nb = (int)G.size();
+    DT<T> Tt, Wt;
+    int rc = tensT(G, &Tt);
+    if (rc == CBC_OK) rc = tensW(G, &Wt);
+    if (rc != CBC_OK) return rc;
     std::vector<DT<T>> envs;
     std::vector<int> lo{LG_SOUT};
     int64_t m = st.phys[i];
     for (size_t j = 0; j < ch[i].size(); ++j) {
+      std::vector<const T*> ep;
+      for (int g : G) ep.push_back(Lsub[ch[g][j]]);
       const int c = ch[i][j];
-      envs.push_back(env_on(Lsub[c], chi_sub[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j)));
+      DT<T> e;
+      rc = env_on(ep, chi_sub[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j), &e);
+      if (rc != CBC_OK) return rc;
+      envs.push_back(e);
       lo.push_back(lg_x((int)j));
       m *= chi_sub[c];
     }
     lo.push_back(LG_BP);
     lo.push_back(LG_AP);
     DT<T> M;
-    int rc = contract_node(i, envs, lo, true, &M);
+    rc = contract_node(Tt, Wt, envs, lo, true, &M);
     if (rc != CBC_OK) return rc;
+    Prec pg = pr;
+    pg.nb = nb;
+    const int n2 = (int)(op.bond[i] * st.bond[i]);
+    T* L = nullptr;
     int k = 0;
-    double dc = 0.0;
-    rc = compress_rows<T>(ar, pr, M.p, (int)m, (int)(op.bond[i] * st.bond[i]), max_bond, tol, o,
-                          sc, s, &Lsub[i], &k, nullptr, &dc);
+    rc = compress_rows<T>(tmp, pg, M.p, (int)m, n2, max_bond, tol, o, sc, s, &L, &k, &ar,
+                          dcut.data());
     if (rc != CBC_OK) return rc;
-    disc[i] += dc;
-    chi_sub[i] = k;
+    for (int b = 0; b < nb; ++b) {
+      Lsub[G[b]] = L + (size_t)b * k * n2;
+      chi_sub[G[b]] = k;
+      disc[G[b]] += dcut[b];
+    }
+    return CBC_OK;
+  };
+  for (int dd = maxd; dd >= 1; --dd) {
+    std::vector<int> nodes;
+    std::vector<std::vector<int64_t>> sig;
+    for (int i = 0; i < n; ++i) {
+      if (depth[i] != dd) continue;
+      std::vector<int64_t> g{st.phys[i], st.bond[i], op.bond[i], (int64_t)ch[i].size()};
+      for (int c : ch[i]) {
+        g.push_back(chi_sub[c]);
+        g.push_back(st.bond[c]);
+        g.push_back(op.bond[c]);
+      }
+      nodes.push_back(i);
+      sig.push_back(g);
+    }
+    std::vector<std::vector<int>> groups;
+    for (const auto& q : group_by(sig)) {
+      std::vector<int> G;
+      for (int x : q) G.push_back(nodes[x]);
+      groups.push_back(G);
+    }
+    int rc = run_groups(groups, step1);
+    if (rc != CBC_OK) return rc;
   }
-  // ---- step 2, Eq. (cbc_tree_second_contraction): complements, root first
+
+  // ---- step 2, Eq. (cbc_tree_second_contraction): complements, root first; an item is
+  // an edge (node i, child slot jk), grouped by slot and shapes
   std::vector<T*> Ldown(n, nullptr);
   std::vector<int64_t> chi_down(n, 1);
   Ldown[st.root] = ar.get<T>(1);
   CKA(Ldown[st.root]);
   CK(cudaMemcpyAsync(Ldown[st.root], &one, sizeof(T), cudaMemcpyHostToDevice, s));
-  for (auto it = post.rbegin(); it != post.rend(); ++it) {
-    const int i = *it;
-    for (size_t jk = 0; jk < ch[i].size(); ++jk) {
-      const int k = ch[i][jk];
-      std::vector<DT<T>> envs{env_on(Ldown[i], chi_down[i], i, LG_XP, LG_BP, LG_AP)};
-      std::vector<int> lo{LG_SOUT, LG_XP};
-      int64_t m = st.phys[i] * chi_down[i];
-      for (size_t j = 0; j < ch[i].size(); ++j) {
-        if (j == jk) continue;
-        const int c = ch[i][j];
-        envs.push_back(env_on(Lsub[c], chi_sub[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j)));
-        lo.push_back(lg_x((int)j));
-        m *= chi_sub[c];
-      }
-      lo.push_back(lg_b((int)jk));
-      lo.push_back(lg_a((int)jk));
-      DT<T> M;
-      int rc = contract_node(i, envs, lo, true, &M);
+  std::vector<std::pair<int, int>> items;
+  auto step2 = [&](const std::vector<int>& G) -> int {
+    const int i = items[G[0]].first, jk = items[G[0]].second;
+    const int nb = (int)G.size();
+    std::vector<int> nodes;
+    for (int q : G) nodes.push_back(items[q].first);
+    DT<T> Tt, Wt;
+    int rc = tensT(nodes, &Tt);
+    if (rc == CBC_OK) rc = tensW(nodes, &Wt);
+    if (rc != CBC_OK) return rc;
+    std::vector<DT<T>> envs;
+    {
+      std::vector<const T*> ep;
+      for (int g : nodes) ep.push_back(Ldown[g]);
+      DT<T> e;
+      rc = env_on(ep, chi_down[i], i, LG_XP, LG_BP, LG_AP, &e);
       if (rc != CBC_OK) return rc;
-      int kk = 0;
-      double dc = 0.0;
-      rc = compress_rows<T>(ar, pr, M.p, (int)m, (int)(op.bond[k] * st.bond[k]), max_bond, tol, o,
-                            sc, s, &Ldown[k], &kk, nullptr, &dc);
-      if (rc != CBC_OK) return rc;
-      disc[k] += dc;
-      chi_down[k] = kk;
+      envs.push_back(e);
     }
+    std::vector<int> lo{LG_SOUT, LG_XP};
+    int64_t m = st.phys[i] * chi_down[i];
+    for (size_t j = 0; j < ch[i].size(); ++j) {
+      if ((int)j == jk) continue;
+      std::vector<const T*> ep;
+      for (int g : nodes) ep.push_back(Lsub[ch[g][j]]);
+      const int c = ch[i][j];
+      DT<T> e;
+      rc = env_on(ep, chi_sub[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j), &e);
+      if (rc != CBC_OK) return rc;
+      envs.push_back(e);
+      lo.push_back(lg_x((int)j));
+      m *= chi_sub[c];
+    }
+    lo.push_back(lg_b(jk));
+    lo.push_back(lg_a(jk));
+    DT<T> M;
+    rc = contract_node(Tt, Wt, envs, lo, true, &M);
+    if (rc != CBC_OK) return rc;
+    const int k0 = ch[i][jk];
+    Prec pg = pr;
+    pg.nb = nb;
+    const int n2 = (int)(op.bond[k0] * st.bond[k0]);
+    T* L = nullptr;
+    int kk = 0;
+    rc = compress_rows<T>(tmp, pg, M.p, (int)m, n2, max_bond, tol, o, sc, s, &L, &kk, &ar,
+                          dcut.data());
+    if (rc != CBC_OK) return rc;
+    for (int b = 0; b < nb; ++b) {
+      const int kc = ch[nodes[b]][jk];
+      Ldown[kc] = L + (size_t)b * kk * n2;
+      chi_down[kc] = kk;
+      disc[kc] += dcut[b];
+    }
+    return CBC_OK;
+  };
+  for (int dd = 0; dd < maxd; ++dd) {
+    items.clear();
+    std::vector<std::vector<int64_t>> sig;
+    for (int i = 0; i < n; ++i) {
+      if (depth[i] != dd) continue;
+      for (size_t jk = 0; jk < ch[i].size(); ++jk) {
+        std::vector<int64_t> g{(int64_t)jk, st.phys[i], st.bond[i], op.bond[i], chi_down[i],
+                               (int64_t)ch[i].size()};
+        for (size_t j = 0; j < ch[i].size(); ++j) {
+          const int c = ch[i][j];
+          g.push_back(j == jk ? -1 : chi_sub[c]);
+          g.push_back(st.bond[c]);
+          g.push_back(op.bond[c]);
+        }
+        items.push_back({i, (int)jk});
+        sig.push_back(g);
+      }
+    }
+    int rc = run_groups(group_by(sig), step2);
+    if (rc != CBC_OK) return rc;
   }
-  // ---- step 3, Eqs. (cbc_tree_third_contraction), (cbc_tree_qr), (cbc_final_contraction)
+
+  // ---- step 3, Eqs. (cbc_tree_third_contraction), (cbc_tree_qr), (cbc_final_contraction):
+  // deepest first
   out->kind = 0;
   out->n = n;
   out->root = st.root;
@@ -965,55 +1137,113 @@ int run_tree(const Net& st, const Net& op, int64_t max_bond, double tol, const O
   out->discarded = disc;
   std::vector<T*> R(n, nullptr);
   std::vector<int64_t> chi_r(n, 1);
-  for (int i : post) {
+  auto step3 = [&](const std::vector<int>& G) -> int {
+    const int i = G[0];
+    const int nb = (int)G.size();
+    const bool is_root = (i == st.root);
+    DT<T> Tt, Wt;
+    int rc = tensT(G, &Tt);
+    if (rc == CBC_OK) rc = tensW(G, &Wt);
+    if (rc != CBC_OK) return rc;
     // Z[(sigma', chi'_c...), (b_p, a_p)] = T W prod_c R^[c]; shared by S^[i] and R^[i]
     std::vector<DT<T>> envs;
     std::vector<int> lo{LG_SOUT};
     int64_t nz = st.phys[i];
     for (size_t j = 0; j < ch[i].size(); ++j) {
+      std::vector<const T*> ep;
+      for (int g : G) ep.push_back(R[ch[g][j]]);
       const int c = ch[i][j];
-      envs.push_back(env_on(R[c], chi_r[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j)));
+      DT<T> e;
+      rc = env_on(ep, chi_r[c], c, lg_x((int)j), lg_b((int)j), lg_a((int)j), &e);
+      if (rc != CBC_OK) return rc;
+      envs.push_back(e);
       lo.push_back(lg_x((int)j));
       nz *= chi_r[c];
     }
     lo.push_back(LG_BP);
     lo.push_back(LG_AP);
     DT<T> Z;
-    int rc = contract_node(i, envs, lo, false, &Z);
+    rc = contract_node(Tt, Wt, envs, lo, false, &Z);
     if (rc != CBC_OK) return rc;
     const int nba = (int)(op.bond[i] * st.bond[i]);
     const int m = (int)chi_down[i];
     const int nzi = (int)nz;
     const int cn = (m < nzi) ? m : nzi;  // square or tall: Q = I (exact, as on chains)
-    T* node = nullptr;
-    CK(pool_malloc(reinterpret_cast<void**>(&node),
-                       sizeof(T) * std::max<size_t>((size_t)cn * nzi, (size_t)m * nzi), s));
-    out->data[i] = node;
-    out->numel[i] = (int64_t)cn * nzi;
-    // S^[i] = L^[(p_i, i)] contracted with Z over (b_p, a_p)
-    if (i == st.root || m < nzi)
-      CK(tgemm<T>(pr, false, false, m, nzi, nba, Ldown[i], View::rowmajor(nba), false, Z.p,
-                  View::transposed(nba), false, node, View::rowmajor(nzi), s));
-    if (i == st.root) {
-      CK(normalize_inplace<T>(node, (int64_t)nzi, sc.log_out, sc.status, sc.scratch, s));
-      out->bond[i] = 1;
-      continue;
-    }
-    if (m < nzi) {
-      rc = lq_rows_inplace<T>(ar, pr, node, m, nzi, sc, s);
+    const bool formed = is_root || m < nzi;
+    const int64_t nbs = formed ? (int64_t)m * nzi : (int64_t)nzi * nzi;
+    const int64_t zbs = (int64_t)nzi * nba;
+    Prec pg = pr;
+    pg.nb = nb;
+    T* node = tmp.get<T>((size_t)nb * nbs);
+    CKA(node);
+    if (formed) {  // S^[i] = L^[(p_i, i)] contracted with Z over (b_p, a_p)
+      std::vector<const T*> ep;
+      for (int g : G) ep.push_back(Ldown[g]);
+      T* Ld = nullptr;
+      rc = gather<T>(tmp, ep, (int64_t)m * nba, s, &Ld);
       if (rc != CBC_OK) return rc;
-    } else {
-      CK(fill_identity<T>(node, nzi, s));
+      CK(tgemm<T>(pg, false, false, m, nzi, nba, Ld, View::rowmajor(nba, (int64_t)m * nba), false,
+                  Z.p, View::transposed(nba, zbs), false, node, View::rowmajor(nzi, nbs), s));
     }
-    // R^[i] = Q* Z over (sigma', chi'_c...)
-    T* Rn = ar.get<T>((size_t)cn * nba);
-    CKA(Rn);
-    CK(tgemm<T>(pr, false, false, cn, nba, nzi, node, View::rowmajor(nzi), true, Z.p,
-                View::rowmajor(nba), false, Rn, View::rowmajor(nba), s));
-    CK(normalize_inplace<T>(Rn, (int64_t)cn * nba, sc.log_out, sc.status, sc.scratch, s));
-    R[i] = Rn;
-    chi_r[i] = cn;
-    out->bond[i] = cn;
+    if (is_root) {
+      CK(normalize_inplace<T>(node, (int64_t)nzi, sc.log_out, sc.status, sc.scratch, s, nb, true));
+    } else {
+      if (m < nzi) {
+        rc = lq_rows_inplace<T>(tmp, pg, node, m, nzi, sc, s);
+        if (rc != CBC_OK) return rc;
+      } else {
+        CK(fill_identity<T>(node, nzi, s, nb));
+      }
+      // R^[i] = Q* Z over (sigma', chi'_c...)
+      const int64_t rbs = (int64_t)cn * nba;
+      T* Rn = ar.get<T>((size_t)nb * rbs);
+      CKA(Rn);
+      CK(tgemm<T>(pg, false, false, cn, nba, nzi, node, View::rowmajor(nzi, nbs), true, Z.p,
+                  View::rowmajor(nba, zbs), false, Rn, View::rowmajor(nba, rbs), s));
+      CK(normalize_inplace<T>(Rn, rbs, sc.log_out, sc.status, sc.scratch, s, nb, true));
+      for (int b = 0; b < nb; ++b) {
+        R[G[b]] = Rn + (size_t)b * rbs;
+        chi_r[G[b]] = cn;
+        out->bond[G[b]] = cn;
+      }
+    }
+    // the node tensors into the output's own allocations
+    const int64_t ne = is_root ? (int64_t)nzi : (int64_t)cn * nzi;
+    std::vector<void*> dst(nb);
+    for (int b = 0; b < nb; ++b) {
+      CK(pool_malloc(&dst[b], sizeof(T) * (size_t)ne, s));
+      out->data[G[b]] = dst[b];
+      out->numel[G[b]] = ne;
+    }
+    T** tab = tmp.get<T*>(nb);
+    CKA(tab);
+    CK(cudaMemcpyAsync(tab, dst.data(), sizeof(void*) * nb, cudaMemcpyHostToDevice, s));
+    CK(group_copy<T>(tab, node, nbs, ne, nb, false, s));
+    return CBC_OK;
+  };
+  for (int dd = maxd; dd >= 0; --dd) {
+    std::vector<int> nodes;
+    std::vector<std::vector<int64_t>> sig;
+    for (int i = 0; i < n; ++i) {
+      if (depth[i] != dd) continue;
+      std::vector<int64_t> g{st.phys[i], st.bond[i], op.bond[i], chi_down[i],
+                             (int64_t)ch[i].size()};
+      for (int c : ch[i]) {
+        g.push_back(chi_r[c]);
+        g.push_back(st.bond[c]);
+        g.push_back(op.bond[c]);
+      }
+      nodes.push_back(i);
+      sig.push_back(g);
+    }
+    std::vector<std::vector<int>> groups;
+    for (const auto& q : group_by(sig)) {
+      std::vector<int> G;
+      for (int x : q) G.push_back(nodes[x]);
+      groups.push_back(G);
+    }
+    int rc = run_groups(groups, step3);
+    if (rc != CBC_OK) return rc;
   }
   int h[2];
   double hl = 0.0;
