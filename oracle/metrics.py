@@ -118,3 +118,21 @@ def chain_applied_norm2(state, op) -> float:
         Z = np.einsum("cePAB,cPtC->etABC", Y, w.conj(), optimize=True)  # sum c, P
         E = np.einsum("etABC,etD->ABCD", Z, t.conj(), optimize=True)    # sum e, t
     return float(E.reshape(-1)[0].real)
+
+
+def chain_applied_overlap(state, op, out) -> complex:
+    """<phi| O |psi> for a chain: phi the network ``out`` (canonical layout, as a CBC result
+    without its scalar), contracted from the left with an environment E[x, b, a] over the
+    open bonds of conj(phi), O and psi (Eqs. (ttns), (ttno))."""
+    L = len(state)
+    E = np.ones((1, 1, 1), dtype=np.complex128)
+    for i in range(L):
+        t = np.asarray(state[i], dtype=np.complex128)
+        w = np.asarray(op[i], dtype=np.complex128)
+        q = np.asarray(out[i], dtype=np.complex128)
+        if i == L - 1:
+            t, w, q = t[..., None], w[..., None], q[..., None]
+        X = np.einsum("xba,asA->xbsA", E, t, optimize=True)      # sum a
+        Y = np.einsum("xbsA,bPsB->xPAB", X, w, optimize=True)     # sum b, s
+        E = np.einsum("xPAB,xPX->XBA", Y, q.conj(), optimize=True)  # sum x, P
+    return complex(E.reshape(-1)[0])

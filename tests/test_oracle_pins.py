@@ -98,3 +98,18 @@ def test_chain_applied_norm_matches_brute_force():
         ex = brute.apply_dense(p.state.parent, p.state.tensors, p.op.tensors)
         got = metrics.chain_applied_norm2(p.state.tensors, p.op.tensors)
         assert abs(got - np.linalg.norm(ex) ** 2) <= 1e-13 * np.linalg.norm(ex) ** 2
+
+
+def test_chain_applied_overlap_matches_brute_force():
+    """<phi|O|psi> of two chains equals the dense inner product (the CBC output of the
+    oracle as phi, so the value is also ||psi'||^2 by the projection identity)."""
+    from oracle import brute, metrics
+    from oracle import cbc as ocbc
+    p = make_problem(2, L=7, chi=8, D=3, max_bond=5, dtype=np.complex128, seed=3)
+    r = ocbc.cbc(p.state.parent, p.state.tensors, p.op.tensors, p.max_bond)
+    ex = brute.apply_dense(p.state.parent, p.state.tensors, p.op.tensors)
+    phi = brute.dense_state(p.state.parent, r.tensors)
+    got = metrics.chain_applied_overlap(p.state.tensors, p.op.tensors, r.tensors)
+    want = np.vdot(phi, ex)
+    assert abs(got - want) <= 1e-13 * abs(want)
+    assert abs(got.real - np.linalg.norm(phi) ** 2) <= 1e-12 * abs(want)
