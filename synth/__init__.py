@@ -13,5 +13,6 @@ from .networks import (  # noqa: F401
     clamp_bonds,
     make_problem,
     random_network,
+    sketch_matrices,
     CONFIGS,
 )

@@ -322,3 +322,19 @@ def make_batch(n: int = 256, seed0: int = 0, scale: Optional[int] = None):
             L = max(4, L // scale)
         probs.append(make_problem(4, seed=j, L=L, chi=chi, D=D, max_bond=chi))
     return probs
+
+
+def sketch_matrices(phys, s: int, seed: int = 0, cplx: bool = False) -> List[np.ndarray]:
+    """The random matrices of the randomised comparator (SRC, Sec. III C): one ``d_i x s``
+    Gaussian matrix per site, standard normal entries (complex ``(x+iy)/sqrt(2)`` when
+    ``cplx``), float64 / complex128, drawn from ``default_rng([seed, 3])`` in site order."""
+    rng = np.random.default_rng([seed, 3])
+    out = []
+    for d in phys:
+        shape = (int(d), int(s))
+        if cplx:
+            x = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(2.0)
+        else:
+            x = rng.standard_normal(shape)
+        out.append(np.ascontiguousarray(x))
+    return out
