@@ -3,8 +3,8 @@
 
 Workload: MPO applied to an MPS and compressed by CBC, L=64 sites, d=2, MPS bond 128,
 MPO bond 16, cap 128, complex64 Gaussian entries with unit Frobenius norm per tensor.
-A step applies B independent instances (default 32; rank r uses seeds r*B .. r*B+B-1)
-through cbc_apply_batched, which runs same-shape instances as one lockstep group; every
+A step applies B independent instances (default 128; rank r uses seeds r*B .. r*B+B-1)
+through cbc_apply_batched, which runs them as one lockstep group of 128; every
 application is a full forward sweep with compressions and backward sweep with
 CholeskyQR2, on inputs resident in HBM.  Several GPUs run independent replicas (no
 collective on the data path); the step time is the maximum over ranks.
@@ -53,7 +53,10 @@ WORKLOADS = {
                            "Gaussian entries", L=100, d=4, chi=1024, D=32, max_bond=1024,
                   input_dtype="complex64"),
 }
-DEFAULT_B = {"mpo_mps": 32, "tree": 8, "serving": 256, "large": 1, "paper": 1}
+DEFAULT_B = {"mpo_mps": 128, "tree": 8, "serving": 256, "large": 1, "paper": 1}
+# instances per lockstep group (cbc_options.max_group) when --group is not given: the whole
+# headline step in one group (larger groups fill more SMs in the per-matrix kernels)
+DEFAULT_GROUP = {"mpo_mps": 128}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64, nominal: the fallback when the DGEMM probe fails
 # DRAM bytes per launch of a class's dominant kernel, read from an ncu capture of this
 # workload; each entry names the summary under profiles/ it comes from.  A class whose
@@ -215,7 +218,9 @@ def blas_threads() -> int:
 
 def run_sweep(args, local):
     """Error against runtime of one application of the paper's benchmark MPS/MPO (Sec. IV A)
-    for max_bond = 2, 4, ..., 40, in both precisions.  The error is ||O psi - psi'|| /
+    for max_bond = 2, 4, ..., 40, in both precisions, for CBC and for the two comparison
+    methods of Sec. III C built here (Zip-Up with the same cap, SRC with sketch width
+    s = max_bond and seeded Gaussian random matrices).  The error is ||O psi - psi'|| /
     ||O psi|| from ||O psi||^2 (one exact FP64 sandwich contraction, the oracle's
     chain_applied_norm2), ||psi'||^2 and the overlap <psi'|O psi> (chain_applied_overlap);
     its floor is ~1e-8 (FP64 cancellation in the sum of the three)."""
@@ -224,7 +229,7 @@ def run_sweep(args, local):
 
     from oracle import metrics
     from paper_2601_19650_gb300 import _cbc, build as _build
-    from synth import make_problem
+    from synth import make_problem, sketch_matrices
 
     _build.build()
     torch.cuda.set_device(local)
@@ -236,43 +241,64 @@ def run_sweep(args, local):
     hs = _cbc.create_from_host(st.parent, st.phys, st.bond, st.tensors, "state")
     ho = _cbc.create_from_host(op.parent, op.phys, op.bond, op.tensors, "op")
     shape = _cbc.output_shape_fn(st.parent, st.phys)
+    methods = [m for m in args.sweep_methods.split(",") if m]
+
+    def apply(method, opt, mb, om):
+        if method == "cbc":
+            return _cbc.cbc_apply(hs, ho, mb, 0.0, opt)
+        if method == "zipup":
+            return _cbc.zipup_apply(hs, ho, mb, 0.0, opt)
+        return _cbc.src_apply(hs, ho, mb, om, opt)
+
     rows = []
     for mb in range(2, 41, 2):
         row = {"max_bond": mb}
-        for name, prec in (("mixed", _cbc.CBC_PREC_MIXED), ("fp64", _cbc.CBC_PREC_FP64)):
-            opt = _cbc.make_options(prec)
-            _cbc.ttn_destroy(_cbc.cbc_apply(hs, ho, mb, 0.0, opt))  # warm-up
-            times = []
-            out = None
-            for _ in range(3):
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                if out is not None:
-                    _cbc.ttn_destroy(out)
-                out = _cbc.cbc_apply(hs, ho, mb, 0.0, opt)
-                e1.record()
-                e1.synchronize()
-                times.append(e0.elapsed_time(e1))
-            tens, bonds, log_norm = _cbc.fetch_network(out, shape, True)
-            _cbc.ttn_destroy(out)
-            # ||O psi - psi'||^2 = ||O psi||^2 + ||psi'||^2 - 2 Re <psi'|O psi>, relative to
-            # ||O psi||^2 (the overlap by an FP64 sandwich: no assumption that psi' is an
-            # exact projection)
-            sc2 = float(np.exp(2.0 * log_norm))
-            out2 = sc2 * float(np.linalg.norm(tens[0].reshape(-1)) ** 2)
-            ov = float(np.exp(log_norm)) * metrics.chain_applied_overlap(st.tensors, op.tensors,
-                                                                        tens).real
-            err = float(np.sqrt(max(0.0, 1.0 + out2 / n2 - 2.0 * ov / n2)))
-            row[name] = {"ms": statistics.median(times), "rel_err": err,
-                         "max_out_bond": int(max(bonds))}
+        om = sketch_matrices(st.phys, mb, seed=0, cplx=True)
+        for method in methods:
+            for name, prec in (("mixed", _cbc.CBC_PREC_MIXED), ("fp64", _cbc.CBC_PREC_FP64)):
+                key = name if method == "cbc" else f"{method}_{name}"
+                opt = _cbc.make_options(prec)
+                try:
+                    _cbc.ttn_destroy(apply(method, opt, mb, om))  # warm-up
+                    times = []
+                    out = None
+                    for _ in range(3):
+                        torch.cuda.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        if out is not None:
+                            _cbc.ttn_destroy(out)
+                        out = apply(method, opt, mb, om)
+                        e1.record()
+                        e1.synchronize()
+                        times.append(e0.elapsed_time(e1))
+                except _cbc.CBCError as exc:
+                    row[key] = {"error": str(exc)[:160]}
+                    continue
+                tens, bonds, log_norm = _cbc.fetch_network(out, shape, True)
+                _cbc.ttn_destroy(out)
+                # ||O psi - psi'||^2 = ||O psi||^2 + ||psi'||^2 - 2 Re <psi'|O psi>, relative
+                # to ||O psi||^2 (the overlap by an FP64 sandwich: no assumption that psi'
+                # is an exact projection)
+                # ||psi'|| by the oracle's QR sweep (the mixed path's isometries are exact
+                # only to its precision, so the root tensor's norm alone is not ||psi'||)
+                sc2 = float(np.exp(2.0 * log_norm))
+                out2 = sc2 * metrics.tree_norm(st.parent, tens) ** 2
+                ov = float(np.exp(log_norm)) * metrics.chain_applied_overlap(
+                    st.tensors, op.tensors, tens).real
+                err = float(np.sqrt(max(0.0, 1.0 + out2 / n2 - 2.0 * ov / n2)))
+                row[key] = {"ms": statistics.median(times), "rel_err": err,
+                            "max_out_bond": int(max(bonds))}
         rows.append(row)
     _cbc.ttn_destroy(hs)
     _cbc.ttno_destroy(ho)
-    line = {"metric": "CBC relative error ||O psi - psi'|| / ||O psi|| against runtime, paper "
-                      "benchmark (Sec. IV A)", "unit": "ms per application",
+    line = {"metric": "relative error ||O psi - psi'|| / ||O psi|| against runtime, paper "
+                      "benchmark (Sec. IV A): CBC and the Sec. III C comparators",
+            "unit": "ms per application",
             "n_gpus": 1, "data": "synthetic", "dtype": "bf16-slices+f64 | f64",
-            "config": dict(WORKLOADS["paper"], seed=0),
+            "config": dict(WORKLOADS["paper"], seed=0, methods=methods,
+                           src_sketch="s = max_bond, Gaussian (x+iy)/sqrt(2), seed 0"),
             "norm_note": f"||O psi||^2 by an exact FP64 sandwich contraction on the host "
                          f"({t_norm:.1f} s), <psi'|O psi> likewise per result; errors below "
                          f"~1e-8 sit at FP64 cancellation",
@@ -319,8 +345,8 @@ def main():
     ap.add_argument("--concurrency", type=int, default=0,
                     help="independent applications per step (seeds rank*B .. rank*B+B-1), "
                          "run by cbc_apply_batched: same-shape instances go in lockstep "
-                         "groups of up to 32 (one launch per step per group); default per "
-                         "workload: mpo_mps 32, tree 8, serving 256, large 1")
+                         "groups (--group; one launch per step per group); default per "
+                         "workload: mpo_mps 128, tree 8, serving 256, large 1")
     ap.add_argument("--workload", default="mpo_mps", choices=sorted(WORKLOADS),
                     help="mpo_mps (the headline), tree, serving, large")
     ap.add_argument("--sites", type=int, default=0,
@@ -330,6 +356,14 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="error-vs-runtime sweep of the paper's benchmark (max_bond 2..40) "
                          "instead of the throughput step; prints one line of rows")
+    ap.add_argument("--sweep-methods", default="cbc,zipup,src",
+                    help="methods of --sweep (comma separated: cbc, zipup, src)")
+    ap.add_argument("--tol", type=float, default=0.0,
+                    help="truncation tolerance of every compression besides max_bond (Sec. V; "
+                         "the large workload's second run uses 1e-8)")
+    ap.add_argument("--group", type=int, default=0,
+                    help="most instances per lockstep group (0: the workload's default, "
+                         "128 for mpo_mps, else the library's 32)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="timed steps of the FP64 arm (after one warm-up step)")
     args = ap.parse_args()
@@ -354,6 +388,8 @@ def main():
         dist_mod.init_process_group("nccl")
         dist = dist_mod
     B = args.concurrency if args.concurrency > 0 else DEFAULT_B[args.workload]
+    if args.group <= 0:
+        args.group = DEFAULT_GROUP.get(args.workload, 0)
     streams = [torch.cuda.Stream() for _ in range(B)]
     stream = streams[0]
     sptr = stream.cuda_stream
@@ -361,6 +397,8 @@ def main():
     # precision of the headline number: mixed when built, else fp64
     prec_name = args.precision
     probs = make_workloads(args.workload, rank, B, args.sites)
+    for p in probs:
+        p.tol = args.tol
     prob = probs[0]
     st, op = prob.state, prob.op
     hs_list, ho_list = [], []
@@ -376,10 +414,10 @@ def main():
     hs, ho = hs_list[0], ho_list[0]
 
     def apply_once(prec):
-        opt = _cbc.make_options(prec)
+        opt = _cbc.make_options(prec, max_group=args.group)
         if B == 1:
-            return [_cbc.cbc_apply(hs, ho, prob.max_bond, 0.0, opt)]
-        return _cbc.cbc_apply_batched(hs_list, ho_list, [p.max_bond for p in probs], [0.0] * B,
+            return [_cbc.cbc_apply(hs, ho, prob.max_bond, prob.tol, opt)]
+        return _cbc.cbc_apply_batched(hs_list, ho_list, [p.max_bond for p in probs], [p.tol for p in probs],
                                       opt)
 
     def destroy(outs):
@@ -427,10 +465,13 @@ def main():
                 e0.record(stream)
             for sm in streams[1:]:
                 sm.wait_event(e0)
+            # an NVTX range per timed step: profilers can select exactly one step's launches
+            torch.cuda.nvtx.range_push("timed_step")
             if single:
-                outs = [_cbc.cbc_apply(hs, ho, prob.max_bond, 0.0, _cbc.make_options(prec_arm))]
+                outs = [_cbc.cbc_apply(hs, ho, prob.max_bond, prob.tol, _cbc.make_options(prec_arm))]
             else:
                 outs = apply_once(prec_arm)
+            torch.cuda.nvtx.range_pop()
             for sm in streams[1:]:
                 ev = torch.cuda.Event()
                 ev.record(sm)
@@ -512,9 +553,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if prec_name == "fp64" else "bf16-slices+f64",
             "data": "synthetic",
-            "config": dict(WORKLOADS[args.workload], precision=prec_name, concurrent_applications=B,
-                           batching="cbc_apply_batched: lockstep groups of <= 32 same-shape "
-                                    "instances" if B > 1 else "single cbc_apply",
+            "config": dict(WORKLOADS[args.workload], precision=prec_name, tol=args.tol, concurrent_applications=B,
+                           batching=(f"cbc_apply_batched: lockstep groups of <= "
+                                     f"{args.group or 32} same-shape instances")
+                           if B > 1 else "single cbc_apply",
                            parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                            l2="flushed between steps (256 MB write, untimed)"),
             "tflops": flops_per_app / B * value / 1e12,
@@ -606,11 +648,11 @@ def main():
                                         sm.cuda_stream) for p, (pa, _), sm in zip(probs, pins, streams)]
             hb = [_cbc.create_from_host(p.op.parent, p.op.phys, p.op.bond, pb, "op", sm.cuda_stream)
                   for p, (_, pb), sm in zip(probs, pins, streams)]
-            opt = _cbc.make_options(prec)
+            opt = _cbc.make_options(prec, max_group=args.group)
             if B == 1:
-                outs = [_cbc.cbc_apply(ha[0], hb[0], prob.max_bond, 0.0, opt)]
+                outs = [_cbc.cbc_apply(ha[0], hb[0], prob.max_bond, prob.tol, opt)]
             else:
-                outs = _cbc.cbc_apply_batched(ha, hb, [p.max_bond for p in probs], [0.0] * B, opt)
+                outs = _cbc.cbc_apply_batched(ha, hb, [p.max_bond for p in probs], [p.tol for p in probs], opt)
             d2h = 0
             for o, shp, cx in zip(outs, shapes, cplxs):
                 tens, bonds, _ = _cbc.fetch_network(o, shp, cx)

@@ -81,7 +81,8 @@ typedef struct cbc_options {
   int precision;     /* enum cbc_prec; default CBC_PREC_FP64                         */
   int slices_fwd;    /* mixed: bf16 slices per operand in the first sweep(s) (0 = 5) */
   int slices_bwd;    /* mixed: bf16 slices per operand in the last sweep (0 = 4)     */
-  int reserved_i;
+  int max_group;     /* cbc_apply_batched: most instances per lockstep group (0 = 32);
+                        larger groups fill more SMs per launch and hold more memory    */
   double eps_rank;   /* singular values s_j <= eps_rank * s_0 are dropped (<= 0: the
                         default, 1e-12 for CBC_PREC_FP64 as in the FP64 reference, 1e-9
                         for CBC_PREC_MIXED, whose products resolve s only to ~3e-11 s_0) */
@@ -136,7 +137,7 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
 /* Apply n operators to n states (independent instances of any sizes and topologies)
  * and compress each; the results equal n calls of cbc_apply.  Tensor-train instances
  * with identical shapes (sites, physical and bond dimensions, real/complex), max_bond
- * and tol form groups of up to 32 that run in lockstep: every step of Sec. III A is one
+ * and tol form groups of up to opt->max_group (default 32) that run in lockstep: every step of Sec. III A is one
  * launch for the whole group, on the stream of the group's first state (the group waits
  * for the other members' streams first and has finished when the call returns).  A
  * group whose members choose different ranks at some cut is rerun member by member.
@@ -150,6 +151,42 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
  * other instances still complete.                                                   */
 int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64_t* max_bond,
                       const double* tol, const cbc_options* opt, int workers, ttn_t* outs);
+
+/* Zip-Up (Sec. III C, "Other Compression Methods"): a comparison method that applies op
+ * to state and compresses in a single sweep over the sites, truncating each bond as soon
+ * as the site is contracted, with only the already compressed part in view.  Tensor
+ * trains only (parent[i] = i - 1).  The sweep runs from the last site to site 0: at site
+ * i the carried tensor (bond to site i+1 already compressed) is contracted with T^[i]
+ * and W^[i] into Z[(alpha_{i-1} beta_{i-1}), (sigma'_i chi_i)]; the new tensor is an
+ * orthonormal row basis of Z's dominant right singular subspace (rank rule of cbc_apply
+ * on Z's singular values, max_bond and tol as there) and the carry is Z projected onto
+ * it.  The state is used as given (no canonical form first).  Output layout, ownership,
+ * precision options, stream use and errors as cbc_apply; CBC_ERR_UNSUPPORTED for a tree.
+ * ttn_get_info's discarded weights are those of Z at each edge.                      */
+int zipup_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
+                const cbc_options* opt, ttn_t* out);
+
+/* Successive randomised compression, SRC (Sec. III C): a comparison method whose first
+ * sweep contracts the network with one random matrix per site (d_i x s, joined across
+ * the sites by the Khatri-Rao product: column j of every site's matrix belongs to the
+ * same sketch vector) instead of compressing by an SVD; the second sweep is CBC's
+ * (Eqs. (right_sweep_init_contr) .. (tt_cbc_final_contraction)) with the sketch in place
+ * of the environments.  On the edge (i-1, i) the LQ takes the first
+ * r = min(s, prod_{k<i} d_k, alpha_{i-1} beta_{i-1}) sketch rows (the generic rank of the
+ * sketched block); when r is at least d_i chi_i the new tensor is the identity.  The
+ * output bonds are therefore at most s; there is no tolerance rule.  Tensor trains only.
+ *   sketch_size      s >= 1
+ *   omega            [n_nodes] host array of pointers; omega[i] (i < n_nodes - 1) is the
+ *                    d_i x s row-major random matrix of site i (the last site's entry is
+ *                    not read and may be NULL), host or device memory per
+ *                    omega_on_device; the caller draws them (e.g. standard Gaussian)
+ *   omega_dtype      CBC_F32/CBC_F64 for real networks, CBC_C64/CBC_C128 for complex ones
+ * The matrices are copied (FP64 storage) before the sweeps and freed on return; the call
+ * synchronises the network's stream.  Output layout, ownership, options, errors as
+ * cbc_apply (CBC_ERR_NOT_POSITIVE_DEFINITE when a sketched block is rank deficient, as for
+ * a degenerate operator); CBC_ERR_INVALID_ARG for a bad sketch argument.             */
+int src_apply(ttn_t state, ttno_t op, int64_t sketch_size, const void* const* omega,
+              int omega_dtype, int omega_on_device, const cbc_options* opt, ttn_t* out);
 
 /* Information about a TTNS (synchronises its stream).
  *   n_nodes_out     may be NULL

@@ -35,7 +35,7 @@ class CBCError(RuntimeError):
 
 class cbc_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("slices_fwd", ctypes.c_int),
-                ("slices_bwd", ctypes.c_int), ("reserved_i", ctypes.c_int),
+                ("slices_bwd", ctypes.c_int), ("max_group", ctypes.c_int),
                 ("eps_rank", ctypes.c_double), ("reserved_d", ctypes.c_double * 3)]
 
 
@@ -65,6 +65,9 @@ def lib():
         L.ttn_create.argtypes = create_args
         L.ttno_create.argtypes = create_args
         L.cbc_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
+        L.zipup_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
+        L.src_apply.argtypes = [vp, vp, i64, P(vp), ctypes.c_int, ctypes.c_int, P(cbc_options),
+                                P(vp)]
         L.ttn_get_info.argtypes = [vp, P(i32), P(i64), P(dbl), P(dbl)]
         L.ttn_get_node.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int]
         L.ttn_get_network.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
@@ -98,7 +101,7 @@ def lib():
         L.cbc_last_error.restype = ctypes.c_char_p
         L.cbc_last_error.argtypes = []
         for f in ("ttn_create", "ttno_create", "cbc_apply", "ttn_get_info", "ttn_get_node",
-                  "ttn_get_network", "ttn_destroy", "ttno_destroy"):
+                  "ttn_get_network", "ttn_destroy", "ttno_destroy", "zipup_apply", "src_apply"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -151,18 +154,38 @@ def ttno_create(parent, phys, bond, dtype: int, ptrs, on_device: bool, stream=No
 
 
 def make_options(precision: int = CBC_PREC_FP64, eps_rank: float = 0.0, slices_fwd: int = 0,
-                 slices_bwd: int = 0) -> cbc_options:
+                 slices_bwd: int = 0, max_group: int = 0) -> cbc_options:
     o = cbc_options()
     o.precision = precision
     o.eps_rank = eps_rank
     o.slices_fwd = slices_fwd
     o.slices_bwd = slices_bwd
+    o.max_group = max_group
     return o
 
 
 def cbc_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options] = None):
     out = ctypes.c_void_p()
     _check(lib().cbc_apply(state, op, int(max_bond), float(tol),
+                           ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
+    return out
+
+
+def zipup_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options] = None):
+    """Zip-Up comparison method (tensor trains); same arguments and output as cbc_apply."""
+    out = ctypes.c_void_p()
+    _check(lib().zipup_apply(state, op, int(max_bond), float(tol),
+                             ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
+    return out
+
+
+def src_apply(state, op, sketch_size: int, omega, opt: Optional[cbc_options] = None):
+    """SRC comparison method (tensor trains) with host numpy random matrices omega[i]
+    (d_i x sketch_size; real for real networks, complex for complex ones)."""
+    arrs = [np.ascontiguousarray(o) for o in omega]
+    ptrs = (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
+    out = ctypes.c_void_p()
+    _check(lib().src_apply(state, op, int(sketch_size), ptrs, _DT_OF[arrs[0].dtype], 0,
                            ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
     return out
 

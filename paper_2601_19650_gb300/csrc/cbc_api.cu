@@ -360,6 +360,9 @@ static int parse_options(const cbc_options* opt, Options* o) {
     o->precision = opt->precision;
     if (opt->slices_fwd > 0) o->slices_fwd = opt->slices_fwd;
     if (opt->slices_bwd > 0) o->slices_bwd = opt->slices_bwd;
+    if (opt->max_group < 0 || opt->max_group > 1024)
+      return fail(CBC_ERR_INVALID_ARG, "cbc_apply: max_group %d outside [0, 1024]", opt->max_group);
+    if (opt->max_group > 0) o->max_group = opt->max_group;
   }
   if (o->precision != CBC_PREC_FP64 && o->precision != CBC_PREC_MIXED)
     return fail(CBC_ERR_INVALID_ARG, "cbc_apply: bad precision %d", o->precision);
@@ -399,6 +402,110 @@ static int apply_one(ttn_t state, ttno_t op, int64_t max_bond, double tol,
   return CBC_OK;
 }
 
+// ---- comparison methods of Sec. III C on tensor trains --------------------------------
+static int check_chain_pair(ttn_t state, ttno_t op, const char* who) {
+  if (!state || !op) return fail(CBC_ERR_INVALID_ARG, "%s: NULL network", who);
+  if (state->kind != 0 || op->kind != 1) return fail(CBC_ERR_INVALID_ARG, "%s: wrong handle kinds", who);
+  if (state->n != op->n || state->parent != op->parent || state->phys != op->phys)
+    return fail(CBC_ERR_TOPOLOGY_MISMATCH, "%s: state and operator trees differ", who);
+  for (int i = 0; i < state->n; ++i)
+    if (state->parent[i] != i - 1)
+      return fail(CBC_ERR_UNSUPPORTED, "%s: only tensor trains (parent[i] = i - 1) are supported", who);
+  return CBC_OK;
+}
+
+static int run_method(ttn_t state, ttno_t op, int64_t max_bond, double tol, Options& o,
+                      ttn_t* out) {
+  auto* res = new cbc_ttn_s();
+  int rc = run_cbc(*state, *op, max_bond, tol, o, res);
+  if (rc != CBC_OK) {
+    delete res;
+    return rc;
+  }
+  *out = res;
+  return CBC_OK;
+}
+
+int zipup_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_options* opt,
+                ttn_t* out) {
+  if (!out) return fail(CBC_ERR_INVALID_ARG, "zipup_apply: out is NULL");
+  *out = nullptr;
+  int rc = check_chain_pair(state, op, "zipup_apply");
+  if (rc != CBC_OK) return rc;
+  if (!std::isfinite(tol)) return fail(CBC_ERR_INVALID_ARG, "zipup_apply: tol is not finite");
+  Options o;
+  rc = parse_options(opt, &o);
+  if (rc != CBC_OK) return rc;
+  o.method = kMethodZipUp;
+  return run_method(state, op, max_bond, tol, o, out);
+}
+
+int src_apply(ttn_t state, ttno_t op, int64_t sketch_size, const void* const* omega,
+              int omega_dtype, int omega_on_device, const cbc_options* opt, ttn_t* out) {
+  if (!out) return fail(CBC_ERR_INVALID_ARG, "src_apply: out is NULL");
+  *out = nullptr;
+  int rc = check_chain_pair(state, op, "src_apply");
+  if (rc != CBC_OK) return rc;
+  if (sketch_size < 1 || sketch_size > (1 << 20))
+    return fail(CBC_ERR_INVALID_ARG, "src_apply: sketch_size %lld outside [1, 2^20]",
+                (long long)sketch_size);
+  if (!omega || !valid_dtype(omega_dtype))
+    return fail(CBC_ERR_INVALID_ARG, "src_apply: omega is NULL or its dtype is invalid");
+  const bool ocplx = (omega_dtype == CBC_C64 || omega_dtype == CBC_C128);
+  if (ocplx != state->cplx)
+    return fail(CBC_ERR_INVALID_ARG,
+                "src_apply: omega must be real for real networks and complex for complex ones");
+  const int L = state->n;
+  for (int i = 0; i + 1 < L; ++i)
+    if (!omega[i]) return fail(CBC_ERR_INVALID_ARG, "src_apply: omega[%d] is NULL", i);
+  Options o;
+  rc = parse_options(opt, &o);
+  if (rc != CBC_OK) return rc;
+  // the random matrices in FP64 storage of the network's type, one allocation
+  cudaStream_t s = state->stream;
+  const size_t es = state->elem_bytes(), hs = dtype_bytes(omega_dtype);
+  std::vector<int64_t> off(L + 1, 0);
+  for (int i = 0; i < L; ++i)
+    off[i + 1] = off[i] + ((i + 1 < L) ? (state->phys[i] * sketch_size + 31) / 32 * 32 : 0);
+  void* block = nullptr;
+  void* flag = nullptr;
+  cudaError_t e = pool_malloc(&block, std::max<int64_t>(off[L], 1) * es, s);
+  if (e != cudaSuccess) return cuda_fail(e, "src_apply: device allocation");
+  std::vector<void*> mats(L, nullptr);
+  for (int i = 0; i + 1 < L; ++i) mats[i] = static_cast<char*>(block) + off[i] * es;
+  e = pool_malloc(&flag, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  void* staging = nullptr;
+  if (e == cudaSuccess && !omega_on_device) {
+    e = pool_malloc(&staging, std::max<int64_t>(off[L], 1) * hs, s);
+    for (int i = 0; i + 1 < L && e == cudaSuccess; ++i)
+      e = cudaMemcpyAsync(static_cast<char*>(staging) + off[i] * hs, omega[i],
+                          state->phys[i] * sketch_size * hs, cudaMemcpyHostToDevice, s);
+  }
+  for (int i = 0; i + 1 < L && e == cudaSuccess; ++i)
+    e = widen_to_f64(omega_on_device ? omega[i] : static_cast<char*>(staging) + off[i] * hs,
+                     omega_dtype, mats[i], state->phys[i] * sketch_size, s,
+                     static_cast<int*>(flag));
+  int hflag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (staging) cudaFreeAsync(staging, s);
+  if (flag) cudaFreeAsync(flag, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || hflag) {
+    cudaFreeAsync(block, s);
+    cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "src_apply: upload of omega");
+    return fail(CBC_ERR_NUMERICAL, "src_apply: omega holds NaN or Inf");
+  }
+  o.method = kMethodSRC;
+  o.sketch = (int)sketch_size;
+  o.sketch_mats = mats.data();
+  rc = run_method(state, op, 0, 0.0, o, out);
+  cudaFreeAsync(block, s);
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
 int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64_t* max_bond,
                       const double* tol, const cbc_options* opt, int workers, ttn_t* outs) {
   if (n < 0 || (n > 0 && (!states || !ops || !outs)))
@@ -407,7 +514,11 @@ int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64
   if (n == 0) return CBC_OK;
   // groups: chains with identical shapes, max_bond and tol (at most kMaxGroup each) run
   // in lockstep, one launch per step for the whole group; the rest one by one
-  constexpr int kMaxGroup = 32;
+  int kMaxGroup = 32;
+  {
+    Options o;
+    if (parse_options(opt, &o) == CBC_OK) kMaxGroup = o.max_group;
+  }
   std::vector<std::vector<int>> tasks;
   {
     std::vector<int> open_task;  // index into tasks of the open group per signature

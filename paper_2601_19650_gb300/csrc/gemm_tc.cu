@@ -37,7 +37,9 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "kernels.cuh"
 #include "planner.h"
@@ -48,8 +50,10 @@ namespace tc {
 constexpr int BM = 128;          // rows of the output tile (TMEM lanes)
 constexpr int KA = 64;           // bf16 elements per K atom (one 128-byte swizzle row)
 constexpr int NSTAGE = 2;
-// warps: 0 TMA, 1 MMA, then 4 epilogue warps per 32 accumulator columns
-__host__ __device__ constexpr int epi_warps(int BN) { return (BN / 32) * 4; }
+// warps: 0 TMA, 1 MMA, then 4 epilogue warps (one per TMEM lane quarter) per group of 32
+// accumulator columns, or of 16 when BN is not a multiple of 32 (BN = 48)
+__host__ __device__ constexpr int epi_cols(int BN) { return (BN % 32 == 0) ? 32 : 16; }
+__host__ __device__ constexpr int epi_warps(int BN) { return (BN / epi_cols(BN)) * 4; }
 __host__ __device__ constexpr int nthreads(int BN) { return 64 + 32 * epi_warps(BN); }
 constexpr long long WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
@@ -153,6 +157,24 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+template <int CW>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[CW]) {
+  if constexpr (CW == 32)
+    tmem_ld32(taddr, r);
+  else
+    tmem_ld16(taddr, r);
 }
 
 struct TcArgs {
@@ -348,7 +370,8 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
   } else {
     // ---------------- epilogue (warps 2 ..) ----------------
     // warp w may read TMEM lanes 32*(w%4) .. +31; warps 2-5 take accumulator columns
-    // 0-31, warps 6-9 columns 32-63 (BN = 64)
+    // 0 .. CW-1, warps 6-9 the next CW columns, and so on
+    constexpr int CW = epi_cols(BN);
     const int ew = warp - 2;
     const int quarter = warp & 3;
     const int colg = ew >> 2;
@@ -357,9 +380,9 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
     for (int t = blockIdx.x; t < a.total_tiles && run; t += gridDim.x) {
       const Tile q = tile_of(t);
       const int row = q.m0 + quarter * 32 + lane;
-      long long acc[32];
+      long long acc[CW];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i] = 0;
+      for (int i = 0; i < CW; ++i) acc[i] = 0;
       for (int c = 0; c < q.n_chunks; ++c, ++cg) {
         const int buf = cg & 1, use = cg >> 1;
         if (!mbar_wait(tfull + buf, use & 1, abort_flag, a.status)) {
@@ -370,12 +393,12 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
 #pragma unroll
         for (int g = 0; g < S; ++g) {
           const int shift = 8 * (S - 1 - g);
-          uint32_t r[32];
-          tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) +
-                        (uint32_t)((buf * S + g) * BN + colg * 32),
-                    r);
+          uint32_t r[CW];
+          tmem_ld<CW>(tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                          (uint32_t)((buf * S + g) * BN + colg * CW),
+                      r);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < CW; ++i) {
             long long qv = (long long)__float2int_rn(__uint_as_float(r[i]));
             acc[i] += qv << shift;
           }
@@ -386,13 +409,13 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
       }
       if (!run) break;
       if (q.n_chunks > 0) {
-        // the 32 columns of this warp are shared by its lanes (the lanes are rows): lane i
+        // the CW columns of this warp are shared by its lanes (the lanes are rows): lane i
         // finds column i's offset and exponent once, the loop takes them by shuffle
         const int* expB = a.expB + (int64_t)q.prob * a.ebsB;
         char* Cp = a.C + (int64_t)q.prob * a.vc.bs * (a.cplx ? 16 : 8);
-        const int mycol = q.n0 + colg * 32 + lane;
+        const int mycol = q.n0 + colg * CW + lane;
         const int myn = a.cplx ? (mycol >> 1) : mycol;
-        const bool myok = mycol < a.N2;
+        const bool myok = lane < CW && mycol < a.N2;
         const long long mycoff = myok ? (long long)a.vc.coff(myn) : 0;
         const int myexp = myok ? expB[myn] : 0;
         const bool rowok = row < a.M;
@@ -400,10 +423,10 @@ __global__ void __launch_bounds__(nthreads(BN), 1)
         const int bias = -14 - 8 * (S - 1);
         const int64_t ro = rowok ? a.vc.roff(row) : 0;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < CW; ++i) {
           const long long co = __shfl_sync(0xffffffffu, mycoff, i);
           const int eb = __shfl_sync(0xffffffffu, myexp, i);
-          const int col = q.n0 + colg * 32 + i;
+          const int col = q.n0 + colg * CW + i;
           if (rowok && col < a.N2) {
             const double v = i64_ldexp(acc[i], ea + eb + bias);
             double* dst;
@@ -658,16 +681,14 @@ bool make_map(CUtensorMap* m, void* base, int K2_pad, int rows_pad, int S, int b
   return r == CUDA_SUCCESS;
 }
 
-int bn_for(int S) { return S <= 4 ? 64 : 32; }
 int atoms_per_chunk_for(int S) { return std::max(1, (1024 / S) / KA); }
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct Geo {
-  int Mp, N2, N2p, K2, K2p, BN;
+  int Mp, N2, N2p, K2, K2p;
 };
 Geo geometry(int M, int N, int K, bool cplx, int S) {
   Geo g;
-  g.BN = bn_for(S);
   g.Mp = (M + BM - 1) / BM * BM;
   g.N2 = cplx ? 2 * N : N;
   // a multiple of 64 so that complex B^T planes hold whole 32-row slicing tiles
@@ -677,27 +698,68 @@ Geo geometry(int M, int N, int K, bool cplx, int S) {
   return g;
 }
 
-template <int S>
-size_t smem_bytes() {
-  constexpr int BN = S <= 4 ? 64 : 32;
+// Tile widths a slice count can use: two sets of S accumulators of BN columns fit the
+// 512 TMEM columns of an SM (2 S BN <= 512) and two smem stages of S (128 + BN) x 64 bf16
+// fit the 227 KB opt-in shared memory.  S = 5: 32 or 48; S = 4: 32 or 64; S <= 3: 64.
+int bn_candidates(int S, int (&out)[2]) {
+  if (S == 5) {
+    out[0] = 32;
+    out[1] = 48;
+    return 2;
+  }
+  if (S == 4) {
+    out[0] = 32;
+    out[1] = 64;
+    return 2;
+  }
+  out[0] = 64;
+  return 1;
+}
+
+template <int S, int BN>
+constexpr size_t smem_bytes() {
   return (size_t)NSTAGE * S * (BM * KA * 2 + BN * KA * 2) + 1024 + 256;
 }
 
-template <int S>
-cudaError_t launch(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args, dim3 grid,
-                   cudaStream_t s) {
-  constexpr int BN = S <= 4 ? 64 : 32;
-  static bool attr_set = false;
-  size_t sm = smem_bytes<S>();
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel<S, BN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  gemm_tc_kernel<S, BN><<<grid, nthreads(BN), sm, s>>>(ma, mb, args);
+template <int S, int BN>
+cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args, dim3 grid,
+                      cudaStream_t s) {
+  static_assert(smem_bytes<S, BN>() <= 232448, "shared memory");
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(gemm_tc_kernel<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<S, BN>());
+  });
+  if (attr != cudaSuccess) return attr;
+  gemm_tc_kernel<S, BN><<<grid, nthreads(BN), smem_bytes<S, BN>(), s>>>(ma, mb, args);
   return cudaGetLastError();
 }
+
+cudaError_t launch(int S, int BN, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& args,
+                   dim3 grid, cudaStream_t s) {
+  switch (S * 1000 + BN) {
+    case 2064: return launch_bn<2, 64>(ma, mb, args, grid, s);
+    case 3064: return launch_bn<3, 64>(ma, mb, args, grid, s);
+    case 4032: return launch_bn<4, 32>(ma, mb, args, grid, s);
+    case 4064: return launch_bn<4, 64>(ma, mb, args, grid, s);
+    case 5032: return launch_bn<5, 32>(ma, mb, args, grid, s);
+    case 5048: return launch_bn<5, 48>(ma, mb, args, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Autotuned tile width per problem shape: the first call of a shape runs every candidate
+// width on its own operands, times each with CUDA events on its stream and keeps the
+// fastest for every later call of that shape (process-wide, all threads).
+struct TuneKey {
+  int S, Mp, N2p, K2p, nb, cplx;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(S, Mp, N2p, K2p, nb, cplx) < std::tie(o.S, o.Mp, o.N2p, o.K2p, o.nb, o.cplx);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
 
 int g_sms = 0;
 
@@ -757,51 +819,89 @@ cudaError_t gemm_tc(int M, int N, int K, const T* A, const View& va, bool conjA,
   // slices of A (rows) and of B (columns, embedded); problem p owns row block p
   pack_operand<T, false>(A, va, conjA, M, K, g.Mp, g.K2p, S, sa, ea, status, s, nb);
   pack_operand<T, true>(B, vb, conjB, N, K, g.N2p, g.K2p, S, sb, eb, status, s, nb);
-  CUtensorMap ma, mb;
-  if (!make_map(&ma, sa, g.K2p, nb * g.Mp, S, BM) || !make_map(&mb, sb, g.K2p, nb * g.N2p, S, g.BN))
-    return cudaErrorInvalidValue;
+  CUtensorMap ma;
+  if (!make_map(&ma, sa, g.K2p, nb * g.Mp, S, BM)) return cudaErrorInvalidValue;
   const int atoms = g.K2p / KA;
   const int apc = atoms_per_chunk_for(S);
-  const int tiles = (g.Mp / BM) * (g.N2p / g.BN) * nb;
   const int chunks = (atoms + apc - 1) / apc;
-  int splits = 1;
-  if (tiles < g_sms && chunks > 1) splits = std::min(chunks, std::max(1, g_sms / tiles));
-  const int chunks_per_split = (chunks + splits - 1) / splits;
-  splits = (chunks + chunks_per_split - 1) / chunks_per_split;
-  TcArgs args;
-  args.M = M;
-  args.N2 = g.N2;
-  args.atoms_total = atoms;
-  args.atoms_per_chunk = apc;
-  args.atoms_per_split = chunks_per_split * apc;
-  args.expA = ea;
-  args.expB = eb;
-  args.cplx = CPLX ? 1 : 0;
-  args.atomic = splits > 1 ? 1 : 0;
-  args.C = reinterpret_cast<char*>(C);
-  args.vc = vc;
-  args.status = status;
-  args.splits = splits;
-  args.Mp = g.Mp;
-  args.N2p = g.N2p;
-  args.ebsB = CPLX ? g.N2p / 2 : g.N2p;
-  if (splits > 1) {
-    // the split partial sums are added into a zeroed C
-    cudaError_t e = gemm_f64<T>(M, N, 0, nb, A, va, false, B, vb, false, C, vc, s);
-    if (e != cudaSuccess) return e;
+  // one launch with tile width BN; a partial last column tile reads the next problem's
+  // rows (or the zero fill past the planes) for columns the epilogue never writes
+  auto run_bn = [&](int BN) -> cudaError_t {
+    CUtensorMap mb;
+    if (!make_map(&mb, sb, g.K2p, nb * g.N2p, S, BN)) return cudaErrorInvalidValue;
+    const int tiles_n = (g.N2p + BN - 1) / BN;
+    const int tiles = (g.Mp / BM) * tiles_n * nb;
+    int splits = 1;
+    if (tiles < g_sms && chunks > 1) splits = std::min(chunks, std::max(1, g_sms / tiles));
+    const int chunks_per_split = (chunks + splits - 1) / splits;
+    splits = (chunks + chunks_per_split - 1) / chunks_per_split;
+    TcArgs args;
+    args.M = M;
+    args.N2 = g.N2;
+    args.atoms_total = atoms;
+    args.atoms_per_chunk = apc;
+    args.atoms_per_split = chunks_per_split * apc;
+    args.expA = ea;
+    args.expB = eb;
+    args.cplx = CPLX ? 1 : 0;
+    args.atomic = splits > 1 ? 1 : 0;
+    args.C = reinterpret_cast<char*>(C);
+    args.vc = vc;
+    args.status = status;
+    args.splits = splits;
+    args.Mp = g.Mp;
+    args.N2p = g.N2p;
+    args.ebsB = CPLX ? g.N2p / 2 : g.N2p;
+    if (splits > 1) {
+      // the split partial sums are added into a zeroed C
+      cudaError_t e = gemm_f64<T>(M, N, 0, nb, A, va, false, B, vb, false, C, vc, s);
+      if (e != cudaSuccess) return e;
+    }
+    args.tiles_m = g.Mp / BM;
+    args.tiles_n = tiles_n;
+    args.total_tiles = args.tiles_m * args.tiles_n * splits * nb;
+    dim3 grid(std::min(args.total_tiles, g_sms));
+    note_launches(CBC_K_GEMM_TC, 1);
+    note_flops(CBC_K_TC_ISSUED,
+               2.0 * g.Mp * ((double)tiles_n * BN) * g.K2p * (S * (S + 1) / 2) * nb);
+    return launch(S, BN, ma, mb, args, grid, s);
+  };
+  int cand[2] = {64, 64};
+  const int ncand = bn_candidates(S, cand);
+  const TuneKey key{S, g.Mp, g.N2p, g.K2p, nb, CPLX ? 1 : 0};
+  int BN = -1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) BN = it->second;
   }
-  args.tiles_m = g.Mp / BM;
-  args.tiles_n = g.N2p / g.BN;
-  args.total_tiles = args.tiles_m * args.tiles_n * splits * nb;
-  dim3 grid(std::min(args.total_tiles, g_sms));
-  note_launches(CBC_K_GEMM_TC, 1);
-  note_flops(CBC_K_TC_ISSUED, 2.0 * g.Mp * g.N2p * g.K2p * (S * (S + 1) / 2) * nb);
-  switch (S) {
-    case 2: return launch<2>(ma, mb, args, grid, s);
-    case 3: return launch<3>(ma, mb, args, grid, s);
-    case 4: return launch<4>(ma, mb, args, grid, s);
-    default: return launch<5>(ma, mb, args, grid, s);
+  if (BN > 0 || ncand == 1) return run_bn(BN > 0 ? BN : cand[0]);
+  // first call of this shape: every candidate computes the same exact sums, so the
+  // output of the last one stands; the fastest is kept for later calls
+  cudaEvent_t ev[3];
+  for (int c = 0; c <= ncand; ++c) cudaEventCreate(&ev[c]);
+  cudaError_t e = cudaEventRecord(ev[0], s);
+  for (int c = 0; c < ncand && e == cudaSuccess; ++c) {
+    e = run_bn(cand[c]);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[c + 1], s);
   }
+  if (e == cudaSuccess) e = cudaEventSynchronize(ev[ncand]);
+  if (e == cudaSuccess) {
+    int best = cand[0];
+    float best_ms = 0.0f;
+    for (int c = 0; c < ncand; ++c) {
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, ev[c], ev[c + 1]);
+      if (c == 0 || ms < best_ms) {
+        best_ms = ms;
+        best = cand[c];
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.emplace(key, best);
+  }
+  for (int c = 0; c <= ncand; ++c) cudaEventDestroy(ev[c]);
+  return e;
 }
 
 template cudaError_t gemm_tc<double>(int, int, int, const double*, const View&, bool,

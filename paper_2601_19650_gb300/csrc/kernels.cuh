@@ -167,6 +167,13 @@ cudaError_t sum_squares(const T* x, int64_t n, double* out, cudaStream_t s, int 
 template <typename T>
 cudaError_t scaled_adjoint_w(const T* V, int ldv, const double* w, int64_t w_bs, int k, int n,
                              T* L, int64_t l_bs, cudaStream_t s, int nb = 1);
+// Sketch step of SRC (Sec. III C): C[j, col] = sum_p Lp[(cj, p), col] * om[p, j] with
+// cj = j (c == s) or 0 (c == 1, the first site), Lp: (c d) x ncol row-major, om: d x s
+// row-major, C: s x ncol; nb problems, Lp lp_bs, om om_bs and C c_bs elements apart.
+template <typename T>
+cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om, int s,
+                            int64_t lp_bs, int64_t om_bs, T* C, int64_t c_bs, cudaStream_t st,
+                            int nb = 1);
 // dst_b[i] = src_b[i] for i < n, src_b = src + b * s_bs, dst_b = dst + b * d_bs
 template <typename T>
 cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n,

@@ -483,6 +483,37 @@ cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64
   return cudaGetLastError();
 }
 
+// one thread per (j, col): the d products of the sketch row j with column col of Lp
+template <typename T>
+__global__ void sketch_kernel(const T* Lp, int c, int d, int64_t ncol, const T* om, int s,
+                              int64_t lp_bs, int64_t om_bs, T* C, int64_t c_bs) {
+  using O = ops<T>;
+  const int b = blockIdx.z, j = blockIdx.y;
+  Lp += (int64_t)b * lp_bs;
+  om += (int64_t)b * om_bs;
+  C += (int64_t)b * c_bs;
+  const int cj = (c == 1) ? 0 : j;
+  for (int64_t col = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; col < ncol;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    T acc = O::zero();
+    for (int p = 0; p < d; ++p)
+      acc = O::fma(Lp[((int64_t)cj * d + p) * ncol + col], om[(int64_t)p * s + j], acc);
+    C[(int64_t)j * ncol + col] = acc;
+  }
+}
+
+template <typename T>
+cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om, int s,
+                            int64_t lp_bs, int64_t om_bs, T* C, int64_t c_bs, cudaStream_t st,
+                            int nb) {
+  if (s <= 0 || ncol <= 0 || nb <= 0) return cudaSuccess;
+  if (c != 1 && c != s) return cudaErrorInvalidValue;
+  note_launches(CBC_K_AUX, 1);
+  const int gx = (int)std::min<int64_t>((ncol + 255) / 256, 1024);
+  sketch_kernel<T><<<dim3(gx, s, nb), 256, 0, st>>>(Lp, c, d, ncol, om, s, lp_bs, om_bs, C, c_bs);
+  return cudaGetLastError();
+}
+
 #define CBC_MISC_INST(T)                                                                     \
   template cudaError_t row_norms2<T>(const T*, int, int, int64_t, int64_t, double*,          \
                                      cudaStream_t, int);                                     \
@@ -495,7 +526,9 @@ cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64
                                            T*, int64_t, cudaStream_t, int);                  \
   template cudaError_t copy_batched<T>(const T*, int64_t, T*, int64_t, int64_t, cudaStream_t, \
                                        int);                                                 \
-  template cudaError_t scale_rows<T>(T*, int, int, int64_t, const double*, cudaStream_t, int);
+  template cudaError_t scale_rows<T>(T*, int, int, int64_t, const double*, cudaStream_t, int); \
+  template cudaError_t sketch_contract<T>(const T*, int, int, int64_t, const T*, int, int64_t, \
+                                          int64_t, T*, int64_t, cudaStream_t, int);
 CBC_MISC_INST(double)
 CBC_MISC_INST(zdbl)
 #undef CBC_MISC_INST

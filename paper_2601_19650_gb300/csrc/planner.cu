@@ -543,7 +543,9 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
   env[0] = ar.get<T>(nb);
   CKA(env[0]);
   CK(cudaMemcpyAsync(env[0], ones.data(), sizeof(T) * nb, cudaMemcpyHostToDevice, s));
-  for (int i = 0; i < L - 1; ++i) {
+  // Zip-Up (Sec. III C) has no first sweep: it truncates during the single sweep below
+  const int fwd_end = (o.method == kMethodZipUp) ? 0 : L - 1;
+  for (int i = 0; i < fwd_end; ++i) {
     const int c = chi[i], b = ob(i), a = sb(i), d = (int)st.phys[i], a2 = sb(i + 1), b2 = ob(i + 1);
     const size_t mk = tmp.mark();
     const T *Ti = nullptr, *Wi = nullptr;
@@ -573,12 +575,25 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     vl.cols2(a2, (int64_t)d * b2 * a2, 1);
     vl.bs = lbs;
     CK(tgemm<T>(pr, true, false, d * b2, c * a2, b * d, Wi, vw, false, X, vx, false, Lp, vl, s));
-    // F3: compress M[(chi sigma'), (b' a')]
     int k = 0;
-    rc = compress_rows<T>(tmp, pr, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k,
-                          &ar, dcut.data());
-    if (rc != CBC_OK) return rc;
-    for (int b = 0; b < nb; ++b) disc[b][i + 1] = dcut[b];
+    if (o.method == kMethodSRC) {
+      // SRC (Sec. III C): the sketch takes the place of the truncation, C[j, (b' a')] =
+      // sum_sigma' L'[(j sigma'), (b' a')] Omega_i[sigma', j] (j shared by all sites)
+      k = o.sketch;
+      const int64_t cbs = (int64_t)k * b2 * a2;
+      T* Cn = ar.get<T>((size_t)nb * cbs);
+      CKA(Cn);
+      CK(sketch_contract<T>(Lp, c, d, (int64_t)b2 * a2, static_cast<const T*>(o.sketch_mats[i]), k,
+                            lbs, 0, Cn, cbs, s, nb));
+      CK(normalize_inplace<T>(Cn, cbs, sc.log_fwd, sc.status, sc.scratch, s, nb));
+      env[i + 1] = Cn;
+    } else {
+      // F3: compress M[(chi sigma'), (b' a')]
+      rc = compress_rows<T>(tmp, pr, Lp, c * d, b2 * a2, max_bond, tol, o, sc, s, &env[i + 1], &k,
+                            &ar, dcut.data());
+      if (rc != CBC_OK) return rc;
+      for (int b = 0; b < nb; ++b) disc[b][i + 1] = dcut[b];
+    }
     chi[i + 1] = k;
     tmp.release(mk);
   }
@@ -634,7 +649,40 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
                 false, Y, vy, false, Z, vz, s));
     // B3: S[chi, (sigma' chi')] = sum_{(b a)} L^[i-1][chi, (b a)] Z[(b a), (sigma' chi')]
     const int n = d * cp;
-    const int m = c;
+    int m = c;
+    T* Lz = nullptr;  // Zip-Up, SRC: a factor whose rows span the kept subspace (then its LQ)
+    if (i > 0 && o.method == kMethodSRC) {
+      // SRC: the rows of the sketch that enter the LQ, the generic rank of the sketched
+      // block (beyond it the block is rank deficient): min(s, prod_{k<i} d_k, a b)
+      int64_t pl = 1;
+      for (int q = 0; q < i && pl < c; ++q) pl *= st.phys[q];
+      m = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)c, pl, (int64_t)a_in * b_in}));
+      if (m < n) {
+        // the new tensor is an orthonormal basis of the sketched block's rows; a sketch of a
+        // fast-decaying spectrum is too ill conditioned for CholeskyQR, so the rows first go
+        // through the rank-revealing compression (every direction above the rank floor
+        // kept), whose factor CholeskyQR2 then orthonormalises
+        T* Sk = tmp.get<T>((size_t)nb * m * n);
+        CKA(Sk);
+        CK(tgemm<T>(pr, false, false, m, n, b_in * a_in, env[i],
+                    View::rowmajor(b_in * a_in, (int64_t)c * b_in * a_in), false, Z,
+                    View::rowmajor(n, zbs), false, Sk, View::rowmajor(n, (int64_t)m * n), s));
+        int k = 0;
+        rc = compress_rows<T>(tmp, pr, Sk, m, n, m, 0.0, o, sc, s, &Lz, &k, nullptr, nullptr);
+        if (rc != CBC_OK) return rc;
+        m = k;
+      }
+    } else if (i > 0 && o.method == kMethodZipUp) {
+      // Zip-Up (Sec. III C): truncate the (sigma', chi') leg of Z[(b a), (sigma' chi')] at
+      // once, by the rank rule on Z's singular values; the new tensor is an orthonormal row
+      // basis of the kept right singular subspace
+      int k = 0;
+      rc = compress_rows<T>(tmp, pr, Z, b_in * a_in, n, max_bond, tol, o, sc, s, &Lz, &k, nullptr,
+                            dcut.data());
+      if (rc != CBC_OK) return rc;
+      for (int b = 0; b < nb; ++b) outs[b]->discarded[i] = dcut[b];
+      m = k;
+    }
     // at least as many rows as columns: every unitary Q spans the whole row space, so the
     // identity is exact (and skips an ill-conditioned square CholeskyQR)
     const int cn = (m < n) ? m : n;
@@ -649,8 +697,10 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
       if (!node) return cuda_fail(tmp.err, "workspace allocation S");
     }
     for (int b = 0; b < nb; ++b) outs[b]->numel[i] = (int64_t)cn * n;
-    if (formed) {
-      CK(tgemm<T>(pr, false, false, m, n, b_in * a_in, env[i], View::rowmajor(b_in * a_in, (int64_t)m * b_in * a_in),
+    if (formed && Lz) {
+      CK(copy_batched<T>(Lz, (int64_t)m * n, node, nbs, (int64_t)m * n, s, nb));
+    } else if (formed) {  // (SRC uses the first m of the c rows of its sketch)
+      CK(tgemm<T>(pr, false, false, m, n, b_in * a_in, env[i], View::rowmajor(b_in * a_in, (int64_t)c * b_in * a_in),
                   false, Z, View::rowmajor(n, zbs), false, node, View::rowmajor(n, nbs), s));
     }
     // publishes the group's node tensors into the per-instance outputs

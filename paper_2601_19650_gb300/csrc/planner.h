@@ -31,6 +31,8 @@ struct Net {
   virtual ~Net();
 };
 
+enum { kMethodCBC = 0, kMethodZipUp = 1, kMethodSRC = 2 };
+
 struct Options {
   int precision = CBC_PREC_FP64;
   // rank floor: singular values s_j <= eps_rank * s_0 are dropped.  FP64 keeps the
@@ -39,6 +41,14 @@ struct Options {
   double eps_rank = 1e-12;
   int slices_fwd = 5;
   int slices_bwd = 4;
+  // cbc_apply_batched: most instances per lockstep group
+  int max_group = 32;
+  // the method the chain sweeps run (Sec. III A, or a comparison method of Sec. III C)
+  int method = kMethodCBC;
+  // SRC: sketch width s and, per site, the device pointer of its d x s random matrix
+  // (FP64 storage of the network's type; the last site's is not used)
+  int sketch = 0;
+  const void* const* sketch_mats = nullptr;
   // set for instances that run next to others on their own streams (cbc_apply_batched):
   // kernels whose CTAs wait on each other then use cluster launches, which run
   // concurrently with other streams' work, instead of cooperative ones, which do not

@@ -74,6 +74,11 @@ def test_library_loads_and_rejects_bad_arguments(libpath):
     # an empty batch is a no-op; a batch with NULL arrays is rejected
     assert L.cbc_apply_batched(0, None, None, None, None, None, 0, None) == 0
     assert L.cbc_apply_batched(2, None, None, None, None, None, 0, None) == 1
+    # the comparison methods check their handles before any device work
+    assert L.zipup_apply(None, None, 4, 0.0, None, ctypes.byref(out)) == 1
+    assert "zipup_apply" in _cbc.cbc_last_error() and out.value is None
+    assert L.src_apply(None, None, 4, None, 1, 0, None, ctypes.byref(out)) == 1
+    assert "src_apply" in _cbc.cbc_last_error() and out.value is None
 
 
 def test_build_targets_sm103a_only():

@@ -203,7 +203,8 @@ def test_comparator_oracle_pin(check):
 MUTATIONS = {
     "zipup-R-update-drops-conj": ('R = np.einsum("yPx,abPx->yab", Q.conj(), Z, optimize=True)      # = (U_k s_k)^T',
                                   'R = np.einsum("yPx,abPx->yab", Q, Z, optimize=True)      # = (U_k s_k)^T'),
-    "zipup-keeps-smallest": ("Q = Vh[:k].reshape(k, d, c)", "Q = Vh[-k:].reshape(k, d, c)"),
+    "zipup-keeps-smallest": ("Q = Vh[:k].reshape(k, d, c)                     # (chi'",
+                             "Q = Vh[-k:].reshape(k, d, c)                     # (chi'"),
     "zipup-operator-in-out-swapped": ('Z = np.einsum("asyB,bPsB->abPy", Y, W[i], optimize=True)        # sum over sigma, beta_i',
                                       'Z = np.einsum("asyB,bsPB->abPy", Y, W[i], optimize=True)        # sum over sigma, beta_i'),
     "src-omega-conjugated": ('Om = np.asarray(omega[i])', 'Om = np.asarray(omega[i]).conj()'),

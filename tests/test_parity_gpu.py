@@ -183,7 +183,7 @@ def test_large_bonds(precision):
 # ---------------------------------------------------------------------------------------
 # lockstep groups: cbc_apply_batched runs instances of one shape as one launch per step
 # ---------------------------------------------------------------------------------------
-def _apply_batched(probs, precision, workers=1):
+def _apply_batched(probs, precision, workers=1, max_group=0):
     """All instances through cbc_apply_batched (one stream each); host outputs and the
     launch statistics of the call."""
     import torch
@@ -202,7 +202,8 @@ def _apply_batched(probs, precision, workers=1):
     _cbc.cbc_stats_enable(True)
     try:
         outs = _cbc.cbc_apply_batched(hs, ho, [p.max_bond for p in probs],
-                                      [p.tol for p in probs], _cbc.make_options(precision),
+                                      [p.tol for p in probs],
+                                      _cbc.make_options(precision, max_group=max_group),
                                       workers=workers)
     finally:
         stats = _cbc.cbc_stats_read()
@@ -254,6 +255,17 @@ def test_group_wide_batch(precision, bar):
     # instance refines (second level, on that instance alone) adds one group of its own
     assert 16 - 1 <= stats["eig"]["groups"] <= 16 - 1 + 2 * len(probs), stats["eig"]
     assert stats["tridiag"]["launches"] >= 16 - 1
+
+
+@pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
+def test_group_larger_than_32(precision, bar):
+    # max_group 64: 40 instances in one lockstep group (grids and workspaces scale with the
+    # group; every launch covers all 40)
+    L = 8
+    probs = [make_problem(2, seed=200 + j, L=L, chi=16, D=4, max_bond=12) for j in range(40)]
+    res, stats = _apply_batched(probs, precision, max_group=64)
+    _check_against_oracle(probs, res, bar)
+    assert stats["eig"]["groups"] == L - 1, stats["eig"]
 
 
 def test_group_mixed_shapes_and_real():
