@@ -6,7 +6,7 @@ this module: only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline
 
 It is a plain, slow transcription of the method in float64 / complex128 NumPy:
 contractions are ``numpy.einsum`` on named legs, the compression is a truncated
-``numpy.linalg.svd`` (the paper compresses "for example via SVD", Sec. III A) and the
+``numpy.linalg.svd`` (an SVD is the compression the paper names, Sec. III A) and the
 new node tensors come from ``numpy.linalg.qr`` (Eqs. (tt_cbc_qr_decomp),
 (cbc_tree_qr)).  It shares no code with the GPU path, which reaches the same result
 through Gram matrices, a Hermitian eigensolver and CholeskyQR.
@@ -20,8 +20,8 @@ notes of the repository):
 * the output case "if i = 0" of Sec. III A means the leftmost site;
 * the tree R-update Eq. (cbc_final_contraction) uses the complex conjugate ``Q*`` as in
   the tensor-train Eq. (tt_cbc_final_contraction);
-* rank rule (Sec. III A "compressed down to the desired bond dimension", Sec. V
-  "tolerance for the SVD"): keep the singular values ``s_j > eps_rank * s_0``, then the
+* rank rule (Sec. III A compresses to a target bond dimension; Sec. V mentions an SVD
+  tolerance as the adaptive alternative): keep the singular values ``s_j > eps_rank * s_0``, then the
   smallest ``k`` whose discarded weight ``sum_{j>=k} s_j^2 <= tol^2 sum_j s_j^2`` (if
   ``tol > 0``), then at most ``max_bond`` (if ``max_bond > 0``);
 * when the QR of Eq. (tt_cbc_qr_decomp) / (cbc_tree_qr) has more rows than columns on

@@ -28,11 +28,8 @@ Readings (listed with their reasons in the design notes):
   first ``r`` sketch rows enter the LQ (beyond that the block is rank deficient);
   when ``r`` is at least the column count ``d_i chi_i`` the new tensor is the identity
   (any unitary gives the same state), as for CBC;
-* SRC's new tensor is an orthonormal basis of the rows of the sketched block (the paper's
-  QR): its right singular vectors whose singular values exceed the rank floor of CBC
-  (``eps_rank * s_0``), so that a block whose condition number exceeds what the floor
-  resolves keeps only its resolved directions (in exact arithmetic and for a
-  well-conditioned block this is the LQ's Q up to a unitary, the same state).
+* SRC's new tensor is the Q of the LQ of the sketched block's first ``r`` rows (the
+  paper's QR; Householder QR here, so any condition number of the block is handled).
 """
 from __future__ import annotations
 
@@ -40,7 +37,7 @@ from typing import List, Optional
 
 import numpy as np
 
-from .cbc import EPS_RANK, CBCResult, CutInfo, _as_tt, choose_rank
+from .cbc import EPS_RANK, CBCResult, CutInfo, _as_tt, choose_rank, lq_rows
 
 
 def zipup_tt(state: List[np.ndarray], op: List[np.ndarray], max_bond: int = 0,
@@ -102,8 +99,7 @@ def src_rank(phys, C_i: np.ndarray, i: int) -> int:
     return max(1, min(s, p_left, a * b))
 
 
-def src_tt(state: List[np.ndarray], op: List[np.ndarray], omega: List[np.ndarray],
-           eps_rank: float = EPS_RANK) -> CBCResult:
+def src_tt(state: List[np.ndarray], op: List[np.ndarray], omega: List[np.ndarray]) -> CBCResult:
     """SRC of an MPO applied to an MPS (Sec. III C) with the given random matrices
     ``omega[i]`` (``d_i x s``; the last site's is not used)."""
     T, W = _as_tt(state, op)
@@ -127,11 +123,8 @@ def src_tt(state: List[np.ndarray], op: List[np.ndarray], omega: List[np.ndarray
         if m >= d * c:
             Q = np.eye(d * c, dtype=dt).reshape(d * c, d, c)
         else:
-            # an orthonormal basis of the rows of the sketched block: its right singular
-            # vectors above the rank floor (in exact arithmetic the LQ's Q, up to a unitary)
-            _, sv, Vh = np.linalg.svd(S.transpose(1, 0, 2).reshape(m, d * c), full_matrices=False)
-            k = max(1, int(np.count_nonzero(sv > eps_rank * sv[0]))) if sv[0] > 0 else 1
-            Q = Vh[:k].reshape(k, d, c)
+            _, Qm = lq_rows(S.transpose(1, 0, 2).reshape(m, d * c))   # the paper's QR
+            Q = Qm.reshape(-1, d, c)
         out[i] = Q
         R = np.einsum("yPx,abPx->yab", Q.conj(), Z, optimize=True)
     out[L - 1] = out[L - 1][..., 0]

@@ -1,6 +1,6 @@
 // FP64 Hermitian eigensolver for the truncation of Sec. III A / III B.
 //
-// The paper compresses the fused leg "for example via SVD" (Sec. III A).  The GPU path
+// The paper names an SVD as one way to compress the fused leg (Sec. III A).  The GPU path
 // reaches the same truncation through the Gram matrix K = M M^H (or M^H M): its
 // eigenvectors are the singular vectors of M and its eigenvalues the squared singular
 // values, so keeping the k largest eigenpairs keeps the same subspace as the truncated
@@ -726,13 +726,13 @@ __global__ void bisect32_kernel(const double* d, const double* e, int m, float* 
 }
 
 // ---- eigenvectors of T by FP64 inverse iteration ----------------------------------
-// One thread per kept candidate.  The LU of T - sigma I with partial pivoting (the
-// layout of LAPACK's tridiagonal factorisation) lives in shared memory, [i][thread],
-// with the pivots stored as reciprocals so the solves are division free.  Candidates
-// whose single-precision eigenvalues lie within 1e-4 of the spectral radius of each
-// other form a cluster that the thread of its first member computes in order, each new
-// vector orthogonalised against the earlier ones.  The eigenvalue is the FP64 Rayleigh
-// quotient of the converged vector.
+// The LU of T - sigma I with partial pivoting (the layout of LAPACK's tridiagonal
+// factorisation) lives in shared memory, [i][member], with the pivots stored as
+// reciprocals so the solves are division free.  A candidate whose single-precision
+// eigenvalue is separated from its neighbours by more than 1e-4 of the spectral radius
+// gets a thread of its own (invit_kernel); a run of closer candidates is a cluster that
+// one warp iterates as a block, orthonormalising after every solve
+// (invit_cluster_kernel).  The eigenvalue is the FP64 Rayleigh quotient of the vector.
 __device__ __forceinline__ uint32_t hash32(uint32_t x) {
   x ^= x >> 16;
   x *= 0x7feb352dU;
@@ -753,128 +753,232 @@ struct InvArgs {
   size_t wb;           // workspace bytes between the matrices of a batch (blockIdx.y)
 };
 
+// Shared-memory arrays of the members handled by one CTA: element i of member t at
+// [i * tpb + t] (consecutive members' rows side by side).
+struct InvSmem {
+  double *dl, *di, *du, *du2, *b;  // multipliers, reciprocal pivots, U's two superdiagonals, vector
+  unsigned char* piv;
+  int tpb;
+  __device__ InvSmem(double* base, int m, int tpb_) : tpb(tpb_) {
+    dl = base;
+    di = dl + (size_t)m * tpb;
+    du = di + (size_t)m * tpb;
+    du2 = du + (size_t)m * tpb;
+    b = du2 + (size_t)m * tpb;
+    piv = reinterpret_cast<unsigned char*>(b + (size_t)m * tpb);
+  }
+};
+#define SH(arr, i) w.arr[(size_t)(i) * w.tpb + t]
+
+// LU with partial pivoting of T - sigma I for member t (pivots kept as reciprocals, so the
+// solves are division free)
+__device__ void invit_factor(const double* d, const double* e, int m, double sigma, double tiny,
+                             const InvSmem& w, int t) {
+  double dcur = d[0] - sigma;
+  double ucur = (m > 1) ? e[0] : 0.0;  // superdiagonal entry of the current row
+  for (int i = 0; i < m - 1; ++i) {
+    const double li = e[i];
+    const double dn = d[i + 1] - sigma;
+    const double un = (i + 1 < m - 1) ? e[i + 1] : 0.0;
+    if (fabs(dcur) >= fabs(li)) {
+      double dv = (fabs(dcur) < tiny) ? ((dcur < 0.0) ? -tiny : tiny) : dcur;
+      double r = rcp64(dv);
+      double f = li * r;
+      SH(piv, i) = 0;
+      SH(dl, i) = f;
+      SH(di, i) = r;
+      SH(du, i) = ucur;
+      SH(du2, i) = 0.0;
+      dcur = dn - f * ucur;
+      ucur = un;
+    } else {
+      double r = rcp64(li);
+      double f = dcur * r;
+      SH(piv, i) = 1;
+      SH(dl, i) = f;
+      SH(di, i) = r;
+      SH(du, i) = dn;
+      SH(du2, i) = un;
+      dcur = ucur - f * dn;
+      ucur = -f * un;
+    }
+  }
+  double dv = (fabs(dcur) < tiny) ? ((dcur < 0.0) ? -tiny : tiny) : dcur;
+  SH(di, m - 1) = rcp64(dv);
+}
+
+// b <- (T - sigma I)^{-1} b for member t with its factors: L y = P b, then U x = y
+__device__ void invit_solve(int m, const InvSmem& w, int t) {
+  double carry = SH(b, 0);
+  for (int i = 0; i < m - 1; ++i) {
+    double nxt = SH(b, i + 1);
+    if (SH(piv, i) == 0) {
+      SH(b, i) = carry;
+      carry = nxt - SH(dl, i) * carry;
+    } else {
+      SH(b, i) = nxt;
+      carry = carry - SH(dl, i) * nxt;
+    }
+  }
+  SH(b, m - 1) = carry;
+  double x1 = 0.0, x2 = 0.0;
+  for (int i = m - 1; i >= 0; --i) {
+    double sv = SH(b, i) - SH(du, i) * x1 - SH(du2, i) * x2;
+    if (i == m - 1) sv = SH(b, i);
+    double xi = sv * SH(di, i);
+    SH(b, i) = xi;
+    x2 = x1;
+    x1 = xi;
+  }
+}
+
+// random start vector of candidate j (fixed hash, so every run is reproducible)
+__device__ void invit_start(int m, int j, const InvSmem& w, int t) {
+  for (int i = 0; i < m; ++i) {
+    uint32_t h = hash32((uint32_t)(i * 7919 + j * 104729 + 17));
+    SH(b, i) = ((double)(h & 0xffffff) / 16777216.0) - 0.5;
+  }
+}
+
+// sum_i x_i y_i over strided arrays with four independent partial sums (the FP64
+// latency chain is the cost of a lone thread's dot product)
+__device__ __forceinline__ double dot4(const double* x, size_t sx, const double* y, size_t sy,
+                                       int m) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  int i = 0;
+  for (; i + 3 < m; i += 4) {
+    a0 = fma(x[(size_t)i * sx], y[(size_t)i * sy], a0);
+    a1 = fma(x[(size_t)(i + 1) * sx], y[(size_t)(i + 1) * sy], a1);
+    a2 = fma(x[(size_t)(i + 2) * sx], y[(size_t)(i + 2) * sy], a2);
+    a3 = fma(x[(size_t)(i + 3) * sx], y[(size_t)(i + 3) * sy], a3);
+  }
+  for (; i < m; ++i) a0 = fma(x[(size_t)i * sx], y[(size_t)i * sy], a0);
+  return (a0 + a1) + (a2 + a3);
+}
+
+// Rayleigh quotient of member t's (unit) vector, written with the vector to column j of X
+__device__ void invit_finish(const InvArgs& a, int j, const InvSmem& w, int t) {
+  const int m = a.m, K = a.kmax;
+  double rqv = 0.0;
+  for (int i = 0; i < m; ++i) {
+    const double xi = SH(b, i);
+    double tx = a.d[i] * xi;
+    if (i > 0) tx += a.e[i - 1] * SH(b, i - 1);
+    if (i < m - 1) tx += a.e[i] * SH(b, i + 1);
+    rqv += xi * tx;
+    a.X[(size_t)i * K + j] = xi;
+  }
+  a.rq[j] = rqv;
+}
+
+__device__ __forceinline__ void invit_shift(InvArgs& a) {
+  const size_t off = blockIdx.y * a.wb;
+  a.d = byte_shift(a.d, off);
+  a.e = byte_shift(a.e, off);
+  a.lam32 = byte_shift(a.lam32, off);
+  a.X = byte_shift(a.X, off);
+  a.rq = byte_shift(a.rq, off);
+}
+
+// Each solve shrinks the components along eigenvectors at distance delta by about
+// |lambda - sigma| / delta with |lambda - sigma| ~ 1e-7 span (single-precision shifts);
+// four solves reach FP64 accuracy for delta >= 1e-4 span.  Candidates closer than that
+// to a neighbour form a cluster (invit_cluster_kernel).
+__device__ __forceinline__ double invit_span(const InvArgs& a) {
+  return fmax(fabs((double)a.lam32[0]), fabs((double)a.lam32[a.m - 1])) + DBL_MIN;
+}
+__device__ __forceinline__ bool close_pair(const InvArgs& a, int j, double ortol) {
+  return (double)a.lam32[j] - (double)a.lam32[j + 1] <= ortol;  // descending
+}
+
+// candidates that are not part of a cluster: one thread each
 __global__ void invit_kernel(InvArgs a) {
   extern __shared__ double shd[];
-  {
-    const size_t off = blockIdx.y * a.wb;
-    a.d = byte_shift(a.d, off);
-    a.e = byte_shift(a.e, off);
-    a.lam32 = byte_shift(a.lam32, off);
-    a.X = byte_shift(a.X, off);
-    a.rq = byte_shift(a.rq, off);
-  }
-  const int tpb = blockDim.x, tid = threadIdx.x;
-  const int m = a.m, K = a.kmax;
-  double* dl = shd;
-  double* di = dl + (size_t)m * tpb;   // reciprocal pivots
-  double* du = di + (size_t)m * tpb;
-  double* du2 = du + (size_t)m * tpb;
-  double* b = du2 + (size_t)m * tpb;
-  unsigned char* piv = reinterpret_cast<unsigned char*>(b + (size_t)m * tpb);
-#define SH(arr, i) arr[(size_t)(i) * tpb + tid]
-  const int jj = blockIdx.x * tpb + tid;
+  invit_shift(a);
+  const int m = a.m, K = a.kmax, t = threadIdx.x;
+  const InvSmem w(shd, m, blockDim.x);
+  const int jj = blockIdx.x * blockDim.x + t;
   if (jj >= K) return;
-  const double span = fmax(fabs((double)a.lam32[0]), fabs((double)a.lam32[m - 1])) + DBL_MIN;
-  // Each solve shrinks the components along eigenvectors at distance delta by about
-  // |lambda - sigma| / delta with |lambda - sigma| ~ 1e-7 span (single-precision
-  // shifts); four solves reach FP64 accuracy for delta >= 1e-4 span.  Closer pairs are
-  // handled as a cluster with explicit orthogonalisation.
+  const double span = invit_span(a);
   const double ortol = 1e-4 * span;
-  if (jj > 0 && (double)a.lam32[jj - 1] - (double)a.lam32[jj] <= ortol) return;
-  int cend = jj + 1;
-  while (cend < K && (double)a.lam32[cend - 1] - (double)a.lam32[cend] <= ortol) ++cend;
-  const double eps = 2.220446049250313e-16;
-  const double tiny = eps * span;
-  double prev_sigma = 0.0;
-  for (int jc = jj; jc < cend; ++jc) {
-    double sigma = (double)a.lam32[jc];
-    if (jc > jj && prev_sigma - sigma < 1e-10 * span) sigma = prev_sigma - 1e-10 * span;
-    prev_sigma = sigma;
-    // LU with partial pivoting of T - sigma I
-    double dcur = a.d[0] - sigma;
-    double ucur = (m > 1) ? a.e[0] : 0.0;  // superdiagonal entry of the current row
-    for (int i = 0; i < m - 1; ++i) {
-      const double li = a.e[i];
-      const double dn = a.d[i + 1] - sigma;
-      const double un = (i + 1 < m - 1) ? a.e[i + 1] : 0.0;
-      if (fabs(dcur) >= fabs(li)) {
-        double dv = (fabs(dcur) < tiny) ? ((dcur < 0.0) ? -tiny : tiny) : dcur;
-        double r = rcp64(dv);
-        double f = li * r;
-        SH(piv, i) = 0;
-        SH(dl, i) = f;
-        SH(di, i) = r;
-        SH(du, i) = ucur;
-        SH(du2, i) = 0.0;
-        dcur = dn - f * ucur;
-        ucur = un;
-      } else {
-        double r = rcp64(li);
-        double f = dcur * r;
-        SH(piv, i) = 1;
-        SH(dl, i) = f;
-        SH(di, i) = r;
-        SH(du, i) = dn;
-        SH(du2, i) = un;
-        dcur = ucur - f * dn;
-        ucur = -f * un;
-      }
+  if ((jj > 0 && close_pair(a, jj - 1, ortol)) || (jj + 1 < K && close_pair(a, jj, ortol))) return;
+  const double tiny = 2.220446049250313e-16 * span;
+  invit_factor(a.d, a.e, m, (double)a.lam32[jj], tiny, w, t);
+  invit_start(m, jj, w, t);
+  for (int it = 0; it < 4; ++it) {
+    invit_solve(m, w, t);
+    const double nrm = dot4(&SH(b, 0), w.tpb, &SH(b, 0), w.tpb, m);
+    const double inv = (nrm > 0.0) ? rcp64(sqrt(nrm)) : 0.0;
+    for (int i = 0; i < m; ++i) SH(b, i) *= inv;
+  }
+  invit_finish(a, jj, w, t);
+}
+
+// A cluster of candidates (neighbours closer than 1e-4 of the spectral radius) by one
+// warp: `per` members at a time, one per lane, iterated as a block (block inverse
+// iteration): every lane solves with its own shift (shifts at least 1e-10 span apart),
+// then the block is orthonormalised (modified Gram-Schmidt, lanes in parallel) against
+// the cluster's finished columns and within itself, four times.  The vectors then span
+// the invariant subspace of the cluster's eigenvalues (any basis of it is a valid set of
+// eigenvectors when they are not resolved individually).
+__global__ void invit_cluster_kernel(InvArgs a, int per) {
+  extern __shared__ double shd[];
+  invit_shift(a);
+  const int m = a.m, K = a.kmax, lane = threadIdx.x;
+  const InvSmem w(shd, m, per);
+  const int jj = blockIdx.x;
+  if (jj >= K) return;
+  const double span = invit_span(a);
+  const double ortol = 1e-4 * span;
+  // the first member of a cluster of two or more leads it
+  if (jj > 0 && close_pair(a, jj - 1, ortol)) return;
+  if (!(jj + 1 < K && close_pair(a, jj, ortol))) return;
+  int cend = jj + 2;
+  while (cend < K && close_pair(a, cend - 1, ortol)) ++cend;
+  const double tiny = 2.220446049250313e-16 * span;
+  for (int j0 = jj; j0 < cend; j0 += per) {
+    const int nact = min(per, cend - j0);
+    const bool act = lane < nact;
+    const int t = act ? lane : 0;
+    const int j = j0 + lane;
+    if (act) {
+      double sigma = (double)a.lam32[jj];
+      for (int q = jj + 1; q <= j; ++q) sigma = fmin((double)a.lam32[q], sigma - 1e-10 * span);
+      invit_factor(a.d, a.e, m, sigma, tiny, w, t);
+      invit_start(m, j, w, t);
     }
-    {
-      double dv = (fabs(dcur) < tiny) ? ((dcur < 0.0) ? -tiny : tiny) : dcur;
-      SH(di, m - 1) = rcp64(dv);
-    }
-    for (int i = 0; i < m; ++i) {
-      uint32_t h = hash32((uint32_t)(i * 7919 + jc * 104729 + 17));
-      SH(b, i) = ((double)(h & 0xffffff) / 16777216.0) - 0.5;
-    }
+    __syncwarp();
     for (int it = 0; it < 4; ++it) {
-      // forward: L y = P b
-      double carry = SH(b, 0);
-      for (int i = 0; i < m - 1; ++i) {
-        double nxt = SH(b, i + 1);
-        if (SH(piv, i) == 0) {
-          SH(b, i) = carry;
-          carry = nxt - SH(dl, i) * carry;
-        } else {
-          SH(b, i) = nxt;
-          carry = carry - SH(dl, i) * nxt;
+      if (act) {
+        invit_solve(m, w, t);
+        // against the finished columns of the cluster
+        for (int q = jj; q < j0; ++q) {
+          const double dv = dot4(a.X + q, (size_t)K, &SH(b, 0), w.tpb, m);
+          for (int i = 0; i < m; ++i) SH(b, i) -= dv * a.X[(size_t)i * K + q];
         }
       }
-      SH(b, m - 1) = carry;
-      // back: U x = y
-      double x1 = 0.0, x2 = 0.0;
-      for (int i = m - 1; i >= 0; --i) {
-        double sv = SH(b, i) - SH(du, i) * x1 - SH(du2, i) * x2;
-        if (i == m - 1) sv = SH(b, i);
-        double xi = sv * SH(di, i);
-        SH(b, i) = xi;
-        x2 = x1;
-        x1 = xi;
+      __syncwarp();
+      // within the block, in member order
+      for (int q = 0; q < nact; ++q) {
+        if (lane == q) {
+          const double nrm = dot4(&SH(b, 0), w.tpb, &SH(b, 0), w.tpb, m);
+          const double inv = (nrm > 0.0) ? rcp64(sqrt(nrm)) : 0.0;
+          for (int i = 0; i < m; ++i) SH(b, i) *= inv;
+        }
+        __syncwarp();
+        if (act && lane > q) {
+          const double* bq = w.b + q;
+          const double dv = dot4(bq, w.tpb, &SH(b, 0), w.tpb, m);
+          for (int i = 0; i < m; ++i) SH(b, i) -= dv * bq[(size_t)i * w.tpb];
+        }
+        __syncwarp();
       }
-      for (int q = jj; q < jc; ++q) {
-        double dotv = 0.0;
-        for (int i = 0; i < m; ++i) dotv += a.X[(size_t)i * K + q] * SH(b, i);
-        for (int i = 0; i < m; ++i) SH(b, i) -= dotv * a.X[(size_t)i * K + q];
-      }
-      double nrm = 0.0;
-      for (int i = 0; i < m; ++i) nrm += SH(b, i) * SH(b, i);
-      double inv = (nrm > 0.0) ? rcp64(sqrt(nrm)) : 0.0;
-      for (int i = 0; i < m; ++i) SH(b, i) *= inv;
     }
-    double rqv = 0.0;
-    for (int i = 0; i < m; ++i) {
-      const double xi = SH(b, i);
-      double tx = a.d[i] * xi;
-      if (i > 0) tx += a.e[i - 1] * SH(b, i - 1);
-      if (i < m - 1) tx += a.e[i] * SH(b, i + 1);
-      rqv += xi * tx;
-      a.X[(size_t)i * K + jc] = xi;
-    }
-    a.rq[jc] = rqv;
+    if (act) invit_finish(a, j, w, t);
+    __syncwarp();
   }
-#undef SH
 }
+#undef SH
 
 // rank rule on the Rayleigh quotients of the candidates; the discarded weight is the
 // exact trace of T minus the kept eigenvalues.  Writes k and the full eigenvalue list.
@@ -1265,6 +1369,15 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   if (err != cudaSuccess) return err;
   InvArgs ia{d, e, lam32, m, kmax, X, rq, wb};
   invit_kernel<<<dim3((kmax + tpb - 1) / tpb, nb), tpb, shi, s>>>(ia);
+  // clusters: one warp each (a warp per candidate is launched; all but the clusters'
+  // first members return at once), as many members per pass as shared memory holds
+  {
+    const int per = (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024 - 64) / ((size_t)m * 41)));
+    const size_t shc = (size_t)per * m * 41 + 64;
+    err = allow_max_smem((const void*)invit_cluster_kernel);
+    if (err != cudaSuccess) return err;
+    invit_cluster_kernel<<<dim3(kmax, nb), 32, shc, s>>>(ia, per);
+  }
   // 4. rank rule on the refined eigenvalues
   rank_kernel<<<nb, 256, 0, s>>>(d, rq, lam32, m, kmax, (long long)max_bond, tol, floor_rel,
                                  k_dev, lam, wb);

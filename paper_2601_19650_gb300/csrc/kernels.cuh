@@ -174,6 +174,9 @@ template <typename T>
 cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om, int s,
                             int64_t lp_bs, int64_t om_bs, T* C, int64_t c_bs, cudaStream_t st,
                             int nb = 1);
+// G_b[i, i] += shift for i < m (nb matrices m*m elements apart)
+template <typename T>
+cudaError_t add_diagonal(T* G, int m, double shift, cudaStream_t s, int nb = 1);
 // dst_b[i] = src_b[i] for i < n, src_b = src + b * s_bs, dst_b = dst + b * d_bs
 template <typename T>
 cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n,

@@ -242,6 +242,16 @@ __global__ void scale_rows_kernel(T* X, int rows, int cols, int64_t bs, const do
   }
 }
 
+// G_b[i, i] += shift (real) for i < m, nb matrices m*m elements apart
+template <typename T>
+__global__ void add_diag_kernel(T* G, int m, double shift) {
+  G += (int64_t)blockIdx.y * m * m;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    T v = G[(int64_t)i * m + i];
+    G[(int64_t)i * m + i] = ops<T>::make(ops<T>::real(v) + shift, ops<T>::imag(v));
+  }
+}
+
 template <typename T>
 __global__ void copy_batched_kernel(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n) {
   src += (int64_t)blockIdx.y * s_bs;
@@ -474,6 +484,13 @@ cudaError_t scale_rows(T* X, int rows, int cols, int64_t bs, const double* norms
 }
 
 template <typename T>
+cudaError_t add_diagonal(T* G, int m, double shift, cudaStream_t s, int nb) {
+  note_launches(CBC_K_AUX, 1);
+  add_diag_kernel<T><<<dim3((m + 255) / 256, nb), 256, 0, s>>>(G, m, shift);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t copy_batched(const T* src, int64_t s_bs, T* dst, int64_t d_bs, int64_t n,
                          cudaStream_t s, int nb) {
   if (n <= 0) return cudaSuccess;
@@ -527,6 +544,7 @@ cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om
   template cudaError_t copy_batched<T>(const T*, int64_t, T*, int64_t, int64_t, cudaStream_t, \
                                        int);                                                 \
   template cudaError_t scale_rows<T>(T*, int, int, int64_t, const double*, cudaStream_t, int); \
+  template cudaError_t add_diagonal<T>(T*, int, double, cudaStream_t, int);                 \
   template cudaError_t sketch_contract<T>(const T*, int, int, int64_t, const T*, int, int64_t, \
                                           int64_t, T*, int64_t, cudaStream_t, int);
 CBC_MISC_INST(double)

@@ -144,7 +144,7 @@ cudaError_t tgemm(const Prec& pr, bool fwd, bool gram, int M, int N, int K, cons
 // ---- truncation of a fused leg (Sec. III A, text after Eq. (tt_cbc_first_contraction);
 // Sec. III B steps 1 and 2) --------------------------------------------------------------
 //
-// The paper compresses "for example via SVD".  Here the candidate directions come from the
+// The paper names an SVD as one way to compress.  Here the candidate directions come from the
 // Gram K = M M^H (or G = M^H M) and a Hermitian eigensolver, but the rank rule runs on
 // weights measured on M itself: w_j = ||u_j^H M||^2 (or ||M v_j||^2) and, in tolerance
 // mode, the exact weight outside the candidates ||M - U U^H M||_F^2.  A Gram holds the
@@ -266,7 +266,7 @@ int refine_level2(Arena& ar, const Prec& pr, const T* M, int m, int n, int kmax,
 
 template <typename T>
 int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars& sc,
-                    cudaStream_t s);
+                    cudaStream_t s, bool shifted = false);
 
 // Compression of the row leg of M (m x n, row-major): writes the k x n factor whose
 // Gram reproduces the rank-k truncation of M^H M, normalised, and returns k (and the
@@ -428,10 +428,14 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
 
 // S (m x n, row-major) -> Q with orthonormal rows spanning the row space of S, in place
 // (CholeskyQR2; Eq. (tt_cbc_qr_decomp) is the LQ on chi_{i-1}).  Used for m < n.
+// `shifted`: shifted CholeskyQR3 for S of any condition number (the first Cholesky
+// factors S S^H + sigma I with sigma = 11 (m n + m (m + 1)) u ||S||^2, u the Gram's
+// relative precision, which cannot break down and leaves a factor whose condition
+// number CholeskyQR2 then handles; Fukaya et al., shifted CholeskyQR).
 // (nb instances: S m*n elements apart.)
 template <typename T>
 int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars& sc,
-                    cudaStream_t s) {
+                    cudaStream_t s, bool shifted) {
   const int nb = pr.nb;
   const size_t mk = ar.mark();
   T* G = ar.get<T>((size_t)nb * m * m);
@@ -453,9 +457,15 @@ int lq_rows_inplace(Arena& ar, const Prec& pr, T* S, int m, int n, const Scalars
   // number, so it needs more of the product's bits than the contractions do
   Prec pg = pr;
   if (pr.cholqr_f64) pg.mixed = false;
-  for (int rep = 0; rep < 2; ++rep) {
+  for (int rep = 0; rep < (shifted ? 3 : 2); ++rep) {
     CK(tgemm<T>(pg, true, true, m, m, n, S, View::rowmajor(n, sbs), false, S,
                 View::transposed(n, sbs), true, G, View::rowmajor(m, (int64_t)m * m), s));
+    if (shifted && rep == 0) {
+      // rows of unit norm: ||S||_2^2 <= ||S||_F^2 = m; the slices' Gram carries ~2^-38
+      const double u = pg.mixed ? 3.637978807091713e-12 : 1.1102230246251565e-16;
+      const double shift = 11.0 * ((double)m * n + (double)m * (m + 1)) * u * m;
+      CK(add_diagonal<T>(G, m, shift, s, nb));
+    }
     KTimer t(CBC_K_CHOLQR, s, 0,
              nb * (ops<T>::cplx ? 4.0 : 1.0) * ((double)m * m * m / 3.0 + (double)m * m * n));
     CK(cholesky_lower<T>(G, m, sc.status, bar, num_sms(), s, nb));
@@ -650,28 +660,13 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     // B3: S[chi, (sigma' chi')] = sum_{(b a)} L^[i-1][chi, (b a)] Z[(b a), (sigma' chi')]
     const int n = d * cp;
     int m = c;
-    T* Lz = nullptr;  // Zip-Up, SRC: a factor whose rows span the kept subspace (then its LQ)
+    T* Lz = nullptr;  // Zip-Up: a factor whose rows span the kept subspace (then its LQ)
     if (i > 0 && o.method == kMethodSRC) {
       // SRC: the rows of the sketch that enter the LQ, the generic rank of the sketched
       // block (beyond it the block is rank deficient): min(s, prod_{k<i} d_k, a b)
       int64_t pl = 1;
       for (int q = 0; q < i && pl < c; ++q) pl *= st.phys[q];
       m = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)c, pl, (int64_t)a_in * b_in}));
-      if (m < n) {
-        // the new tensor is an orthonormal basis of the sketched block's rows; a sketch of a
-        // fast-decaying spectrum is too ill conditioned for CholeskyQR, so the rows first go
-        // through the rank-revealing compression (every direction above the rank floor
-        // kept), whose factor CholeskyQR2 then orthonormalises
-        T* Sk = tmp.get<T>((size_t)nb * m * n);
-        CKA(Sk);
-        CK(tgemm<T>(pr, false, false, m, n, b_in * a_in, env[i],
-                    View::rowmajor(b_in * a_in, (int64_t)c * b_in * a_in), false, Z,
-                    View::rowmajor(n, zbs), false, Sk, View::rowmajor(n, (int64_t)m * n), s));
-        int k = 0;
-        rc = compress_rows<T>(tmp, pr, Sk, m, n, m, 0.0, o, sc, s, &Lz, &k, nullptr, nullptr);
-        if (rc != CBC_OK) return rc;
-        m = k;
-      }
     } else if (i > 0 && o.method == kMethodZipUp) {
       // Zip-Up (Sec. III C): truncate the (sigma', chi') leg of Z[(b a), (sigma' chi')] at
       // once, by the rank rule on Z's singular values; the new tensor is an orthonormal row
@@ -727,7 +722,9 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
     }
     // B4: S = R Q on chi_{i-1}; Q^[i] is the new tensor
     if (m < n) {
-      rc = lq_rows_inplace<T>(tmp, pr, node, m, n, sc, s);
+      // SRC: the sketched block can be arbitrarily ill conditioned (a fast-decaying
+      // spectrum), so its LQ uses shifted CholeskyQR3
+      rc = lq_rows_inplace<T>(tmp, pr, node, m, n, sc, s, o.method == kMethodSRC);
       if (rc != CBC_OK) return rc;
     } else {  // more rows than columns: any unitary basis of the columns; take the identity
       CK(fill_identity<T>(node, n, s, nb));

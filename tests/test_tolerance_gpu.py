@@ -1,4 +1,4 @@
-"""Truncation by tolerance down to tol = 1e-8 (Sec. V "tolerance for the SVD"), and rank
+"""Truncation by tolerance down to tol = 1e-8 (the adaptive SVD tolerance of Sec. V), and rank
 floors, on the CUDA path against the FP64 oracle.
 
 At tol = 1e-8 a compression may discard a relative weight of only 1e-16, below what a
