@@ -1,4 +1,4 @@
-"""FP64 CPU oracle of two comparison methods of Sec. III C of arXiv 2601.19650, on chains.
+"""FP64 CPU oracle of three comparison methods of Sec. III C of arXiv 2601.19650, on chains.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/cbc.py``): only ``tests/`` and the CPU legs of
 ``bench.py`` import it.  Plain einsum / ``numpy.linalg`` transcriptions, shared with
@@ -16,6 +16,12 @@ nothing on the GPU path.
   in place of the truncated SVD), then a second sweep in which each new tensor is the
   orthonormal row basis (LQ) of the sketched block (Sec. III C).  The random matrices
   are inputs, so the GPU path and this oracle see the same ones.
+* ``direct_tt`` -- the direct method: contract operator and state into one MPS (bond
+  ``alpha beta`` on every edge), then compress it as a separate step: a QR sweep from the
+  first site makes every site but the last left-orthonormal, and a sweep of truncated SVDs
+  from the last site back to the first keeps the dominant right singular vectors of each
+  site (the Schmidt vectors of the current state, since the part to the left is
+  orthonormal) and passes the rest to the left.
 
 Readings (listed with their reasons in the design notes):
 
@@ -130,3 +136,40 @@ def src_tt(state: List[np.ndarray], op: List[np.ndarray], omega: List[np.ndarray
     out[L - 1] = out[L - 1][..., 0]
     bonds = [1] + [int(out[i].shape[0]) for i in range(1, L)]
     return CBCResult(out, [], [int(c.shape[0]) for c in C], bonds, C)
+
+
+def direct_tt(state: List[np.ndarray], op: List[np.ndarray], max_bond: int = 0,
+              tol: float = 0.0, eps_rank: float = EPS_RANK) -> CBCResult:
+    """The direct method on a chain (Sec. III C): contract, then compress by a QR sweep
+    (first site to last) and a truncating SVD sweep (last site to first), CBC's rank rule
+    on each Schmidt spectrum."""
+    T, W = _as_tt(state, op)
+    L = len(T)
+    dt = T[0].dtype
+    # 1. the product MPS: N_i[(alpha beta), sigma', (alpha' beta')]
+    N = []
+    for i in range(L):
+        t = np.einsum("asA,bPsB->abPAB", T[i], W[i], optimize=True)
+        a, b, d, A, B = t.shape
+        N.append(t.reshape(a * b, d, A * B))
+    # 2. left-orthonormal sites 0 .. L-2 (QR), the remainder pushed to the right
+    for i in range(L - 1):
+        l, d, r = N[i].shape
+        Q, R = np.linalg.qr(N[i].reshape(l * d, r), mode="reduced")
+        N[i] = Q.reshape(l, d, -1)
+        N[i + 1] = np.einsum("xr,rPy->xPy", R, N[i + 1], optimize=True)
+    # 3. truncating SVDs from the last site to the first
+    out: List[Optional[np.ndarray]] = [None] * L
+    cuts: List[CutInfo] = []
+    for i in range(L - 1, 0, -1):
+        l, d, r = N[i].shape
+        U, s, Vh = np.linalg.svd(N[i].reshape(l, d * r), full_matrices=False)
+        k = choose_rank(s, max_bond, tol, eps_rank)
+        cuts.append(CutInfo(s, k))
+        out[i] = Vh[:k].reshape(k, d, r)
+        N[i - 1] = np.einsum("xPl,lk->xPk", N[i - 1], U[:, :k] * s[:k], optimize=True)
+    out[0] = N[0]                                       # (1, sigma', chi_1)
+    out[L - 1] = out[L - 1][..., 0]
+    bonds = [1] + [int(out[i].shape[0]) for i in range(1, L)]
+    return CBCResult(out, cuts, bonds[1:], bonds)
+

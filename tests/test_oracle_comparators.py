@@ -189,9 +189,58 @@ def check_src_keeps_sketched_row_space(mod):
             P_right = P
 
 
+# ---- direct (contract, then QR and SVD sweeps) -------------------------------------------
+def _run_direct(mod, p, max_bond=None):
+    return mod.direct_tt(p.state.tensors, p.op.tensors,
+                         p.max_bond if max_bond is None else max_bond)
+
+
+def check_direct_exact(mod):
+    _exact(lambda p: _run_direct(mod, p, 10 ** 6))
+
+
+def check_direct_projection(mod):
+    _projection_and_isometries(lambda p: _run_direct(mod, p))
+
+
+def check_direct_first_cut_is_optimal(mod):
+    """The first truncation (the last edge) sees O|psi> with an orthonormal left part: it
+    keeps the dominant right Schmidt vectors of the brute-force O|psi> across that edge."""
+    for p in _cases():
+        r = _run_direct(mod, p)
+        L = len(r.tensors)
+        H = _hpsi_unfolded(p, L - 1)
+        k = r.tensors[L - 1].shape[0]
+        u, s, vh = np.linalg.svd(H, full_matrices=False)
+        if k < s.size and (s[k - 1] - s[k]) < 1e-8 * s[0]:
+            continue
+        q = r.tensors[L - 1].reshape(k, -1)
+        e = np.abs(q.conj().T @ q - vh[:k].conj().T @ vh[:k]).max()
+        assert e < 1e-9, (p.name, e)
+
+
+def check_direct_sequential_bound(mod):
+    """Sequential SVD truncation with orthonormal left parts: ||O psi - psi'||^2 is at most
+    the sum over the edges of the weight that the best approximation of the same bond
+    discards on that edge (each step's discarded weight is at most that edge's
+    Eckart-Young tail of O|psi>)."""
+    for p in _cases():
+        r = _run_direct(mod, p)
+        ex = brute.apply_dense(p.state.parent, p.state.tensors, p.op.tensors)
+        got = brute.dense_state(p.state.parent, r.tensors)
+        L = len(r.tensors)
+        bound2 = 0.0
+        for i in range(1, L):
+            s = np.linalg.svd(_hpsi_unfolded(p, i), compute_uv=False)
+            bound2 += float(np.sum(s[r.out_bonds[i]:] ** 2))
+        err2 = float(np.linalg.norm(ex - got) ** 2)
+        assert err2 <= bound2 * (1 + 1e-9) + 1e-24, (p.name, err2, bound2)
+
+
 CHECKS = [check_zipup_exact, check_zipup_projection, check_zipup_keeps_best_local_subspace,
           check_src_exact, check_src_projection, check_src_sketch_is_khatri_rao,
-          check_src_keeps_sketched_row_space]
+          check_src_keeps_sketched_row_space, check_direct_exact, check_direct_projection,
+          check_direct_first_cut_is_optimal, check_direct_sequential_bound]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=lambda c: c.__name__)
@@ -212,6 +261,13 @@ MUTATIONS = {
                                   'C.append(np.einsum("jPAB,Pk->kAB", Lp, Om, optimize=True))'),
     "src-rank-ignores-left-dimension": ("return max(1, min(s, p_left, a * b))",
                                         "return max(1, min(s, a * b))"),
+    "direct-remainder-not-pushed": ('        N[i + 1] = np.einsum("xr,rPy->xPy", R, N[i + 1], optimize=True)\n',
+                                    '        pass\n'),
+    "direct-carry-without-singular-values": ('N[i - 1] = np.einsum("xPl,lk->xPk", N[i - 1], U[:, :k] * s[:k], optimize=True)',
+                                             'N[i - 1] = np.einsum("xPl,lk->xPk", N[i - 1], U[:, :k], optimize=True)'),
+    "direct-keeps-smallest": ('out[i] = Vh[:k].reshape(k, d, r)', 'out[i] = Vh[-k:].reshape(k, d, r)'),
+    "direct-operator-in-out-swapped": ('t = np.einsum("asA,bPsB->abPAB", T[i], W[i], optimize=True)',
+                                       't = np.einsum("asA,bsPB->abPAB", T[i], W[i], optimize=True)'),
     "src-R-update-drops-conj": ('R = np.einsum("yPx,abPx->yab", Q.conj(), Z, optimize=True)\n    out[L - 1] = out[L - 1][..., 0]\n    bonds = [1] + [int(out[i].shape[0]) for i in range(1, L)]\n    return CBCResult(out, [], ',
                                 'R = np.einsum("yPx,abPx->yab", Q, Z, optimize=True)\n    out[L - 1] = out[L - 1][..., 0]\n    bonds = [1] + [int(out[i].shape[0]) for i in range(1, L)]\n    return CBCResult(out, [], '),
 }
