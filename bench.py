@@ -218,9 +218,10 @@ def blas_threads() -> int:
 
 def run_sweep(args, local):
     """Error against runtime of one application of the paper's benchmark MPS/MPO (Sec. IV A)
-    for max_bond = 2, 4, ..., 40, in both precisions, for CBC and for the two comparison
-    methods of Sec. III C built here (Zip-Up with the same cap, SRC with sketch width
-    s = max_bond and seeded Gaussian random matrices).  The error is ||O psi - psi'|| /
+    for max_bond = 2, 4, ..., 40, in both precisions, for CBC and for the comparison methods
+    of Sec. III C built here (Zip-Up with the same cap, SRC with sketch width s = max_bond and
+    seeded Gaussian random matrices, the direct method at max_bond 4, 20 and 40 in the mixed
+    path, one timed run).  The error is ||O psi - psi'|| /
     ||O psi|| from ||O psi||^2 (one exact FP64 sandwich contraction, the oracle's
     chain_applied_norm2), ||psi'||^2 and the overlap <psi'|O psi> (chain_applied_overlap);
     its floor is ~1e-8 (FP64 cancellation in the sum of the three)."""
@@ -248,6 +249,8 @@ def run_sweep(args, local):
             return _cbc.cbc_apply(hs, ho, mb, 0.0, opt)
         if method == "zipup":
             return _cbc.zipup_apply(hs, ho, mb, 0.0, opt)
+        if method == "direct":
+            return _cbc.direct_apply(hs, ho, mb, 0.0, opt)
         return _cbc.src_apply(hs, ho, mb, om, opt)
 
     rows = []
@@ -255,14 +258,21 @@ def run_sweep(args, local):
         row = {"max_bond": mb}
         om = sketch_matrices(st.phys, mb, seed=0, cplx=True)
         for method in methods:
-            for name, prec in (("mixed", _cbc.CBC_PREC_MIXED), ("fp64", _cbc.CBC_PREC_FP64)):
+            # the direct method contracts to bond D_S D_O = 1600 first (~6 GB, seconds per
+            # application): a few bonds only
+            if method == "direct" and mb not in (4, 20, 40):
+                continue
+            precs = (("mixed", _cbc.CBC_PREC_MIXED), ("fp64", _cbc.CBC_PREC_FP64))
+            if method == "direct":
+                precs = precs[:1]
+            for name, prec in precs:
                 key = name if method == "cbc" else f"{method}_{name}"
                 opt = _cbc.make_options(prec)
                 try:
                     _cbc.ttn_destroy(apply(method, opt, mb, om))  # warm-up
                     times = []
                     out = None
-                    for _ in range(3):
+                    for _ in range(1 if method == "direct" else 3):
                         torch.cuda.synchronize()
                         e0 = torch.cuda.Event(enable_timing=True)
                         e1 = torch.cuda.Event(enable_timing=True)
@@ -298,6 +308,7 @@ def run_sweep(args, local):
             "unit": "ms per application",
             "n_gpus": 1, "data": "synthetic", "dtype": "bf16-slices+f64 | f64",
             "config": dict(WORKLOADS["paper"], seed=0, methods=methods,
+                           direct_bonds=[4, 20, 40],
                            src_sketch="s = max_bond, Gaussian (x+iy)/sqrt(2), seed 0"),
             "norm_note": f"||O psi||^2 by an exact FP64 sandwich contraction on the host "
                          f"({t_norm:.1f} s), <psi'|O psi> likewise per result; errors below "
@@ -356,8 +367,8 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="error-vs-runtime sweep of the paper's benchmark (max_bond 2..40) "
                          "instead of the throughput step; prints one line of rows")
-    ap.add_argument("--sweep-methods", default="cbc,zipup,src",
-                    help="methods of --sweep (comma separated: cbc, zipup, src)")
+    ap.add_argument("--sweep-methods", default="cbc,zipup,src,direct",
+                    help="methods of --sweep (comma separated: cbc, zipup, src, direct)")
     ap.add_argument("--tol", type=float, default=0.0,
                     help="truncation tolerance of every compression besides max_bond (Sec. V; "
                          "the large workload's second run uses 1e-8)")

@@ -152,7 +152,7 @@ int cbc_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
 int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64_t* max_bond,
                       const double* tol, const cbc_options* opt, int workers, ttn_t* outs);
 
-/* Zip-Up (Sec. III C, "Other Compression Methods"): a comparison method that applies op
+/* Zip-Up (Sec. III C): a comparison method that applies op
  * to state and compresses in a single sweep over the sites, truncating each bond as soon
  * as the site is contracted, with only the already compressed part in view.  Tensor
  * trains only (parent[i] = i - 1).  The sweep runs from the last site to site 0: at site
@@ -165,6 +165,19 @@ int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64
  * ttn_get_info's discarded weights are those of Z at each edge.                      */
 int zipup_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
                 const cbc_options* opt, ttn_t* out);
+
+/* The direct method (Sec. III C): a comparison method that
+ * contracts op and state into one MPS (bond alpha_i beta_i on every edge) and compresses it
+ * as a separate step.  Tensor trains only.  A QR sweep from site 0 makes sites 0 .. L-2
+ * left-orthonormal (shifted CholeskyQR3 on the GPU), then a sweep from the last site to
+ * site 0 truncates every edge by the rank rule of cbc_apply (max_bond, tol) on the Schmidt
+ * values of the current state and keeps an orthonormal basis of the dominant right
+ * singular vectors.  The product MPS holds d_i (alpha beta)^2 elements per site, so this
+ * method needs far more memory than CBC.  Output layout, ownership, options, stream use
+ * and errors as cbc_apply; CBC_ERR_UNSUPPORTED for a tree; ttn_get_info's discarded
+ * weights are those of the truncating sweep.                                        */
+int direct_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
+                 const cbc_options* opt, ttn_t* out);
 
 /* Successive randomised compression, SRC (Sec. III C): a comparison method whose first
  * sweep contracts the network with one random matrix per site (d_i x s, joined across

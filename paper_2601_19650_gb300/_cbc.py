@@ -66,6 +66,7 @@ def lib():
         L.ttno_create.argtypes = create_args
         L.cbc_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
         L.zipup_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
+        L.direct_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
         L.src_apply.argtypes = [vp, vp, i64, P(vp), ctypes.c_int, ctypes.c_int, P(cbc_options),
                                 P(vp)]
         L.ttn_get_info.argtypes = [vp, P(i32), P(i64), P(dbl), P(dbl)]
@@ -101,7 +102,8 @@ def lib():
         L.cbc_last_error.restype = ctypes.c_char_p
         L.cbc_last_error.argtypes = []
         for f in ("ttn_create", "ttno_create", "cbc_apply", "ttn_get_info", "ttn_get_node",
-                  "ttn_get_network", "ttn_destroy", "ttno_destroy", "zipup_apply", "src_apply"):
+                  "ttn_get_network", "ttn_destroy", "ttno_destroy", "zipup_apply", "src_apply",
+                  "direct_apply"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -176,6 +178,15 @@ def zipup_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options]
     out = ctypes.c_void_p()
     _check(lib().zipup_apply(state, op, int(max_bond), float(tol),
                              ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
+    return out
+
+
+def direct_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options] = None):
+    """Direct method (contract, then QR and SVD sweeps; tensor trains); arguments and output
+    as cbc_apply."""
+    out = ctypes.c_void_p()
+    _check(lib().direct_apply(state, op, int(max_bond), float(tol),
+                              ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
     return out
 
 

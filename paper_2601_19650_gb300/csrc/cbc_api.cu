@@ -440,6 +440,20 @@ int zipup_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_
   return run_method(state, op, max_bond, tol, o, out);
 }
 
+int direct_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol, const cbc_options* opt,
+                 ttn_t* out) {
+  if (!out) return fail(CBC_ERR_INVALID_ARG, "direct_apply: out is NULL");
+  *out = nullptr;
+  int rc = check_chain_pair(state, op, "direct_apply");
+  if (rc != CBC_OK) return rc;
+  if (!std::isfinite(tol)) return fail(CBC_ERR_INVALID_ARG, "direct_apply: tol is not finite");
+  Options o;
+  rc = parse_options(opt, &o);
+  if (rc != CBC_OK) return rc;
+  o.method = kMethodDirect;
+  return run_method(state, op, max_bond, tol, o, out);
+}
+
 int src_apply(ttn_t state, ttno_t op, int64_t sketch_size, const void* const* omega,
               int omega_dtype, int omega_on_device, const cbc_options* opt, ttn_t* out) {
   if (!out) return fail(CBC_ERR_INVALID_ARG, "src_apply: out is NULL");

@@ -914,28 +914,17 @@ __global__ void invit_kernel(InvArgs a) {
   invit_finish(a, jj, w, t);
 }
 
-// A cluster of candidates (neighbours closer than 1e-4 of the spectral radius) by one
-// warp: `per` members at a time, one per lane, iterated as a block (block inverse
+// The clusters of candidates (runs of neighbours closer than 1e-4 of the spectral radius),
+// each by one warp: `per` members at a time, one per lane, iterated as a block (block inverse
 // iteration): every lane solves with its own shift (shifts at least 1e-10 span apart),
 // then the block is orthonormalised (modified Gram-Schmidt, lanes in parallel) against
 // the cluster's finished columns and within itself, four times.  The vectors then span
 // the invariant subspace of the cluster's eigenvalues (any basis of it is a valid set of
 // eigenvectors when they are not resolved individually).
-__global__ void invit_cluster_kernel(InvArgs a, int per) {
-  extern __shared__ double shd[];
-  invit_shift(a);
+// one cluster [jj, cend) by the warp, `per` members per pass
+__device__ void invit_cluster(const InvArgs& a, const InvSmem& w, int jj, int cend, int per,
+                              double span, double tiny) {
   const int m = a.m, K = a.kmax, lane = threadIdx.x;
-  const InvSmem w(shd, m, per);
-  const int jj = blockIdx.x;
-  if (jj >= K) return;
-  const double span = invit_span(a);
-  const double ortol = 1e-4 * span;
-  // the first member of a cluster of two or more leads it
-  if (jj > 0 && close_pair(a, jj - 1, ortol)) return;
-  if (!(jj + 1 < K && close_pair(a, jj, ortol))) return;
-  int cend = jj + 2;
-  while (cend < K && close_pair(a, cend - 1, ortol)) ++cend;
-  const double tiny = 2.220446049250313e-16 * span;
   for (int j0 = jj; j0 < cend; j0 += per) {
     const int nact = min(per, cend - j0);
     const bool act = lane < nact;
@@ -976,6 +965,30 @@ __global__ void invit_cluster_kernel(InvArgs a, int per) {
     }
     if (act) invit_finish(a, j, w, t);
     __syncwarp();
+  }
+}
+
+__global__ void invit_cluster_kernel(InvArgs a, int per) {
+  extern __shared__ double shd[];
+  invit_shift(a);
+  const int K = a.kmax;
+  const InvSmem w(shd, a.m, per);
+  const double span = invit_span(a);
+  const double ortol = 1e-4 * span;
+  const double tiny = 2.220446049250313e-16 * span;
+  // CTA c takes clusters c, c + gridDim.x, ... in order (a cluster: a run of two or more
+  // candidates whose neighbours are close); every lane scans the same candidates
+  int cidx = -1;
+  for (int jj = 0; jj + 1 < K;) {
+    if (!close_pair(a, jj, ortol)) {
+      ++jj;
+      continue;
+    }
+    int cend = jj + 2;
+    while (cend < K && close_pair(a, cend - 1, ortol)) ++cend;
+    ++cidx;
+    if (cidx % (int)gridDim.x == (int)blockIdx.x) invit_cluster(a, w, jj, cend, per, span, tiny);
+    jj = cend;
   }
 }
 #undef SH
@@ -1369,14 +1382,14 @@ cudaError_t heev_top(T* A, int m, int kmax, int64_t max_bond, double tol, double
   if (err != cudaSuccess) return err;
   InvArgs ia{d, e, lam32, m, kmax, X, rq, wb};
   invit_kernel<<<dim3((kmax + tpb - 1) / tpb, nb), tpb, shi, s>>>(ia);
-  // clusters: one warp each (a warp per candidate is launched; all but the clusters'
-  // first members return at once), as many members per pass as shared memory holds
-  {
+  // clusters: one warp each, four CTAs per matrix that share its clusters round robin, as
+  // many members per pass as shared memory holds
+  if (kmax >= 2) {
     const int per = (int)std::max<size_t>(1, std::min<size_t>(32, (200 * 1024 - 64) / ((size_t)m * 41)));
     const size_t shc = (size_t)per * m * 41 + 64;
     err = allow_max_smem((const void*)invit_cluster_kernel);
     if (err != cudaSuccess) return err;
-    invit_cluster_kernel<<<dim3(kmax, nb), 32, shc, s>>>(ia, per);
+    invit_cluster_kernel<<<dim3(std::min(4, kmax / 2), nb), 32, shc, s>>>(ia, per);
   }
   // 4. rank rule on the refined eigenvalues
   rank_kernel<<<nb, 256, 0, s>>>(d, rq, lam32, m, kmax, (long long)max_bond, tol, floor_rel,

@@ -174,6 +174,9 @@ template <typename T>
 cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om, int s,
                             int64_t lp_bs, int64_t om_bs, T* C, int64_t c_bs, cudaStream_t st,
                             int nb = 1);
+// out (cols x rows, row-major) = the conjugate transpose of in (rows x cols, row-major)
+template <typename T>
+cudaError_t adjoint_copy(const T* in, int rows, int cols, T* out, cudaStream_t s);
 // G_b[i, i] += shift for i < m (nb matrices m*m elements apart)
 template <typename T>
 cudaError_t add_diagonal(T* G, int m, double shift, cudaStream_t s, int nb = 1);

@@ -242,6 +242,17 @@ __global__ void scale_rows_kernel(T* X, int rows, int cols, int64_t bs, const do
   }
 }
 
+// out[c, r] = conj(in[r, c]) (in: rows x cols, out: cols x rows, both row-major)
+template <typename T>
+__global__ void adjoint_kernel(const T* in, int rows, int cols, T* out) {
+  const int64_t total = (int64_t)rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / cols, c = t % cols;
+    out[c * rows + r] = ops<T>::conj(in[t]);
+  }
+}
+
 // G_b[i, i] += shift (real) for i < m, nb matrices m*m elements apart
 template <typename T>
 __global__ void add_diag_kernel(T* G, int m, double shift) {
@@ -484,6 +495,14 @@ cudaError_t scale_rows(T* X, int rows, int cols, int64_t bs, const double* norms
 }
 
 template <typename T>
+cudaError_t adjoint_copy(const T* in, int rows, int cols, T* out, cudaStream_t s) {
+  if ((int64_t)rows * cols <= 0) return cudaSuccess;
+  note_launches(CBC_K_AUX, 1);
+  adjoint_kernel<T><<<grid_for((int64_t)rows * cols), 256, 0, s>>>(in, rows, cols, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t add_diagonal(T* G, int m, double shift, cudaStream_t s, int nb) {
   note_launches(CBC_K_AUX, 1);
   add_diag_kernel<T><<<dim3((m + 255) / 256, nb), 256, 0, s>>>(G, m, shift);
@@ -545,6 +564,7 @@ cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om
                                        int);                                                 \
   template cudaError_t scale_rows<T>(T*, int, int, int64_t, const double*, cudaStream_t, int); \
   template cudaError_t add_diagonal<T>(T*, int, double, cudaStream_t, int);                 \
+  template cudaError_t adjoint_copy<T>(const T*, int, int, T*, cudaStream_t);               \
   template cudaError_t sketch_contract<T>(const T*, int, int, int64_t, const T*, int, int64_t, \
                                           int64_t, T*, int64_t, cudaStream_t, int);
 CBC_MISC_INST(double)

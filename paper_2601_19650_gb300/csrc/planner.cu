@@ -755,9 +755,178 @@ int run_tt_group(const std::vector<const Net*>& sts, const std::vector<const Net
 }
 
 template <typename T>
+int run_tt_direct(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
+                  Net* out);
+
+template <typename T>
 int run_tt(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
            Net* out) {
+  if (o.method == kMethodDirect) return run_tt_direct<T>(st, op, max_bond, tol, o, out);
   return run_tt_group<T>({&st}, {&op}, max_bond, tol, o, {out});
+}
+
+// ---- the direct method (Sec. III C, a comparator): contract, then compress ------------
+// 1. the product MPS N_i[(a b), sigma', (a' b')] = sum_sigma T[a, sigma, a'] W[b, sigma',
+//    sigma, b'] (one GEMM with K = d per site, written through strided views);
+// 2. sites 0 .. L-2 left-orthonormal: a tall site X (rows (l sigma') > columns r) by
+//    shifted CholeskyQR3 of X^H (Q^H with orthonormal rows), R = Q^H X pushed into the next
+//    site; a site that is not tall keeps the identity and passes X on whole (the reduced QR
+//    then has min(l d, r) = l d columns, and any unitary gives the same state);
+// 3. sites L-1 .. 1: the truncation of M = N_i[l, (sigma' r)] (compress_rows: CBC's rank
+//    rule on M's singular values, which are Schmidt values since the left part is
+//    orthonormal), the new tensor an orthonormal row basis of the kept subspace (LQ), the
+//    carry M Q^H multiplied into site i-1.
+template <typename T>
+int run_tt_direct(const Net& st, const Net& op, int64_t max_bond, double tol, const Options& o,
+                  Net* out) {
+  cudaStream_t s = st.stream;
+  const int L = st.n;
+  Arena ar(s);   // the product MPS and scalars: the whole call
+  Arena tmp(s);  // per-step temporaries
+  int* d_int = ar.get<int>(4);
+  double* d_dbl = ar.get<double>(4);
+  CKA(d_int); CKA(d_dbl);
+  CK(cudaMemsetAsync(d_int, 0, 4 * sizeof(int), s));
+  CK(cudaMemsetAsync(d_dbl, 0, 4 * sizeof(double), s));
+  Scalars sc{d_int, d_int + 1, d_dbl, d_dbl + 1, d_dbl + 2};
+  Prec pr;
+  pr.mixed = (o.precision == CBC_PREC_MIXED);
+  pr.cholqr_f64 = o.cholqr_f64;
+  pr.s_fwd = o.slices_fwd;
+  pr.s_bwd = o.slices_bwd;
+  pr.ar = &tmp;
+  pr.status = sc.status;
+  pr.nb = 1;
+  auto sb = [&](int i) { return i < L ? (int)st.bond[i] : 1; };
+  auto ob = [&](int i) { return i < L ? (int)op.bond[i] : 1; };
+  out->kind = 0;
+  out->n = L;
+  out->root = 0;
+  out->parent = st.parent;
+  out->phys = st.phys;
+  out->bond.assign(L, 1);
+  out->children = st.children;
+  out->cplx = st.cplx;
+  out->stream = s;
+  out->data.assign(L, nullptr);
+  out->numel.assign(L, 0);
+  out->discarded.assign(L, 0.0);
+  // 1. product MPS
+  std::vector<T*> N(L, nullptr);
+  std::vector<int> lb(L), rb(L);  // left / right bond of N_i
+  for (int i = 0; i < L; ++i) {
+    const int a = sb(i), b = ob(i), d = (int)st.phys[i], A = sb(i + 1), B = ob(i + 1);
+    lb[i] = a * b;
+    rb[i] = A * B;
+    N[i] = ar.get<T>((size_t)a * b * d * A * B);
+    CKA(N[i]);
+    // C[(a a'), (b sigma' b')] = T'[(a a'), sigma] W'[sigma, (b sigma' b')]
+    View vt;
+    vt.rows2(A, (int64_t)d * A, 1);
+    vt.cs_in = A;
+    View vw;
+    vw.rs_in = B;
+    vw.cols2(B, (int64_t)d * B, 1);  // (b sigma') has stride d B: the b stride d^2 B is d times it
+    View vn;
+    vn.rows2(A, (int64_t)b * d * A * B, B);
+    vn.cols2(B, (int64_t)A * B, 1);
+    CK(tgemm<T>(pr, false, false, a * A, b * d * B, d, static_cast<const T*>(st.data[i]), vt,
+                false, static_cast<const T*>(op.data[i]), vw, false, N[i], vn, s));
+  }
+  // 2. left-orthonormal sites 0 .. L-2
+  for (int i = 0; i + 1 < L; ++i) {
+    const int d = (int)st.phys[i], p = lb[i] * d, r = rb[i];
+    const int d2 = (int)st.phys[i + 1], r2 = rb[i + 1];
+    const size_t mk = tmp.mark();
+    T* Rm = nullptr;  // what the next site absorbs: R (r x r) or X itself (p x r)
+    int nr = 0;       // its row count, the new bond
+    if (p > r) {
+      T* Sx = tmp.get<T>((size_t)r * p);
+      Rm = tmp.get<T>((size_t)r * r);
+      CKA(Sx); CKA(Rm);
+      CK(adjoint_copy<T>(N[i], p, r, Sx, s));
+      int rc = lq_rows_inplace<T>(tmp, pr, Sx, r, p, sc, s, true);
+      if (rc != CBC_OK) return rc;
+      // R = Q^H X, then X := Q
+      CK(tgemm<T>(pr, false, false, r, r, p, Sx, View::rowmajor(p), false, N[i], View::rowmajor(r),
+                  false, Rm, View::rowmajor(r), s));
+      CK(adjoint_copy<T>(Sx, r, p, N[i], s));
+      nr = r;
+    } else {
+      Rm = tmp.get<T>((size_t)p * r);
+      CKA(Rm);
+      CK(cudaMemcpyAsync(Rm, N[i], sizeof(T) * (size_t)p * r, cudaMemcpyDeviceToDevice, s));
+      CK(fill_identity<T>(N[i], p, s));
+      nr = p;
+    }
+    T* Nn = ar.get<T>((size_t)nr * d2 * r2);
+    CKA(Nn);
+    CK(tgemm<T>(pr, false, false, nr, d2 * r2, r, Rm, View::rowmajor(r), false, N[i + 1],
+                View::rowmajor(d2 * r2), false, Nn, View::rowmajor(d2 * r2), s));
+    CK(normalize_inplace<T>(Nn, (int64_t)nr * d2 * r2, sc.log_out, sc.status, sc.scratch, s));
+    ar.drop(N[i + 1]);
+    N[i + 1] = Nn;
+    rb[i] = nr;
+    lb[i + 1] = nr;
+    tmp.release(mk);
+  }
+  // 3. truncating sweep, last site to first
+  for (int i = L - 1; i >= 1; --i) {
+    const int l = lb[i], d = (int)st.phys[i], n = d * rb[i];
+    const size_t mk = tmp.mark();
+    T* Lk = nullptr;
+    int k = 0;
+    double disc = 0.0;
+    int rc = compress_rows<T>(tmp, pr, N[i], l, n, max_bond, tol, o, sc, s, &Lk, &k, nullptr, &disc);
+    if (rc != CBC_OK) return rc;
+    out->discarded[i] = disc;
+    T* q = nullptr;
+    CK(pool_malloc(reinterpret_cast<void**>(&q), sizeof(T) * (size_t)k * n, s));
+    out->data[i] = q;
+    out->numel[i] = (int64_t)k * n;
+    out->bond[i] = k;
+    if (k < n) {
+      CK(cudaMemcpyAsync(q, Lk, sizeof(T) * (size_t)k * n, cudaMemcpyDeviceToDevice, s));
+      rc = lq_rows_inplace<T>(tmp, pr, q, k, n, sc, s);
+      if (rc != CBC_OK) return rc;
+    } else {
+      CK(fill_identity<T>(q, n, s));
+    }
+    // carry C = M Q^H (l x k), then N_{i-1} := N_{i-1} C
+    T* Cc = tmp.get<T>((size_t)l * k);
+    CKA(Cc);
+    CK(tgemm<T>(pr, false, false, l, k, n, N[i], View::rowmajor(n), false, q, View::transposed(n),
+                true, Cc, View::rowmajor(k), s));
+    const int pl = lb[i - 1] * (int)st.phys[i - 1];
+    T* Np = ar.get<T>((size_t)pl * k);
+    CKA(Np);
+    CK(tgemm<T>(pr, false, false, pl, k, l, N[i - 1], View::rowmajor(l), false, Cc,
+                View::rowmajor(k), false, Np, View::rowmajor(k), s));
+    CK(normalize_inplace<T>(Np, (int64_t)pl * k, sc.log_out, sc.status, sc.scratch, s));
+    ar.drop(N[i - 1]);
+    ar.drop(N[i]);
+    N[i - 1] = Np;
+    rb[i - 1] = k;
+    tmp.release(mk);
+  }
+  // the first site: N_0 (1, sigma', chi_1), normalised
+  {
+    const int64_t n0 = (int64_t)lb[0] * st.phys[0] * rb[0];
+    CK(normalize_inplace<T>(N[0], n0, sc.log_out, sc.status, sc.scratch, s));
+    T* q = nullptr;
+    CK(pool_malloc(reinterpret_cast<void**>(&q), sizeof(T) * (size_t)n0, s));
+    CK(cudaMemcpyAsync(q, N[0], sizeof(T) * (size_t)n0, cudaMemcpyDeviceToDevice, s));
+    out->data[0] = q;
+    out->numel[0] = n0;
+  }
+  int hs = 0;
+  double hl = 0.0;
+  CK(cudaMemcpyAsync(&hs, sc.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&hl, sc.log_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (hs != 0) return status_to_rc(hs);
+  out->log_norm = hl;
+  return CBC_OK;
 }
 
 // ---- trees (Sec. III B) ---------------------------------------------------------------

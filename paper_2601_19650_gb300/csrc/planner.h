@@ -31,7 +31,7 @@ struct Net {
   virtual ~Net();
 };
 
-enum { kMethodCBC = 0, kMethodZipUp = 1, kMethodSRC = 2 };
+enum { kMethodCBC = 0, kMethodZipUp = 1, kMethodSRC = 2, kMethodDirect = 3 };
 
 struct Options {
   int precision = CBC_PREC_FP64;

@@ -77,6 +77,8 @@ def test_library_loads_and_rejects_bad_arguments(libpath):
     # the comparison methods check their handles before any device work
     assert L.zipup_apply(None, None, 4, 0.0, None, ctypes.byref(out)) == 1
     assert "zipup_apply" in _cbc.cbc_last_error() and out.value is None
+    assert L.direct_apply(None, None, 4, 0.0, None, ctypes.byref(out)) == 1
+    assert "direct_apply" in _cbc.cbc_last_error() and out.value is None
     assert L.src_apply(None, None, 4, None, 1, 0, None, ctypes.byref(out)) == 1
     assert "src_apply" in _cbc.cbc_last_error() and out.value is None
 

@@ -1,6 +1,6 @@
-"""GPU parity of the comparison methods of Sec. III C (Zip-Up, SRC) against their oracle.
+"""GPU parity of the comparison methods of Sec. III C (Zip-Up, SRC, direct) against their oracle.
 
-Both run through the C ABI (zipup_apply, src_apply) on the same seeded inputs as the
+They run through the C ABI (zipup_apply, src_apply, direct_apply) on the same seeded inputs as the
 oracle; SRC gets the same random matrices.  Bars: FP64 path <= 1e-10, mixed <= 1e-6
 (relative 2-norm distance of the output states, oracle.metrics.rel_err); bonds equal.
 """
@@ -25,6 +25,8 @@ def _run(method, p, precision, arg):
         opt = _cbc.make_options(precision)
         if method == "zipup":
             out = _cbc.zipup_apply(hs, ho, arg[0], arg[1], opt)
+        elif method == "direct":
+            out = _cbc.direct_apply(hs, ho, arg[0], arg[1], opt)
         else:
             out = _cbc.src_apply(hs, ho, arg[0], arg[1], opt)
         try:
@@ -110,6 +112,40 @@ def test_src_matches_oracle(case, precision, bar):
     assert e <= bar, e
 
 
+DIRECT_CASES = [
+    dict(config=1, max_bond=16), dict(config=1, max_bond=3),
+    dict(config=2, L=7, chi=8, D=3, max_bond=5, dtype=np.complex128, seed=3),
+    dict(config=2, L=5, chi=5, D=2, d=3, max_bond=4, dtype=np.complex128, seed=2),
+    dict(config=2, L=12, chi=32, D=4, max_bond=24, seed=1),
+    dict(config=2, L=10, chi=32, D=8, max_bond=32, seed=4),
+    dict(config=2, L=1, chi=4, D=2, max_bond=4, dtype=np.complex128),
+]
+
+
+@pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
+@pytest.mark.parametrize("case", DIRECT_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()
+                                                                      if k != "dtype"))
+def test_direct_matches_oracle(case, precision, bar):
+    case = dict(case)
+    cfg = case.pop("config")
+    p = make_problem(cfg, **case)
+    (got, bonds, log_norm), disc = _run("direct", p, precision, (p.max_bond, 0.0))
+    ref = comparators.direct_tt(p.state.tensors, p.op.tensors, p.max_bond)
+    assert list(bonds) == list(ref.out_bonds), (bonds, ref.out_bonds)
+    e = metrics.rel_err(p.state.parent, got, ref.tensors, log_norm, 0.0)
+    assert e <= bar, e
+
+
+@pytest.mark.parametrize("precision,bar", [(0, FP64_BAR), (1, MIXED_BAR)])
+def test_direct_tolerance(precision, bar):
+    p = make_problem(2, L=10, chi=16, D=4, max_bond=0, dtype=np.complex128, seed=9)
+    (got, bonds, log_norm), _ = _run("direct", p, precision, (0, 1e-2))
+    ref = comparators.direct_tt(p.state.tensors, p.op.tensors, 0, 1e-2)
+    assert list(bonds) == list(ref.out_bonds), (bonds, ref.out_bonds)
+    e = metrics.rel_err(p.state.parent, got, ref.tensors, log_norm, 0.0)
+    assert e <= bar, e
+
+
 def test_comparators_reject_trees():
     from paper_2601_19650_gb300 import _cbc
 
@@ -122,6 +158,8 @@ def test_comparators_reject_trees():
             _cbc.zipup_apply(hs, ho, 4, 0.0)
         with pytest.raises(_cbc.CBCError, match="tensor trains"):
             _cbc.src_apply(hs, ho, 4, sketch_matrices(st.phys, 4))
+        with pytest.raises(_cbc.CBCError, match="tensor trains"):
+            _cbc.direct_apply(hs, ho, 4, 0.0)
     finally:
         _cbc.ttn_destroy(hs)
         _cbc.ttno_destroy(ho)
