@@ -1110,7 +1110,9 @@ __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
   extern __shared__ unsigned char smem_raw[];
   E* u = reinterpret_cast<E*>(smem_raw);  // [m][32]
   E* vs = u + (size_t)m * 32;             // [3][m]: v_j in slot j % 3 (staged one ahead)
-  __shared__ T part[2][BT_WARPS][32];
+  // per-warp partial dots (double-float in the DF variant: the cross-warp sum and the
+  // tau scaling then stay on the FP32 pipes, which every active warp repeats per reflector)
+  __shared__ E part[2][BT_WARPS][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // matrix blockIdx.y of a batch
   V = byte_shift(V, blockIdx.y * wb);
@@ -1144,7 +1146,7 @@ __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
     const E* v = vs + (size_t)(j % 3) * m;
     // partial dot over this warp's rows r > j, four independent accumulators
     const int rs = max(r0, j + 1);
-    T psum;
+    E psum;
     if constexpr (DF) {
       const D z = to_df(O::zero());
       D a0 = z, a1 = z, a2 = z, a3 = z;
@@ -1156,7 +1158,7 @@ __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
         a3 = dff(dfconj(v[r + 3]), u[(size_t)(r + 3) * 32 + lane], a3);
       }
       for (; r < r1; ++r) a0 = dff(dfconj(v[r]), u[(size_t)r * 32 + lane], a0);
-      psum = (from_df(a0) + from_df(a1)) + (from_df(a2) + from_df(a3));
+      psum = df_add(df_add(a0, a1), df_add(a2, a3));
     } else {
       T a0 = O::zero(), a1 = O::zero(), a2 = O::zero(), a3 = O::zero();
       int r = rs;
@@ -1179,14 +1181,17 @@ __global__ void __launch_bounds__(32 * BT_WARPS) backtransform32_kernel(
     }
     __syncthreads();
     if (rs < r1) {
-      T tot = part[par][0][lane];
-#pragma unroll
-      for (int w = 1; w < BT_WARPS; ++w) tot = tot + part[par][w][lane];
-      const T cf = tau[j] * tot;
       if constexpr (DF) {
-        const D ncf = to_df(O::scale(-1.0, cf));
+        D tot = part[par][0][lane];
+#pragma unroll
+        for (int w = 1; w < BT_WARPS; ++w) tot = df_add(tot, part[par][w][lane]);
+        const D ncf = df_neg(dff(to_df(tau[j]), tot, to_df(O::zero())));
         for (int q = rs; q < r1; ++q) u[(size_t)q * 32 + lane] = dff(v[q], ncf, u[(size_t)q * 32 + lane]);
       } else {
+        T tot = part[par][0][lane];
+#pragma unroll
+        for (int w = 1; w < BT_WARPS; ++w) tot = tot + part[par][w][lane];
+        const T cf = tau[j] * tot;
         for (int q = rs; q < r1; ++q) u[(size_t)q * 32 + lane] = u[(size_t)q * 32 + lane] - v[q] * cf;
       }
     }
