@@ -174,6 +174,9 @@ template <typename T>
 cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om, int s,
                             int64_t lp_bs, int64_t om_bs, T* C, int64_t c_bs, cudaStream_t st,
                             int nb = 1);
+// out[b] = the real part of the trace of G_b (g x g, nb matrices bs elements apart)
+template <typename T>
+cudaError_t trace_real(const T* G, int g, int64_t bs, double* out, cudaStream_t s, int nb = 1);
 // out (cols x rows, row-major) = the conjugate transpose of in (rows x cols, row-major)
 template <typename T>
 cudaError_t adjoint_copy(const T* in, int rows, int cols, T* out, cudaStream_t s);

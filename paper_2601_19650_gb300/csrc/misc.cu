@@ -242,6 +242,22 @@ __global__ void scale_rows_kernel(T* X, int rows, int cols, int64_t bs, const do
   }
 }
 
+// out[b] = sum_i Re G_b[i, i] (G_b g x g, bs elements apart): one CTA per matrix
+template <typename T>
+__global__ void trace_kernel(const T* G, int g, int64_t bs, double* out) {
+  __shared__ double red[256];
+  G += (int64_t)blockIdx.x * bs;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < g; i += blockDim.x) acc += ops<T>::real(G[(int64_t)i * g + i]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
 // out[c, r] = conj(in[r, c]) (in: rows x cols, out: cols x rows, both row-major)
 template <typename T>
 __global__ void adjoint_kernel(const T* in, int rows, int cols, T* out) {
@@ -495,6 +511,14 @@ cudaError_t scale_rows(T* X, int rows, int cols, int64_t bs, const double* norms
 }
 
 template <typename T>
+cudaError_t trace_real(const T* G, int g, int64_t bs, double* out, cudaStream_t s, int nb) {
+  if (nb <= 0) return cudaSuccess;
+  note_launches(CBC_K_AUX, 1);
+  trace_kernel<T><<<nb, 256, 0, s>>>(G, g, bs, out);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t adjoint_copy(const T* in, int rows, int cols, T* out, cudaStream_t s) {
   if ((int64_t)rows * cols <= 0) return cudaSuccess;
   note_launches(CBC_K_AUX, 1);
@@ -565,6 +589,7 @@ cudaError_t sketch_contract(const T* Lp, int c, int d, int64_t ncol, const T* om
   template cudaError_t scale_rows<T>(T*, int, int, int64_t, const double*, cudaStream_t, int); \
   template cudaError_t add_diagonal<T>(T*, int, double, cudaStream_t, int);                 \
   template cudaError_t adjoint_copy<T>(const T*, int, int, T*, cudaStream_t);               \
+  template cudaError_t trace_real<T>(const T*, int, int64_t, double*, cudaStream_t, int);   \
   template cudaError_t sketch_contract<T>(const T*, int, int, int64_t, const T*, int, int64_t, \
                                           int64_t, T*, int64_t, cudaStream_t, int);
 CBC_MISC_INST(double)

@@ -295,7 +295,6 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
   double* beyond_dev = dv + (size_t)nb * kmax;
   double* total_dev = beyond_dev + nb;
   CK(cudaMemsetAsync(dv, 0, sizeof(double) * (size_t)nb * (kmax + 2), s));
-  CK(sum_squares<T>(M, mbs, total_dev, s, nb));  // ||M||_F^2, the weight of the cut
   if (rows) {
     CK(tgemm<T>(pr, true, true, m, m, n, M, View::rowmajor(n, mbs), false, M,
                 View::transposed(n, mbs), true, K, View::rowmajor(m, (int64_t)g * g), s));
@@ -303,6 +302,8 @@ int compress_rows(Arena& ar, const Prec& pr, const T* M, int m, int n, int64_t m
     CK(tgemm<T>(pr, true, true, n, n, m, M, View::transposed(n, mbs), true, M,
                 View::rowmajor(n, mbs), false, K, View::rowmajor(n, (int64_t)g * g), s));
   }
+  // ||M||_F^2, the weight of the cut: the trace of the Gram (g reads instead of m n)
+  CK(trace_real<T>(K, g, (int64_t)g * g, total_dev, s, nb));
   // every candidate; the mixed path reduces batches to tridiagonal form in double-float
   CK(heev_top<T>(K, g, kmax, kmax, 0.0, -1.0, lam, U, sc.k, work, sc.status, num_sms(), s, nb,
                  o.concurrent, pr.mixed));
