@@ -201,6 +201,22 @@ int direct_apply(ttn_t state, ttno_t op, int64_t max_bond, double tol,
 int src_apply(ttn_t state, ttno_t op, int64_t sketch_size, const void* const* omega,
               int omega_dtype, int omega_on_device, const cbc_options* opt, ttn_t* out);
 
+/* The truncation rank rule of cbc_apply (Sec. III A compression to a bond cap, Sec. V
+ * adaptive tolerance), on the host with no GPU work, for callers that want to predict or
+ * check the bonds a compression chooses.
+ *   n              number of candidate directions (>= 1)
+ *   w              [n] host, their weights w_j = s_j^2 in descending order
+ *   beyond         weight outside the candidates (0 when they span everything)
+ *   max_bond, tol  as for cbc_apply
+ *   floor_rel      rank floor: directions with s_j <= floor_rel * s_0 are dropped
+ *   k_out          receives the kept rank: the prefix with w_j > floor_rel^2 w_0, then the
+ *                  smallest k with sum_{j>=k} w_j + beyond <= tol^2 (sum_j w_j + beyond) when
+ *                  tol > 0, then at most max_bond when max_bond > 0, at least 1
+ *   discarded_out  NULL or receives the relative discarded weight of that choice
+ * Errors: CBC_ERR_INVALID_ARG for n < 1, NULL w or k_out, or a non-finite argument.   */
+int cbc_rank_rule(int n, const double* w, double beyond, int64_t max_bond, double tol,
+                  double floor_rel, int* k_out, double* discarded_out);
+
 /* Information about a TTNS (synchronises its stream).
  *   n_nodes_out     may be NULL
  *   bond_dims_out   NULL or [n_nodes]: bond of each node to its parent (1 at the root)

@@ -67,6 +67,9 @@ def lib():
         L.cbc_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
         L.zipup_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
         L.direct_apply.argtypes = [vp, vp, i64, dbl, P(cbc_options), P(vp)]
+        L.cbc_rank_rule.argtypes = [ctypes.c_int, P(dbl), dbl, i64, dbl, dbl, P(ctypes.c_int),
+                                    P(dbl)]
+        L.cbc_rank_rule.restype = ctypes.c_int
         L.src_apply.argtypes = [vp, vp, i64, P(vp), ctypes.c_int, ctypes.c_int, P(cbc_options),
                                 P(vp)]
         L.ttn_get_info.argtypes = [vp, P(i32), P(i64), P(dbl), P(dbl)]
@@ -179,6 +182,17 @@ def zipup_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options]
     _check(lib().zipup_apply(state, op, int(max_bond), float(tol),
                              ctypes.byref(opt) if opt is not None else None, ctypes.byref(out)))
     return out
+
+
+def cbc_rank_rule(w, beyond: float, max_bond: int, tol: float, floor_rel: float):
+    """The library's truncation rank rule on host weights w (descending): (k, discarded)."""
+    arr = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+    k = ctypes.c_int()
+    disc = ctypes.c_double()
+    _check(lib().cbc_rank_rule(int(arr.size), arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                               float(beyond), int(max_bond), float(tol), float(floor_rel),
+                               ctypes.byref(k), ctypes.byref(disc)))
+    return k.value, disc.value
 
 
 def direct_apply(state, op, max_bond: int, tol: float, opt: Optional[cbc_options] = None):

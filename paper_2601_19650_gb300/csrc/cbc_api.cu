@@ -520,6 +520,24 @@ int src_apply(ttn_t state, ttno_t op, int64_t sketch_size, const void* const* om
   return rc;
 }
 
+int cbc_rank_rule(int n, const double* w, double beyond, int64_t max_bond, double tol,
+                  double floor_rel, int* k_out, double* discarded_out) {
+  if (n < 1 || !w || !k_out) return fail(CBC_ERR_INVALID_ARG, "cbc_rank_rule: bad arguments");
+  if (!std::isfinite(tol) || !std::isfinite(beyond) || !std::isfinite(floor_rel))
+    return fail(CBC_ERR_INVALID_ARG, "cbc_rank_rule: non-finite argument");
+  const int k = pick_rank(w, n, beyond, max_bond, tol, floor_rel);
+  *k_out = k;
+  if (discarded_out) {  // (beyond + sum_{j>=k} w_j) / (beyond + sum_j w_j)
+    double tail = std::max(beyond, 0.0), total = tail;
+    for (int j = 0; j < n; ++j) {
+      total += std::max(w[j], 0.0);
+      if (j >= k) tail += std::max(w[j], 0.0);
+    }
+    *discarded_out = (total > 0.0) ? tail / total : 0.0;
+  }
+  return CBC_OK;
+}
+
 int cbc_apply_batched(int n, const ttn_t* states, const ttno_t* ops, const int64_t* max_bond,
                       const double* tol, const cbc_options* opt, int workers, ttn_t* outs) {
   if (n < 0 || (n > 0 && (!states || !ops || !outs)))
